@@ -1,0 +1,172 @@
+"""Plain FP64 CPU oracle of the implicit solve (test infrastructure only).
+
+Newton-Raphson on the backward-Euler residual (Sect. 3.3.1) with restarted,
+right-preconditioned GMRES (preconditioning as in Sect. 3.3.2: solve
+A K^-1 y = b, then x = K^-1 y) and a point-block Jacobi K (the block form
+of the Jacobi preconditioner of Sect. 3.3.2: K keeps each cell's own
+n_u x n_u block of A).
+
+GMRES follows the textbook algorithm (Saad 2003, Alg. 6.9 with restarts):
+modified Gram-Schmidt Arnoldi, Givens rotations on the Hessenberg matrix,
+least-squares update at the end of each cycle. The paper uses BiCGStab;
+GMRES(30) is the Krylov method this library implements.
+
+Tiny grids also get the dense Jacobian assembled column by column from J e_k
+and a partial-pivot LU solve (numpy.linalg.solve), the linear-system pin.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional
+
+import numpy as np
+
+from .m1 import Scheme
+
+
+@dataclass
+class GmresResult:
+    x: np.ndarray
+    iters: int
+    converged: bool
+    resid: float  # true ||b - A x|| at exit
+    history: List[float] = field(default_factory=list)
+
+
+def gmres(A: Callable, b: np.ndarray, Minv: Callable, rtol: float = 1e-10, restart: int = 30,
+          maxiter: int = 3000, x0: Optional[np.ndarray] = None) -> GmresResult:
+    """Right-preconditioned restarted GMRES(restart) for A x = b.
+
+    Stops when the Arnoldi residual estimate drops to rtol * ||b|| and the
+    true residual confirms it (else it restarts from the current x).
+    """
+    n = b.size
+    x = np.zeros(n) if x0 is None else x0.copy()
+    bnorm = np.linalg.norm(b)
+    hist = []
+    if bnorm == 0.0:
+        return GmresResult(np.zeros(n), 0, True, 0.0, hist)
+    target = rtol * bnorm
+    total = 0
+    while True:
+        r = b - A(x)
+        beta = np.linalg.norm(r)
+        hist.append(beta)
+        if beta <= target or total >= maxiter:
+            return GmresResult(x, total, beta <= target, beta, hist)
+        m = restart
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k_used = 0
+        for j in range(m):
+            w = A(Minv(V[j]))
+            for i in range(j + 1):  # modified Gram-Schmidt
+                H[i, j] = np.dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0.0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):  # apply previous rotations to column j
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j] = H[j, j] / den if den > 0 else 1.0
+            sn[j] = H[j + 1, j] / den if den > 0 else 0.0
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            k_used = j + 1
+            total += 1
+            if abs(g[j + 1]) <= target or H[j, j] == 0.0 or total >= maxiter:
+                break
+        y = np.zeros(k_used)
+        for i in range(k_used - 1, -1, -1):  # back substitution on the rotated H
+            y[i] = (g[i] - H[i, i + 1:k_used] @ y[i + 1:]) / H[i, i]
+        x = x + Minv(V[:k_used].T @ y)
+
+
+def block_jacobi(blocks: np.ndarray, N: int, nu: int) -> Callable:
+    """K^-1 r with K the point-block diagonal of the Jacobian."""
+    inv = np.linalg.inv(blocks)  # (N, nu, nu)
+
+    def apply(r):
+        rr = r.reshape(nu, N).T  # (N, nu)
+        z = np.einsum("nij,nj->ni", inv, rr)
+        return z.T.reshape(-1)
+
+    return apply
+
+
+@dataclass
+class NewtonResult:
+    u: np.ndarray
+    converged: bool
+    newton_iters: int
+    gmres_iters: int
+    res0: float
+    res: float
+    history: List[float] = field(default_factory=list)
+
+
+def newton_solve(scheme: Scheme, rtol: float = 1e-8, newton_max: int = 30,
+                 gmres_rtol: float = 1e-4, restart: int = 30, gmres_max: int = 3000,
+                 precond: str = "bj", line_search: bool = True) -> NewtonResult:
+    """Backward-Euler step by Newton-Raphson (Sect. 3.3.1) from U^n.
+
+    Converged when ||R(U^k)||_2 <= rtol ||R(U^n)||_2 (2-norm over all unknowns).
+    Each Newton step solves J delta = -R to gmres_rtol; the step is damped by
+    halving theta (up to 6 times) until ||R|| decreases by the Armijo factor
+    (1 - 1e-4 theta); the last trial is taken if none does.
+    """
+    u = scheme.pack(scheme.Un)
+    R = scheme.residual(u)
+    r0 = np.linalg.norm(R)
+    hist = [r0]
+    rn = r0
+    its = 0
+    git = 0
+    N, nu = scheme.N, scheme.nu
+    while rn > rtol * r0 and its < newton_max:
+        if precond == "bj":
+            Minv = block_jacobi(scheme.diag_blocks(u), N, nu)
+        else:
+            Minv = lambda r: r  # noqa: E731
+        res = gmres(lambda v: scheme.jv(u, v), -R, Minv, rtol=gmres_rtol, restart=restart,
+                    maxiter=gmres_max)
+        git += res.iters
+        delta = res.x
+        theta = 1.0
+        for _ in range(7):
+            ut = u + theta * delta
+            Rt = scheme.residual(ut)
+            rt = np.linalg.norm(Rt)
+            if not line_search or rt <= (1.0 - 1e-4 * theta) * rn:
+                break
+            theta *= 0.5
+        u, R, rn = ut, Rt, rt
+        its += 1
+        hist.append(rn)
+    return NewtonResult(u, rn <= rtol * r0, its, git, r0, rn, hist)
+
+
+def dense_jacobian(scheme: Scheme, u: np.ndarray) -> np.ndarray:
+    """J assembled column by column as J e_k (tiny grids only)."""
+    n = u.size
+    J = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        J[:, k] = scheme.jv(u, e)
+    return J
+
+
+def dense_solve(scheme: Scheme, u: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """x = J(u)^-1 b by partial-pivot LU (LAPACK gesv via numpy)."""
+    return np.linalg.solve(dense_jacobian(scheme, u), b)
