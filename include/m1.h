@@ -1,0 +1,193 @@
+/*
+ * m1.h — C ABI of the grey M1 radiation step on one GB300 GPU (sm_103a).
+ *
+ * The library implements the time-implicit grey M1 radiative-transfer step of
+ * Bloch, Tremblin, Gonzalez, Padioleau & Audit (A&A 2021), Sects. 2-3:
+ *   - the M1 closure P = D(f) E (Sect. 2.2) and the M1 eigenvalues
+ *     (Eq. eigenvalues, Sect. 3.1.1);
+ *   - the HLL interface fluxes F*, P* (Sect. 3.1.1) with the asymptotic-
+ *     preserving correction alpha (Eq. asymptoticCorrection, Sect. 3.1.3);
+ *   - the well-balanced flux source (Eqs. wb_smart, boundaryCondition,
+ *     Sect. 3.1.2) or the centred one (Eq. wb_naive);
+ *   - absorption/emission exchange with the gas (Eqs. momentModel,
+ *     internalEnergyEqua, Sect. 2.1);
+ *   - the backward-Euler residual of Sect. 3.1.1, its Jacobian-vector product
+ *     and point-block Jacobi preconditioner, restarted GMRES and Newton-Raphson
+ *     (Sects. 3.3.1-3.3.2);
+ *   - the semi-implicit step of Sect. 3.1 (sources implicit, fluxes explicit),
+ *     whose WB source is the tridiagonal system of Appendix B.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an m1_status; nothing throws or exits across the ABI.
+ *     m1_last_error() gives a human-readable reason for the last failure.
+ *   - Arrays are structure-of-arrays, x fastest, WITHOUT ghost cells: a field
+ *     is N = nx*ny*nz doubles; F is dim consecutive fields (F_x, F_y, F_z);
+ *     an unknown vector is [E, F_x, (F_y), (F_z), (T)] = n_u*N doubles with
+ *     n_u = 1 + dim (+1 with gas coupling).
+ *   - Caller pointers are host or device memory as the m1_mem argument says.
+ *     They are read/written on the context's stream and not retained after the
+ *     call returns (the call synchronises that stream before returning).
+ *   - The context owns all the device memory it allocates (m1_init_grid and,
+ *     lazily, the first implicit call). M1_ERR_NOMEM reports a failed allocation.
+ *   - Units are the caller's: c and a_r are grid parameters (c = a_r = 1 in the
+ *     workloads shipped with this library).
+ */
+#ifndef M1_H
+#define M1_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    M1_OK = 0,
+    M1_ERR_ARG = 1,           /* invalid argument (message in m1_last_error) */
+    M1_ERR_CUDA = 2,          /* a CUDA call failed */
+    M1_ERR_NOMEM = 3,         /* device allocation failed */
+    M1_ERR_NOT_CONVERGED = 4, /* Newton/GMRES did not reach the tolerance */
+    M1_ERR_NONFINITE = 5,     /* NaN/Inf met in a residual or a norm */
+    M1_ERR_TIMEOUT = 6,       /* a bounded device wait ran out */
+    M1_ERR_STATE = 7          /* call out of order (e.g. no state set) */
+} m1_status;
+
+typedef enum { M1_BC_OUTFLOW = 0, M1_BC_PERIODIC = 1, M1_BC_REFLECT = 2, M1_BC_DIRICHLET = 3 } m1_bc;
+typedef enum { M1_MEM_HOST = 0, M1_MEM_DEVICE = 1 } m1_mem;
+typedef enum { M1_PREC_FP64 = 0, M1_PREC_MIXED = 1 } m1_precision;
+typedef enum { M1_PRECOND_NONE = 0, M1_PRECOND_BJ = 1 } m1_precond;
+
+/* Grid and discretisation flags (one context per grid). */
+typedef struct {
+    int dim;              /* 1, 2 or 3 */
+    int n[3];             /* cells per axis; unused axes must be 1 */
+    double lo[3], hi[3];  /* box; dx_a = (hi_a - lo_a) / n_a */
+    int bc[3][2];         /* m1_bc per axis and side (0 = low, 1 = high); periodic on both sides or neither */
+    double c, a_r;        /* speed of light and radiation constant */
+    int gas_coupling;     /* 1: T is an unknown (Eq. internalEnergyEqua); 0: frozen emission B */
+    int well_balanced;    /* 1: Eq. wb_smart; 0: Eq. wb_naive */
+    int ap_correction;    /* 1: alpha of Eq. asymptoticCorrection; 0: alpha = 1 (plain HLL) */
+    int fixed_eigs;       /* 1: lambda+- = +-c; 0: Eq. eigenvalues */
+    double lambda_floor;  /* lambda+ = max(floor, ...), lambda- = min(-floor, ...) (0 in the paper's default) */
+    int wb_boundary;      /* 1: Eq. boundaryCondition at non-periodic boundary faces; 0: plain face average */
+    int implicit_eigs;    /* 1: lambda in F*, P* at the new time level; 0: frozen at time n */
+} m1_grid_desc;
+
+/* Solver options (m1_default_opts fills the defaults shown). */
+typedef struct {
+    double newton_rtol;   /* 1e-8: stop when ||R(U^k)||_2 <= rtol ||R(U^n)||_2 */
+    int newton_max;       /* 30 */
+    int restart;          /* 30 (at most 30): GMRES(restart) */
+    int gmres_max;        /* 3000 total Arnoldi iterations per linear solve */
+    double gmres_rtol;    /* 1e-4: forcing term ||J d + R|| <= rtol ||R|| */
+    int precision;        /* m1_precision: FP64, or FP32 inner FGMRES under FP64 refinement */
+    int precond;          /* m1_precond */
+    int line_search;      /* 1: halve theta up to 6 times until the Armijo decrease holds */
+    int advance;          /* 1: on success U^n <- U^{n+1}; 0: keep U^n (result in m1_get_solution) */
+    int refine_max;       /* mixed precision: max FP64 refinement sweeps per Newton step (4) */
+} m1_solver_opts;
+
+typedef struct {
+    int converged;        /* 1 when ||R|| <= newton_rtol * ||R^0|| */
+    int newton_iters;
+    int gmres_iters;      /* total Arnoldi iterations over all linear solves */
+    int refinements;      /* FP64 refinement sweeps (mixed precision) */
+    double res0, res;     /* ||R(U^n)||_2 and the final ||R||_2 */
+    long long realizability_violations; /* cells with |F| > c E in the result (Sect. 3.1.3) */
+    double time_ms;       /* wall time of the step measured on the stream */
+} m1_step_info;
+
+typedef struct {
+    int converged;
+    int iters;
+    double res0, res;     /* ||b|| and the true ||b - J x|| at exit */
+} m1_solve_info;
+
+typedef struct {
+    long long newton_iters, gmres_iters, jv_calls, residual_calls, precond_builds;
+    long long explicit_steps, implicit_steps, kernel_launches;
+    double bytes_per_jv, bytes_per_residual;  /* algorithmic bytes of one launch */
+} m1_stats_t;
+
+typedef struct m1_ctx m1_ctx;
+
+void m1_default_opts(m1_solver_opts* opts);
+
+/* Create a context on the current CUDA device. cuda_stream: a cudaStream_t
+ * (NULL = the legacy default stream). Validates the descriptor (M1_ERR_ARG).
+ * Allocates the fields, the time-n state and the face arrays. */
+m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out);
+
+/* Free every device allocation of the context. NULL is accepted. */
+m1_status m1_destroy(m1_ctx* ctx);
+
+/* Opacities: sigma_a (absorption/emission, Eq. momentModel energy row) and
+ * sigma_f (flux source and alpha). sigma_f == NULL uses sigma_a. N doubles each. */
+m1_status m1_set_opacity(m1_ctx* ctx, const double* sigma_a, const double* sigma_f, m1_mem mem);
+
+/* Time-n state. E: N, F: dim*N. With gas coupling T (N) and rho_cv (N) are
+ * required; otherwise they must be NULL. Resets the time-n face data (alpha,
+ * lambda at time n). */
+m1_status m1_set_state(m1_ctx* ctx, const double* E, const double* F, const double* T,
+                       const double* rho_cv, m1_mem mem);
+
+/* Copy the context's current state out (T may be NULL without gas coupling). */
+m1_status m1_get_state(const m1_ctx* ctx, double* E, double* F, double* T, m1_mem mem);
+
+/* The result U^{n+1} of the last m1_implicit_step / m1_explicit_step, as an
+ * unknown vector (n_u*N doubles). */
+m1_status m1_get_solution(const m1_ctx* ctx, double* U, m1_mem mem);
+
+/* Dirichlet ghost data of one face (axis, side) whose bc is M1_BC_DIRICHLET:
+ * E (M cells of the face, M = N / n[axis], face cells ordered x fastest over
+ * the remaining axes), F (dim*M), mask (M bytes; 1 = use the given ghost,
+ * 0 = zero-gradient copy; NULL = all 1). */
+m1_status m1_set_boundary(m1_ctx* ctx, int axis, int side, const double* E, const double* F,
+                          const unsigned char* mask, m1_mem mem);
+
+/* Frozen emission B = a_r T_g^4 (N doubles; only without gas coupling; default 0). */
+m1_status m1_set_emission(m1_ctx* ctx, const double* B, m1_mem mem);
+
+/* External energy source S added to dE/dt (N doubles, NULL = none). */
+m1_status m1_set_source(m1_ctx* ctx, const double* S, m1_mem mem);
+
+/* One semi-implicit step of size dt (Sect. 3.1): HLL fluxes and alpha at time n,
+ * backward-Euler exchange and flux source (tridiagonal WB solves along each
+ * component's own axis, Appendix B form). Advances the state. */
+m1_status m1_explicit_step(m1_ctx* ctx, double dt);
+
+/* One backward-Euler step of size dt by Newton-Raphson + right-preconditioned
+ * restarted (F)GMRES (Sect. 3.3). On failure returns M1_ERR_NOT_CONVERGED
+ * (or M1_ERR_NONFINITE) and leaves the state unchanged; info is filled either way. */
+m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m1_step_info* info);
+
+/* R(U) of the backward-Euler step of size dt from the context's time-n state
+ * (the scheme of Sect. 3.1.1). U, R: n_u*N doubles. */
+m1_status m1_residual(m1_ctx* ctx, double dt, const double* U, double* R, m1_mem mem);
+
+/* J(U) v, the exact directional derivative of m1_residual (forward-mode dual
+ * numbers). precision: M1_PREC_FP64, or M1_PREC_MIXED for the FP32 kernel
+ * (inputs rounded to FP32, result widened to FP64). */
+m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double* Jv,
+                int precision, m1_mem mem);
+
+/* Point blocks J_ii = dR_i/dU_i of m1_residual at U (Sect. 3.3.2 block Jacobi):
+ * n_u*n_u*N doubles laid out blocks[(row*n_u + col)*N + cell]. */
+m1_status m1_diag_blocks(m1_ctx* ctx, double dt, const double* U, double* blocks, m1_mem mem);
+
+/* Solve J(U) x = b with the step's GMRES (U NULL = the time-n state).
+ * x is the output (initial guess 0). */
+m1_status m1_gmres_solve(m1_ctx* ctx, double dt, const double* U, const double* b, double* x,
+                         const m1_solver_opts* opts, m1_solve_info* info, m1_mem mem);
+
+/* Cumulative counters of the context. */
+m1_status m1_stats(const m1_ctx* ctx, m1_stats_t* out);
+
+/* Message of the last failed call on this context (never NULL). */
+const char* m1_last_error(const m1_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* M1_H */

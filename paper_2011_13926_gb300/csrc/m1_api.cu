@@ -1,0 +1,1056 @@
+// m1_api.cu — the C ABI (include/m1.h): context, data movement, the
+// semi-implicit step, and the Newton-Raphson / restarted GMRES driver of the
+// backward-Euler step (Sects. 3.3.1-3.3.2 of Bloch et al. 2021).
+//
+// The host only sequences kernels and reads back scalars (norms, the GMRES
+// residual estimate); every vector operation runs on the GPU.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/m1.h"
+#include "m1_internal.h"
+
+using namespace m1;
+
+namespace {
+
+constexpr int kHLd = kMaxRestart + 1;   // Hessenberg leading dimension
+constexpr int kPartCols = kMaxRestart + 1;
+
+struct Faces64 {
+    double* lam_p[3] = {nullptr, nullptr, nullptr};
+    double* lam_m[3] = {nullptr, nullptr, nullptr};
+    double* alpha[3] = {nullptr, nullptr, nullptr};
+};
+struct Faces32 {
+    float* lam_p[3] = {nullptr, nullptr, nullptr};
+    float* lam_m[3] = {nullptr, nullptr, nullptr};
+    float* alpha[3] = {nullptr, nullptr, nullptr};
+};
+
+// device scalars of one Krylov solve
+struct Scal {
+    double* nrm2;     // [4]
+    double* h1;       // [kPartCols]
+    double* h2;       // [kPartCols]
+    double* H;        // [kHLd * kMaxRestart]
+    double* cs;       // [kMaxRestart]
+    double* sn;       // [kMaxRestart]
+    double* g;        // [kPartCols]
+    double* y;        // [kPartCols]
+    double* resid;    // [2]
+};
+
+}  // namespace
+
+struct m1_ctx {
+    m1_grid_desc d{};
+    cudaStream_t s = nullptr;
+    int dim = 1, nu = 2;
+    long long N = 0, n = 0;
+    long long nfaces[3] = {0, 0, 0};
+    long long bM[3] = {0, 0, 0};
+    // FP64 fields
+    double *sig_a = nullptr, *sig_f = nullptr, *B = nullptr, *S = nullptr, *rho_cv = nullptr;
+    double *Un = nullptr, *Unew = nullptr;
+    double *bE[3][2] = {}, *bF[3][2] = {};
+    unsigned char* bmask[3][2] = {};
+    Faces64 f64;
+    // FP32 copies for the inner solver
+    float *sig_a32 = nullptr, *sig_f32 = nullptr, *B32 = nullptr, *S32 = nullptr, *rho_cv32 = nullptr;
+    float* Un32 = nullptr;
+    float *bE32[3][2] = {}, *bF32[3][2] = {};
+    Faces32 f32;
+    bool has_state = false, has_opacity = false, dirty = true, sigf_is_siga = true;
+    // work buffers (allocated on first use)
+    bool work_ok = false, work32_ok = false, expl_ok = false;
+    double *U = nullptr, *R = nullptr, *Ut = nullptr, *Rt = nullptr, *delta = nullptr, *rhs = nullptr;
+    double *w = nullptr, *z = nullptr, *tmp = nullptr, *V = nullptr, *xacc = nullptr;
+    double *blocks = nullptr, *binv = nullptr;
+    float *binv32 = nullptr, *V32 = nullptr, *w32 = nullptr, *z32 = nullptr, *U32 = nullptr, *tmp32 = nullptr;
+    double *Fstar = nullptr, *linework = nullptr;
+    double* partials = nullptr;
+    Scal sc{};
+    double* scal_base = nullptr;
+    int* singular = nullptr;
+    unsigned long long* viol = nullptr;
+    double* hpin = nullptr;  // pinned host scalars
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    m1_stats_t st{};
+    std::string err = "no error";
+};
+
+namespace {
+
+m1_status fail(m1_ctx* c, m1_status code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? M1_ERR_NOMEM : M1_ERR_CUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
+
+#define CKS(expr)                          \
+    do {                                   \
+        m1_status st_ = (expr);            \
+        if (st_ != M1_OK) return st_;      \
+    } while (0)
+
+template <class T>
+m1_status dalloc(m1_ctx* ctx, T** p, size_t count) {
+    if (*p) return M1_OK;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(ctx, M1_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return M1_OK;
+}
+
+m1_status copy_in(m1_ctx* ctx, void* dst, const void* src, size_t bytes, m1_mem mem) {
+    CK(cudaMemcpyAsync(dst, src, bytes, mem == M1_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       ctx->s));
+    return M1_OK;
+}
+m1_status copy_out(m1_ctx* ctx, void* dst, const void* src, size_t bytes, m1_mem mem) {
+    CK(cudaMemcpyAsync(dst, src, bytes, mem == M1_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->s));
+    return M1_OK;
+}
+m1_status sync(m1_ctx* ctx) {
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->s));
+    return M1_OK;
+}
+
+void count(m1_ctx* ctx, int k) { ctx->st.kernel_launches += k; }
+
+template <class R>
+void fill_dev_common(const m1_ctx* ctx, Dev<R>& g) {
+    g.dim = ctx->dim;
+    g.nx = ctx->d.n[0];
+    g.ny = ctx->d.n[1];
+    g.nz = ctx->d.n[2];
+    g.N = ctx->N;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = ctx->d.n[a];
+        const double dx = (ctx->d.hi[a] - ctx->d.lo[a]) / ctx->d.n[a];
+        g.dx[a] = (R)dx;
+        g.inv_dx[a] = (R)(1.0 / dx);
+        g.bM[a] = ctx->bM[a];
+        for (int sd = 0; sd < 2; ++sd) g.bc[a][sd] = ctx->d.bc[a][sd];
+    }
+    g.stride[0] = 1;
+    g.stride[1] = ctx->d.n[0];
+    g.stride[2] = (long long)ctx->d.n[0] * ctx->d.n[1];
+    g.c = (R)ctx->d.c;
+    g.a_r = (R)ctx->d.a_r;
+    g.lambda_floor = (R)ctx->d.lambda_floor;
+    g.gas = ctx->d.gas_coupling;
+    g.wb = ctx->d.well_balanced;
+    g.ap = ctx->d.ap_correction;
+    g.fixed_eigs = ctx->d.fixed_eigs;
+    g.wb_boundary = ctx->d.wb_boundary;
+    g.implicit_eigs = ctx->d.implicit_eigs;
+}
+
+Dev<double> dev64(const m1_ctx* ctx, double dt) {
+    Dev<double> g{};
+    fill_dev_common(ctx, g);
+    g.dt = dt;
+    g.sig_a = ctx->sig_a;
+    g.sig_f = ctx->sig_f;
+    g.B = ctx->d.gas_coupling ? nullptr : ctx->B;
+    g.S = ctx->S;
+    g.rho_cv = ctx->rho_cv;
+    g.Un = ctx->Un;
+    for (int a = 0; a < 3; ++a) {
+        g.alpha[a] = ctx->f64.alpha[a];
+        g.lam_p[a] = ctx->f64.lam_p[a];
+        g.lam_m[a] = ctx->f64.lam_m[a];
+        for (int sd = 0; sd < 2; ++sd) {
+            g.bE[a][sd] = ctx->bE[a][sd];
+            g.bF[a][sd] = ctx->bF[a][sd];
+            g.bmask[a][sd] = ctx->bmask[a][sd];
+        }
+    }
+    return g;
+}
+
+Dev<float> dev32(const m1_ctx* ctx, double dt) {
+    Dev<float> g{};
+    fill_dev_common(ctx, g);
+    g.dt = (float)dt;
+    g.sig_a = ctx->sig_a32;
+    g.sig_f = ctx->sig_f32;
+    g.B = ctx->d.gas_coupling ? nullptr : ctx->B32;
+    g.S = ctx->S ? ctx->S32 : nullptr;
+    g.rho_cv = ctx->rho_cv32;
+    g.Un = ctx->Un32;
+    for (int a = 0; a < 3; ++a) {
+        g.alpha[a] = ctx->f32.alpha[a];
+        g.lam_p[a] = ctx->f32.lam_p[a];
+        g.lam_m[a] = ctx->f32.lam_m[a];
+        for (int sd = 0; sd < 2; ++sd) {
+            g.bE[a][sd] = ctx->bE32[a][sd];
+            g.bF[a][sd] = ctx->bF32[a][sd];
+            g.bmask[a][sd] = ctx->bmask[a][sd];
+        }
+    }
+    return g;
+}
+
+// recompute the time-n face data and the FP32 copies after any input changed
+m1_status prepare(m1_ctx* ctx) {
+    if (!ctx->has_state) return fail(ctx, M1_ERR_STATE, "no state: call m1_set_state first");
+    if (!ctx->has_opacity) return fail(ctx, M1_ERR_STATE, "no opacity: call m1_set_opacity first");
+    for (int a = 0; a < ctx->dim; ++a)
+        for (int sd = 0; sd < 2; ++sd)
+            if (ctx->d.bc[a][sd] == M1_BC_DIRICHLET && !ctx->bE[a][sd])
+                return fail(ctx, M1_ERR_STATE, "Dirichlet boundary without data: call m1_set_boundary");
+    if (!ctx->dirty) return M1_OK;
+    Dev<double> g = dev64(ctx, 0.0);
+    launch_faces_time_n(g, ctx->f64.lam_p, ctx->f64.lam_m, ctx->f64.alpha, ctx->s);
+    count(ctx, ctx->dim);
+    const long long N = ctx->N;
+    launch_f64_to_f32(ctx->sig_a, ctx->sig_a32, N, ctx->s);
+    launch_f64_to_f32(ctx->sig_f, ctx->sig_f32, N, ctx->s);
+    if (ctx->B) launch_f64_to_f32(ctx->B, ctx->B32, N, ctx->s);
+    if (ctx->S) launch_f64_to_f32(ctx->S, ctx->S32, N, ctx->s);
+    if (ctx->rho_cv) launch_f64_to_f32(ctx->rho_cv, ctx->rho_cv32, N, ctx->s);
+    launch_f64_to_f32(ctx->Un, ctx->Un32, ctx->n, ctx->s);
+    for (int a = 0; a < ctx->dim; ++a) {
+        launch_f64_to_f32(ctx->f64.alpha[a], ctx->f32.alpha[a], ctx->nfaces[a], ctx->s);
+        launch_f64_to_f32(ctx->f64.lam_p[a], ctx->f32.lam_p[a], ctx->nfaces[a], ctx->s);
+        launch_f64_to_f32(ctx->f64.lam_m[a], ctx->f32.lam_m[a], ctx->nfaces[a], ctx->s);
+        for (int sd = 0; sd < 2; ++sd)
+            if (ctx->bE[a][sd]) {
+                launch_f64_to_f32(ctx->bE[a][sd], ctx->bE32[a][sd], ctx->bM[a], ctx->s);
+                launch_f64_to_f32(ctx->bF[a][sd], ctx->bF32[a][sd], ctx->bM[a] * ctx->dim, ctx->s);
+            }
+    }
+    ctx->dirty = false;
+    return sync(ctx);
+}
+
+m1_status ensure_work(m1_ctx* ctx) {
+    if (ctx->work_ok) return M1_OK;
+    const long long n = ctx->n, N = ctx->N;
+    const int nu = ctx->nu;
+    CKS(dalloc(ctx, &ctx->U, n));
+    CKS(dalloc(ctx, &ctx->R, n));
+    CKS(dalloc(ctx, &ctx->Ut, n));
+    CKS(dalloc(ctx, &ctx->Rt, n));
+    CKS(dalloc(ctx, &ctx->delta, n));
+    CKS(dalloc(ctx, &ctx->rhs, n));
+    CKS(dalloc(ctx, &ctx->w, n));
+    CKS(dalloc(ctx, &ctx->z, n));
+    CKS(dalloc(ctx, &ctx->tmp, n));
+    CKS(dalloc(ctx, &ctx->xacc, n));
+    CKS(dalloc(ctx, &ctx->V, (size_t)n * (kMaxRestart + 1)));
+    CKS(dalloc(ctx, &ctx->blocks, (size_t)nu * nu * N));
+    CKS(dalloc(ctx, &ctx->binv, (size_t)nu * nu * N));
+    CKS(dalloc(ctx, &ctx->binv32, (size_t)nu * nu * N));
+    ctx->work_ok = true;
+    return M1_OK;
+}
+
+m1_status ensure_work32(m1_ctx* ctx) {
+    if (ctx->work32_ok) return M1_OK;
+    const long long n = ctx->n;
+    CKS(dalloc(ctx, &ctx->V32, (size_t)n * (kMaxRestart + 1)));
+    CKS(dalloc(ctx, &ctx->w32, n));
+    CKS(dalloc(ctx, &ctx->z32, n));
+    CKS(dalloc(ctx, &ctx->U32, n));
+    CKS(dalloc(ctx, &ctx->tmp32, n));
+    ctx->work32_ok = true;
+    return M1_OK;
+}
+
+// ||x||_2 read back to the host (FP64 accumulation)
+m1_status norm_f64(m1_ctx* ctx, const double* x, double* out) {
+    launch_norm2_f64(x, ctx->n, ctx->partials, ctx->sc.nrm2, ctx->s);
+    count(ctx, 2);
+    CK(cudaMemcpyAsync(ctx->hpin, ctx->sc.nrm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CKS(sync(ctx));
+    *out = sqrt(ctx->hpin[0]);
+    return M1_OK;
+}
+
+// R = R(U) and its norm
+m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g, const double* U, double* R, double* nrm) {
+    const int nb = stencil_blocks(ctx->N);
+    launch_residual_f64(g, U, R, ctx->partials, nb, ctx->s);
+    launch_finish_sum(ctx->partials, nb, 1, ctx->sc.nrm2, ctx->s);
+    count(ctx, 2);
+    ctx->st.residual_calls++;
+    CK(cudaMemcpyAsync(ctx->hpin, ctx->sc.nrm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CKS(sync(ctx));
+    *nrm = sqrt(ctx->hpin[0]);
+    return M1_OK;
+}
+
+m1_status build_precond(m1_ctx* ctx, const Dev<double>& g, const double* U) {
+    launch_diag_f64(g, U, ctx->blocks, ctx->s);
+    CK(cudaMemsetAsync(ctx->singular, 0, sizeof(int), ctx->s));
+    launch_block_inverse(ctx->nu, ctx->N, ctx->blocks, ctx->binv, ctx->binv32, ctx->singular, ctx->s);
+    count(ctx, 2);
+    ctx->st.precond_builds++;
+    return M1_OK;
+}
+
+// ---------------------------------------------------------------- GMRES
+// Precision-generic pieces of restarted right-preconditioned GMRES with CGS2
+// Arnoldi (two classical Gram-Schmidt passes), FP64 dot accumulation and an
+// FP64 Hessenberg least-squares solved by Givens rotations on the device.
+struct Ops64 {
+    m1_ctx* ctx;
+    Dev<double> g;
+    const double* U;
+    bool precond;
+    void A(const double* in, double* out) {
+        launch_jv_f64(g, U, in, out, ctx->s);
+        count(ctx, 1);
+        ctx->st.jv_calls++;
+    }
+    void M(const double* in, double* out) {
+        if (precond) {
+            launch_bj_apply_f64(ctx->nu, ctx->N, ctx->binv, in, out, ctx->s);
+        } else {
+            cudaMemcpyAsync(out, in, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s);
+        }
+        count(ctx, 1);
+    }
+};
+struct Ops32 {
+    m1_ctx* ctx;
+    Dev<float> g;
+    const float* U;
+    bool precond;
+    void A(const float* in, float* out) {
+        launch_jv_f32(g, U, in, out, ctx->s);
+        count(ctx, 1);
+        ctx->st.jv_calls++;
+    }
+    void M(const float* in, float* out) {
+        if (precond) {
+            launch_bj_apply_f32(ctx->nu, ctx->N, ctx->binv32, in, out, ctx->s);
+        } else {
+            cudaMemcpyAsync(out, in, sizeof(float) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s);
+        }
+        count(ctx, 1);
+    }
+};
+
+inline void multidot(const double* V, long long ld, int j, const double* w, long long n, double* p, double* h,
+                     cudaStream_t s) {
+    launch_multidot_f64(V, ld, j, w, n, p, h, s);
+}
+inline void multidot(const float* V, long long ld, int j, const float* w, long long n, double* p, double* h,
+                     cudaStream_t s) {
+    launch_multidot_f32(V, ld, j, w, n, p, h, s);
+}
+inline void cgs_update(const double* V, long long ld, int j, const double* h, double* w, long long n, double* p,
+                       cudaStream_t s) {
+    launch_cgs_update_f64(V, ld, j, h, w, n, p, s);
+}
+inline void cgs_update(const float* V, long long ld, int j, const double* h, float* w, long long n, double* p,
+                       cudaStream_t s) {
+    launch_cgs_update_f32(V, ld, j, h, w, n, p, s);
+}
+inline void scale_inv_sqrt(const double* x, const double* n2, double* y, long long n, cudaStream_t s) {
+    launch_scale_inv_sqrt_f64(x, n2, y, n, s);
+}
+inline void scale_inv_sqrt(const float* x, const double* n2, float* y, long long n, cudaStream_t s) {
+    launch_scale_inv_sqrt_f32(x, n2, y, n, s);
+}
+inline void lincomb_add(const double* Z, long long ld, int k, const double* y, double* x, long long n,
+                        cudaStream_t s) {
+    launch_lincomb_add_f64(Z, ld, k, y, x, n, s);
+}
+inline void lincomb_add(const float* Z, long long ld, int k, const double* y, double* x, long long n,
+                        cudaStream_t s) {
+    launch_lincomb_add_f32_to_f64(Z, ld, k, y, x, n, s);
+}
+inline void norm2(const double* x, long long n, double* p, double* out, cudaStream_t s) {
+    launch_norm2_f64(x, n, p, out, s);
+}
+inline void norm2(const float* x, long long n, double* p, double* out, cudaStream_t s) {
+    launch_norm2_f32(x, n, p, out, s);
+}
+
+// One GMRES(m) cycle on A M^-1 from the residual r0 (||r0||^2 in sc.nrm2[0],
+// ||r0|| = beta). On return ctx->tmp (FP64) holds V y, the caller adds
+// M^-1 V y to its solution. *kout = Arnoldi steps taken, *est = the final
+// residual estimate |g_k|.
+template <class T, class Ops>
+m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, double beta, double target, int maxk,
+                      int* kout, double* est) {
+    const long long n = ctx->n;
+    cudaStream_t s = ctx->s;
+    const Scal& sc = ctx->sc;
+    scale_inv_sqrt(r0, sc.nrm2, V, n, s);
+    count(ctx, 1);
+    std::vector<double> g0(kPartCols, 0.0);
+    g0[0] = beta;
+    CK(cudaMemcpyAsync(sc.g, g0.data(), sizeof(double) * kPartCols, cudaMemcpyHostToDevice, s));
+    int k = 0;
+    double e = beta;
+    for (int j = 0; j < maxk; ++j) {
+        T* Vj = V + (long long)j * n;
+        ops.M(Vj, z);
+        ops.A(z, w);
+        multidot(V, n, j, w, n, ctx->partials, sc.h1, s);
+        cgs_update(V, n, j, sc.h1, w, n, nullptr, s);
+        multidot(V, n, j, w, n, ctx->partials, sc.h2, s);
+        cgs_update(V, n, j, sc.h2, w, n, ctx->partials, s);
+        launch_finish_sum(ctx->partials, reduce_blocks(), 1, sc.nrm2 + 1, s);
+        launch_givens(sc.H, sc.cs, sc.sn, sc.g, sc.h1, sc.h2, sc.nrm2 + 1, j, sc.resid, s);
+        scale_inv_sqrt(w, sc.nrm2 + 1, V + (long long)(j + 1) * n, n, s);
+        count(ctx, 10);
+        CK(cudaMemcpyAsync(ctx->hpin, sc.resid, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CKS(sync(ctx));
+        k = j + 1;
+        e = ctx->hpin[0];
+        ctx->st.gmres_iters++;
+        if (!(e == e)) return fail(ctx, M1_ERR_NONFINITE, "non-finite GMRES residual estimate");
+        if (e <= target || ctx->hpin[1] == 0.0) break;
+    }
+    launch_backsolve(sc.H, sc.g, k, sc.y, s);
+    CK(cudaMemsetAsync(ctx->tmp, 0, sizeof(double) * n, s));
+    lincomb_add(V, n, k, sc.y, ctx->tmp, n, s);
+    count(ctx, 2);
+    *kout = k;
+    *est = e;
+    return M1_OK;
+}
+
+// Restarted right-preconditioned GMRES in FP64: x = J(U)^-1 b to rtol.
+m1_status gmres64(m1_ctx* ctx, Ops64& ops, const double* b, double* x, double rtol, int restart, int maxit,
+                  int* iters, double* bnorm_out, double* res_out, bool* conv) {
+    const long long n = ctx->n;
+    cudaStream_t s = ctx->s;
+    double bnorm;
+    CKS(norm_f64(ctx, b, &bnorm));
+    *bnorm_out = bnorm;
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    *iters = 0;
+    *conv = false;
+    *res_out = bnorm;
+    if (bnorm == 0.0) {
+        *conv = true;
+        return M1_OK;
+    }
+    if (!(bnorm == bnorm)) return fail(ctx, M1_ERR_NONFINITE, "non-finite right-hand side");
+    const double target = rtol * bnorm;
+    for (bool first = true;; first = false) {
+        double beta;
+        if (first) {  // x = 0: r = b, ||b||^2 already in sc.nrm2[0]
+            CK(cudaMemcpyAsync(ctx->rhs, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            beta = bnorm;
+        } else {  // r = b - J x
+            ops.A(x, ctx->w);
+            launch_axpby_f64(1.0, b, -1.0, ctx->w, ctx->rhs, n, s);
+            count(ctx, 1);
+            CKS(norm_f64(ctx, ctx->rhs, &beta));
+        }
+        *res_out = beta;
+        if (!(beta == beta)) return fail(ctx, M1_ERR_NONFINITE, "non-finite GMRES residual");
+        if (beta <= target) {
+            *conv = true;
+            return M1_OK;
+        }
+        if (*iters >= maxit) return M1_OK;
+        int k;
+        double est;
+        const int maxk = std::min(restart, maxit - *iters);
+        CKS(gmres_cycle<double>(ctx, ops, ctx->V, ctx->w, ctx->z, ctx->rhs, beta, target, maxk, &k, &est));
+        *iters += k;
+        ops.M(ctx->tmp, ctx->z);
+        launch_axpy_f64(1.0, ctx->z, x, n, s);
+        count(ctx, 1);
+    }
+}
+
+// Mixed precision: FP32 inner GMRES (FP32 Jv, FP32 basis and block inverse,
+// FP64 dot accumulation and Hessenberg) on r / ||r||, refined against the
+// FP64 linear residual r = b - J x (FP64 Jv) until rtol is met.
+m1_status gmres_mixed(m1_ctx* ctx, Ops64& ops64, Ops32& ops32, const double* b, double* x, double rtol,
+                      int restart, int maxit, int refine_max, int* iters, int* refinements, double* bnorm_out,
+                      double* res_out, bool* conv) {
+    const long long n = ctx->n;
+    cudaStream_t s = ctx->s;
+    double bnorm;
+    CKS(norm_f64(ctx, b, &bnorm));  // leaves ||b||^2 in sc.nrm2[0]
+    *bnorm_out = bnorm;
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    *iters = 0;
+    *refinements = 0;
+    *conv = false;
+    *res_out = bnorm;
+    if (bnorm == 0.0) {
+        *conv = true;
+        return M1_OK;
+    }
+    const double target = rtol * bnorm;
+    CK(cudaMemcpyAsync(ctx->rhs, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    double rnorm = bnorm;
+    for (int sweep = 0;; ++sweep) {
+        *res_out = rnorm;
+        if (!(rnorm == rnorm)) return fail(ctx, M1_ERR_NONFINITE, "non-finite refinement residual");
+        if (rnorm <= target) {
+            *conv = true;
+            return M1_OK;
+        }
+        if (sweep > refine_max || *iters >= maxit) return M1_OK;
+        // inner relative tolerance that meets the outer target if FP32 were exact
+        const double inner_rtol = std::max(0.5 * target / rnorm, 1e-6);
+        launch_scale_f64_to_f32(ctx->rhs, ctx->sc.nrm2, ctx->w32, n, s);  // unit right-hand side
+        CK(cudaMemsetAsync(ctx->xacc, 0, sizeof(double) * n, s));
+        count(ctx, 1);
+        for (bool first = true;; first = false) {
+            // r32 = unit rhs - J32 xacc
+            if (first) {
+                CK(cudaMemcpyAsync(ctx->tmp32, ctx->w32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+            } else {
+                launch_f64_to_f32(ctx->xacc, ctx->z32, n, s);
+                ops32.A(ctx->z32, ctx->tmp32);
+                launch_f32_to_f64(ctx->tmp32, ctx->tmp, n, s);
+                launch_f32_to_f64(ctx->w32, ctx->z, n, s);
+                launch_axpby_f64(1.0, ctx->z, -1.0, ctx->tmp, ctx->tmp, n, s);
+                launch_f64_to_f32(ctx->tmp, ctx->tmp32, n, s);
+                count(ctx, 4);
+            }
+            launch_norm2_f32(ctx->tmp32, n, ctx->partials, ctx->sc.nrm2, s);
+            count(ctx, 2);
+            CK(cudaMemcpyAsync(ctx->hpin, ctx->sc.nrm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CKS(sync(ctx));
+            const double beta = sqrt(ctx->hpin[0]);
+            if (!(beta == beta)) return fail(ctx, M1_ERR_NONFINITE, "non-finite inner residual");
+            if (beta <= inner_rtol || *iters >= maxit) break;
+            int k;
+            double est;
+            const int maxk = std::min(restart, maxit - *iters);
+            CKS(gmres_cycle<float>(ctx, ops32, ctx->V32, ctx->z32 /*w*/, ctx->tmp32 /*z*/, ctx->tmp32, beta,
+                                   inner_rtol, maxk, &k, &est));
+            *iters += k;
+            ops64.M(ctx->tmp, ctx->z);
+            launch_axpy_f64(1.0, ctx->z, ctx->xacc, n, s);
+            count(ctx, 1);
+        }
+        // x += ||r|| xacc ; r = b - J64 x
+        launch_axpy_f64(rnorm, ctx->xacc, x, n, s);
+        ops64.A(x, ctx->w);
+        launch_axpby_f64(1.0, b, -1.0, ctx->w, ctx->rhs, n, s);
+        count(ctx, 2);
+        CKS(norm_f64(ctx, ctx->rhs, &rnorm));  // leaves ||r||^2 in sc.nrm2[0]
+        ++*refinements;
+    }
+}
+
+m1_status validate(const m1_grid_desc* d, std::string& why) {
+    if (!d) {
+        why = "null descriptor";
+        return M1_ERR_ARG;
+    }
+    if (d->dim < 1 || d->dim > 3) {
+        why = "dim must be 1, 2 or 3";
+        return M1_ERR_ARG;
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (d->n[a] < 1) {
+            why = "n[a] must be >= 1";
+            return M1_ERR_ARG;
+        }
+        if (a >= d->dim && d->n[a] != 1) {
+            why = "unused axes must have n = 1";
+            return M1_ERR_ARG;
+        }
+        if (a < d->dim) {
+            if (!(d->hi[a] > d->lo[a])) {
+                why = "hi must exceed lo";
+                return M1_ERR_ARG;
+            }
+            for (int sd = 0; sd < 2; ++sd)
+                if (d->bc[a][sd] < 0 || d->bc[a][sd] > 3) {
+                    why = "unknown boundary kind";
+                    return M1_ERR_ARG;
+                }
+            if ((d->bc[a][0] == M1_BC_PERIODIC) != (d->bc[a][1] == M1_BC_PERIODIC)) {
+                why = "periodic must be set on both sides of an axis";
+                return M1_ERR_ARG;
+            }
+        }
+    }
+    if (!(d->c > 0.0) || !(d->a_r > 0.0)) {
+        why = "c and a_r must be positive";
+        return M1_ERR_ARG;
+    }
+    if (!(d->lambda_floor >= 0.0)) {
+        why = "lambda_floor must be >= 0";
+        return M1_ERR_ARG;
+    }
+    const long long N = (long long)d->n[0] * d->n[1] * d->n[2];
+    if (N > (1LL << 31)) {
+        why = "grid too large";
+        return M1_ERR_ARG;
+    }
+    return M1_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+void m1_default_opts(m1_solver_opts* o) {
+    if (!o) return;
+    o->newton_rtol = 1e-8;
+    o->newton_max = 30;
+    o->restart = 30;
+    o->gmres_max = 3000;
+    o->gmres_rtol = 1e-4;
+    o->precision = M1_PREC_FP64;
+    o->precond = M1_PRECOND_BJ;
+    o->line_search = 1;
+    o->advance = 1;
+    o->refine_max = 4;
+}
+
+m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out) {
+    if (!out) return M1_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    m1_status v = validate(desc, why);
+    if (v != M1_OK) return v;
+    m1_ctx* ctx = new (std::nothrow) m1_ctx();
+    if (!ctx) return M1_ERR_NOMEM;
+    ctx->d = *desc;
+    ctx->s = (cudaStream_t)cuda_stream;
+    ctx->dim = desc->dim;
+    ctx->nu = 1 + desc->dim + (desc->gas_coupling ? 1 : 0);
+    ctx->N = (long long)desc->n[0] * desc->n[1] * desc->n[2];
+    ctx->n = ctx->N * ctx->nu;
+    for (int a = 0; a < 3; ++a) {
+        ctx->nfaces[a] = ctx->N / desc->n[a] * (desc->n[a] + 1);
+        ctx->bM[a] = ctx->N / desc->n[a];
+    }
+    auto cleanup = [&](m1_status st) {
+        ctx->err.clear();
+        m1_destroy(ctx);
+        return st;
+    };
+    const long long N = ctx->N, n = ctx->n;
+#define AL(p, cnt)                                        \
+    do {                                                  \
+        m1_status st_ = dalloc(ctx, &(p), (size_t)(cnt)); \
+        if (st_ != M1_OK) return cleanup(st_);            \
+    } while (0)
+    AL(ctx->sig_a, N);
+    AL(ctx->sig_f, N);
+    AL(ctx->Un, n);
+    AL(ctx->Unew, n);
+    AL(ctx->sig_a32, N);
+    AL(ctx->sig_f32, N);
+    AL(ctx->Un32, n);
+    if (desc->gas_coupling) {
+        AL(ctx->rho_cv, N);
+        AL(ctx->rho_cv32, N);
+    } else {
+        AL(ctx->B, N);
+        AL(ctx->B32, N);
+    }
+    for (int a = 0; a < ctx->dim; ++a) {
+        AL(ctx->f64.alpha[a], ctx->nfaces[a]);
+        AL(ctx->f64.lam_p[a], ctx->nfaces[a]);
+        AL(ctx->f64.lam_m[a], ctx->nfaces[a]);
+        AL(ctx->f32.alpha[a], ctx->nfaces[a]);
+        AL(ctx->f32.lam_p[a], ctx->nfaces[a]);
+        AL(ctx->f32.lam_m[a], ctx->nfaces[a]);
+    }
+    AL(ctx->partials, (size_t)reduce_blocks() * kPartCols + stencil_blocks(N));
+    const size_t nscal = 4 + 4 * kPartCols + (size_t)kHLd * kMaxRestart + 2 * kMaxRestart + 2;
+    AL(ctx->scal_base, nscal);
+    AL(ctx->singular, 1);
+    AL(ctx->viol, 1);
+#undef AL
+    double* p = ctx->scal_base;
+    ctx->sc.nrm2 = p;
+    p += 4;
+    ctx->sc.h1 = p;
+    p += kPartCols;
+    ctx->sc.h2 = p;
+    p += kPartCols;
+    ctx->sc.g = p;
+    p += kPartCols;
+    ctx->sc.y = p;
+    p += kPartCols;
+    ctx->sc.H = p;
+    p += (size_t)kHLd * kMaxRestart;
+    ctx->sc.cs = p;
+    p += kMaxRestart;
+    ctx->sc.sn = p;
+    p += kMaxRestart;
+    ctx->sc.resid = p;
+    if (cudaMallocHost((void**)&ctx->hpin, 16 * sizeof(double)) != cudaSuccess) return cleanup(M1_ERR_NOMEM);
+    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
+        return cleanup(M1_ERR_CUDA);
+    if (cudaMemsetAsync(ctx->scal_base, 0, nscal * sizeof(double), ctx->s) != cudaSuccess) return cleanup(M1_ERR_CUDA);
+    if (!desc->gas_coupling && cudaMemsetAsync(ctx->B, 0, N * sizeof(double), ctx->s) != cudaSuccess)
+        return cleanup(M1_ERR_CUDA);
+    if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cleanup(M1_ERR_CUDA);
+    ctx->st.bytes_per_jv = (double)N * (8.0 * (2 * ctx->nu + ctx->nu) + 8.0 * 2 + 8.0 * ctx->dim);
+    ctx->st.bytes_per_residual = (double)N * (8.0 * (3 * ctx->nu) + 8.0 * 3 + 8.0 * ctx->dim);
+    *out = ctx;
+    return M1_OK;
+}
+
+m1_status m1_destroy(m1_ctx* ctx) {
+    if (!ctx) return M1_OK;
+    cudaStreamSynchronize(ctx->s);
+    void* ptrs[] = {ctx->sig_a, ctx->sig_f, ctx->B, ctx->S, ctx->rho_cv, ctx->Un, ctx->Unew, ctx->sig_a32,
+                    ctx->sig_f32, ctx->B32, ctx->S32, ctx->rho_cv32, ctx->Un32, ctx->U, ctx->R, ctx->Ut, ctx->Rt,
+                    ctx->delta, ctx->rhs, ctx->w, ctx->z, ctx->tmp, ctx->V, ctx->xacc, ctx->blocks, ctx->binv,
+                    ctx->binv32, ctx->V32, ctx->w32, ctx->z32, ctx->U32, ctx->tmp32, ctx->Fstar, ctx->linework,
+                    ctx->partials, ctx->scal_base, ctx->singular, ctx->viol};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    for (int a = 0; a < 3; ++a) {
+        void* fp[] = {ctx->f64.alpha[a], ctx->f64.lam_p[a], ctx->f64.lam_m[a],
+                      ctx->f32.alpha[a], ctx->f32.lam_p[a], ctx->f32.lam_m[a]};
+        for (void* q : fp)
+            if (q) cudaFree(q);
+        for (int sd = 0; sd < 2; ++sd) {
+            void* bp[] = {ctx->bE[a][sd], ctx->bF[a][sd], ctx->bmask[a][sd], ctx->bE32[a][sd], ctx->bF32[a][sd]};
+            for (void* q : bp)
+                if (q) cudaFree(q);
+        }
+    }
+    if (ctx->hpin) cudaFreeHost(ctx->hpin);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+    return M1_OK;
+}
+
+m1_status m1_set_opacity(m1_ctx* ctx, const double* sigma_a, const double* sigma_f, m1_mem mem) {
+    if (!ctx) return M1_ERR_ARG;
+    if (!sigma_a) return fail(ctx, M1_ERR_ARG, "sigma_a is required");
+    const size_t bytes = sizeof(double) * ctx->N;
+    CKS(copy_in(ctx, ctx->sig_a, sigma_a, bytes, mem));
+    CKS(copy_in(ctx, ctx->sig_f, sigma_f ? sigma_f : sigma_a, bytes, mem));
+    ctx->has_opacity = true;
+    ctx->dirty = true;
+    return sync(ctx);
+}
+
+m1_status m1_set_state(m1_ctx* ctx, const double* E, const double* F, const double* T, const double* rho_cv,
+                       m1_mem mem) {
+    if (!ctx) return M1_ERR_ARG;
+    if (!E || !F) return fail(ctx, M1_ERR_ARG, "E and F are required");
+    const bool gas = ctx->d.gas_coupling != 0;
+    if (gas && (!T || !rho_cv)) return fail(ctx, M1_ERR_ARG, "gas coupling needs T and rho_cv");
+    if (!gas && (T || rho_cv)) return fail(ctx, M1_ERR_ARG, "T/rho_cv given without gas coupling");
+    const size_t fb = sizeof(double) * ctx->N;
+    CKS(copy_in(ctx, ctx->Un, E, fb, mem));
+    CKS(copy_in(ctx, ctx->Un + ctx->N, F, fb * ctx->dim, mem));
+    if (gas) {
+        CKS(copy_in(ctx, ctx->Un + (1 + ctx->dim) * ctx->N, T, fb, mem));
+        CKS(copy_in(ctx, ctx->rho_cv, rho_cv, fb, mem));
+    }
+    ctx->has_state = true;
+    ctx->dirty = true;
+    return sync(ctx);
+}
+
+m1_status m1_get_state(const m1_ctx* cctx, double* E, double* F, double* T, m1_mem mem) {
+    m1_ctx* ctx = const_cast<m1_ctx*>(cctx);
+    if (!ctx) return M1_ERR_ARG;
+    if (!ctx->has_state) return fail(ctx, M1_ERR_STATE, "no state");
+    const size_t fb = sizeof(double) * ctx->N;
+    if (E) CKS(copy_out(ctx, E, ctx->Un, fb, mem));
+    if (F) CKS(copy_out(ctx, F, ctx->Un + ctx->N, fb * ctx->dim, mem));
+    if (T && ctx->d.gas_coupling) CKS(copy_out(ctx, T, ctx->Un + (1 + ctx->dim) * ctx->N, fb, mem));
+    return sync(ctx);
+}
+
+m1_status m1_get_solution(const m1_ctx* cctx, double* U, m1_mem mem) {
+    m1_ctx* ctx = const_cast<m1_ctx*>(cctx);
+    if (!ctx || !U) return M1_ERR_ARG;
+    CKS(copy_out(ctx, U, ctx->Unew, sizeof(double) * ctx->n, mem));
+    return sync(ctx);
+}
+
+m1_status m1_set_boundary(m1_ctx* ctx, int axis, int side, const double* E, const double* F,
+                          const unsigned char* mask, m1_mem mem) {
+    if (!ctx) return M1_ERR_ARG;
+    if (axis < 0 || axis >= ctx->dim || side < 0 || side > 1) return fail(ctx, M1_ERR_ARG, "bad axis/side");
+    if (ctx->d.bc[axis][side] != M1_BC_DIRICHLET) return fail(ctx, M1_ERR_ARG, "face is not Dirichlet");
+    if (!E || !F) return fail(ctx, M1_ERR_ARG, "E and F are required");
+    const long long M = ctx->bM[axis];
+    CKS(dalloc(ctx, &ctx->bE[axis][side], M));
+    CKS(dalloc(ctx, &ctx->bF[axis][side], M * ctx->dim));
+    CKS(dalloc(ctx, &ctx->bE32[axis][side], M));
+    CKS(dalloc(ctx, &ctx->bF32[axis][side], M * ctx->dim));
+    CKS(copy_in(ctx, ctx->bE[axis][side], E, sizeof(double) * M, mem));
+    CKS(copy_in(ctx, ctx->bF[axis][side], F, sizeof(double) * M * ctx->dim, mem));
+    if (mask) {
+        CKS(dalloc(ctx, &ctx->bmask[axis][side], M));
+        CKS(copy_in(ctx, ctx->bmask[axis][side], mask, M, mem));
+    } else if (ctx->bmask[axis][side]) {
+        cudaFree(ctx->bmask[axis][side]);
+        ctx->bmask[axis][side] = nullptr;
+    }
+    ctx->dirty = true;
+    return sync(ctx);
+}
+
+m1_status m1_set_emission(m1_ctx* ctx, const double* B, m1_mem mem) {
+    if (!ctx) return M1_ERR_ARG;
+    if (ctx->d.gas_coupling) return fail(ctx, M1_ERR_ARG, "emission is a_r T^4 with gas coupling");
+    if (!B) return fail(ctx, M1_ERR_ARG, "B is required");
+    CKS(copy_in(ctx, ctx->B, B, sizeof(double) * ctx->N, mem));
+    ctx->dirty = true;
+    return sync(ctx);
+}
+
+m1_status m1_set_source(m1_ctx* ctx, const double* S, m1_mem mem) {
+    if (!ctx) return M1_ERR_ARG;
+    if (!S) {
+        if (ctx->S) cudaFree(ctx->S);
+        if (ctx->S32) cudaFree(ctx->S32);
+        ctx->S = nullptr;
+        ctx->S32 = nullptr;
+        ctx->dirty = true;
+        return M1_OK;
+    }
+    CKS(dalloc(ctx, &ctx->S, ctx->N));
+    CKS(dalloc(ctx, &ctx->S32, ctx->N));
+    CKS(copy_in(ctx, ctx->S, S, sizeof(double) * ctx->N, mem));
+    ctx->dirty = true;
+    return sync(ctx);
+}
+
+m1_status m1_explicit_step(m1_ctx* ctx, double dt) {
+    if (!ctx) return M1_ERR_ARG;
+    if (!(dt > 0.0)) return fail(ctx, M1_ERR_ARG, "dt must be positive");
+    CKS(prepare(ctx));
+    if (!ctx->expl_ok) {
+        CKS(dalloc(ctx, &ctx->Fstar, (size_t)ctx->dim * ctx->N));
+        CKS(dalloc(ctx, &ctx->linework, (size_t)3 * ctx->N));
+        ctx->expl_ok = true;
+    }
+    Dev<double> g = dev64(ctx, dt);
+    launch_explicit_hyp(g, ctx->Unew, ctx->Fstar, ctx->s);
+    count(ctx, 1);
+    for (int b = 0; b < ctx->dim; ++b) {
+        launch_wb_lines(g, b, ctx->Fstar, ctx->Unew + (1 + b) * ctx->N, ctx->linework, ctx->s);
+        count(ctx, 1);
+    }
+    CK(cudaMemcpyAsync(ctx->Un, ctx->Unew, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s));
+    ctx->dirty = true;
+    ctx->st.explicit_steps++;
+    CKS(sync(ctx));
+    return prepare(ctx);
+}
+
+m1_status m1_residual(m1_ctx* ctx, double dt, const double* U, double* R, m1_mem mem) {
+    if (!ctx || !U || !R) return M1_ERR_ARG;
+    CKS(prepare(ctx));
+    CKS(ensure_work(ctx));
+    CKS(copy_in(ctx, ctx->U, U, sizeof(double) * ctx->n, mem));
+    double nrm;
+    CKS(residual_norm(ctx, dev64(ctx, dt), ctx->U, ctx->R, &nrm));
+    CKS(copy_out(ctx, R, ctx->R, sizeof(double) * ctx->n, mem));
+    return sync(ctx);
+}
+
+m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double* Jv, int precision, m1_mem mem) {
+    if (!ctx || !U || !v || !Jv) return M1_ERR_ARG;
+    CKS(prepare(ctx));
+    CKS(ensure_work(ctx));
+    CKS(copy_in(ctx, ctx->U, U, sizeof(double) * ctx->n, mem));
+    CKS(copy_in(ctx, ctx->z, v, sizeof(double) * ctx->n, mem));
+    if (precision == M1_PREC_MIXED) {
+        CKS(ensure_work32(ctx));
+        launch_f64_to_f32(ctx->U, ctx->U32, ctx->n, ctx->s);
+        launch_f64_to_f32(ctx->z, ctx->z32, ctx->n, ctx->s);
+        launch_jv_f32(dev32(ctx, dt), ctx->U32, ctx->z32, ctx->w32, ctx->s);
+        launch_f32_to_f64(ctx->w32, ctx->w, ctx->n, ctx->s);
+        count(ctx, 4);
+    } else {
+        launch_jv_f64(dev64(ctx, dt), ctx->U, ctx->z, ctx->w, ctx->s);
+        count(ctx, 1);
+    }
+    ctx->st.jv_calls++;
+    CKS(copy_out(ctx, Jv, ctx->w, sizeof(double) * ctx->n, mem));
+    return sync(ctx);
+}
+
+m1_status m1_diag_blocks(m1_ctx* ctx, double dt, const double* U, double* blocks, m1_mem mem) {
+    if (!ctx || !U || !blocks) return M1_ERR_ARG;
+    CKS(prepare(ctx));
+    CKS(ensure_work(ctx));
+    CKS(copy_in(ctx, ctx->U, U, sizeof(double) * ctx->n, mem));
+    launch_diag_f64(dev64(ctx, dt), ctx->U, ctx->blocks, ctx->s);
+    count(ctx, 1);
+    CKS(copy_out(ctx, blocks, ctx->blocks, sizeof(double) * ctx->nu * ctx->nu * ctx->N, mem));
+    return sync(ctx);
+}
+
+static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const double* b, double* x,
+                              const m1_solver_opts* o, int* iters, int* refinements, double* bnorm, double* res,
+                              bool* conv) {
+    const bool pre = o->precond == M1_PRECOND_BJ;
+    if (o->restart < 1 || o->restart > kMaxRestart)
+        return fail(ctx, M1_ERR_ARG, "restart must be in [1, 30]");
+    Dev<double> g = dev64(ctx, dt);
+    if (pre) CKS(build_precond(ctx, g, Ud));
+    Ops64 ops{ctx, g, Ud, pre};
+    *refinements = 0;
+    if (o->precision == M1_PREC_MIXED) {
+        CKS(ensure_work32(ctx));
+        launch_f64_to_f32(Ud, ctx->U32, ctx->n, ctx->s);
+        count(ctx, 1);
+        Ops32 ops32{ctx, dev32(ctx, dt), ctx->U32, pre};
+        return gmres_mixed(ctx, ops, ops32, b, x, o->gmres_rtol, o->restart, o->gmres_max, o->refine_max, iters,
+                           refinements, bnorm, res, conv);
+    }
+    return gmres64(ctx, ops, b, x, o->gmres_rtol, o->restart, o->gmres_max, iters, bnorm, res, conv);
+}
+
+m1_status m1_gmres_solve(m1_ctx* ctx, double dt, const double* U, const double* b, double* x,
+                         const m1_solver_opts* opts, m1_solve_info* info, m1_mem mem) {
+    if (!ctx || !b || !x) return M1_ERR_ARG;
+    m1_solver_opts o;
+    m1_default_opts(&o);
+    if (opts) o = *opts;
+    CKS(prepare(ctx));
+    CKS(ensure_work(ctx));
+    if (U)
+        CKS(copy_in(ctx, ctx->U, U, sizeof(double) * ctx->n, mem));
+    else
+        CK(cudaMemcpyAsync(ctx->U, ctx->Un, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s));
+    CKS(copy_in(ctx, ctx->Rt, b, sizeof(double) * ctx->n, mem));
+    int it = 0, ref = 0;
+    double bn = 0, rs = 0;
+    bool conv = false;
+    CKS(linear_solve(ctx, dt, ctx->U, ctx->Rt, ctx->delta, &o, &it, &ref, &bn, &rs, &conv));
+    // true residual of the returned x in FP64
+    launch_jv_f64(dev64(ctx, dt), ctx->U, ctx->delta, ctx->w, ctx->s);
+    launch_axpby_f64(1.0, ctx->Rt, -1.0, ctx->w, ctx->rhs, ctx->n, ctx->s);
+    count(ctx, 2);
+    double tr;
+    CKS(norm_f64(ctx, ctx->rhs, &tr));
+    CKS(copy_out(ctx, x, ctx->delta, sizeof(double) * ctx->n, mem));
+    CKS(sync(ctx));
+    if (info) {
+        info->converged = conv;
+        info->iters = it;
+        info->res0 = bn;
+        info->res = tr;
+    }
+    return conv ? M1_OK : fail(ctx, M1_ERR_NOT_CONVERGED, "GMRES did not converge");
+}
+
+m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m1_step_info* info) {
+    if (!ctx) return M1_ERR_ARG;
+    if (!(dt > 0.0)) return fail(ctx, M1_ERR_ARG, "dt must be positive");
+    m1_solver_opts o;
+    m1_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.restart < 1 || o.restart > kMaxRestart) return fail(ctx, M1_ERR_ARG, "restart must be in [1, 30]");
+    CKS(prepare(ctx));
+    CKS(ensure_work(ctx));
+    m1_step_info inf{};
+    cudaStream_t s = ctx->s;
+    CK(cudaEventRecord(ctx->ev0, s));
+    const long long n = ctx->n;
+    Dev<double> g = dev64(ctx, dt);
+    CK(cudaMemcpyAsync(ctx->U, ctx->Un, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    double r0, rn;
+    CKS(residual_norm(ctx, g, ctx->U, ctx->R, &r0));
+    inf.res0 = r0;
+    if (!(r0 == r0) || isinf(r0)) {
+        if (info) *info = inf;
+        return fail(ctx, M1_ERR_NONFINITE, "non-finite initial residual");
+    }
+    rn = r0;
+    m1_status result = M1_OK;
+    while (rn > o.newton_rtol * r0 && inf.newton_iters < o.newton_max) {
+        // delta solves J delta = -R
+        launch_axpby_f64(-1.0, ctx->R, 0.0, ctx->R, ctx->Rt, n, s);
+        count(ctx, 1);
+        int it = 0, ref = 0;
+        double bn, rs;
+        bool conv;
+        m1_status ls = linear_solve(ctx, dt, ctx->U, ctx->Rt, ctx->delta, &o, &it, &ref, &bn, &rs, &conv);
+        inf.gmres_iters += it;
+        inf.refinements += ref;
+        if (ls != M1_OK) {
+            result = ls;
+            break;
+        }
+        double theta = 1.0, rt = 0.0;
+        for (int ls_it = 0; ls_it < 7; ++ls_it) {
+            launch_axpby_f64(theta, ctx->delta, 1.0, ctx->U, ctx->Ut, n, s);
+            count(ctx, 1);
+            CKS(residual_norm(ctx, g, ctx->Ut, ctx->Rt, &rt));
+            if (!o.line_search || rt <= (1.0 - 1e-4 * theta) * rn) break;
+            theta *= 0.5;
+        }
+        std::swap(ctx->U, ctx->Ut);
+        std::swap(ctx->R, ctx->Rt);
+        rn = rt;
+        inf.newton_iters++;
+        ctx->st.newton_iters++;
+        if (!(rn == rn) || isinf(rn)) {
+            result = fail(ctx, M1_ERR_NONFINITE, "non-finite residual in Newton");
+            break;
+        }
+    }
+    inf.res = rn;
+    inf.converged = (result == M1_OK) && rn <= o.newton_rtol * r0;
+    CK(cudaMemsetAsync(ctx->viol, 0, sizeof(unsigned long long), s));
+    launch_realizability(ctx->U, ctx->dim, ctx->N, ctx->d.c, ctx->viol, s);
+    count(ctx, 1);
+    CK(cudaMemcpyAsync(ctx->Unew, ctx->U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (inf.converged && o.advance) {
+        CK(cudaMemcpyAsync(ctx->Un, ctx->U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        ctx->dirty = true;
+    }
+    CK(cudaEventRecord(ctx->ev1, s));
+    unsigned long long hv = 0;
+    CK(cudaMemcpyAsync(ctx->hpin, ctx->viol, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CKS(sync(ctx));
+    memcpy(&hv, ctx->hpin, sizeof(hv));
+    inf.realizability_violations = (long long)hv;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    inf.time_ms = ms;
+    ctx->st.implicit_steps++;
+    if (info) *info = inf;
+    if (ctx->dirty) CKS(prepare(ctx));
+    if (result != M1_OK) return result;
+    if (!inf.converged) return fail(ctx, M1_ERR_NOT_CONVERGED, "Newton did not converge");
+    return M1_OK;
+}
+
+m1_status m1_stats(const m1_ctx* ctx, m1_stats_t* out) {
+    if (!ctx || !out) return M1_ERR_ARG;
+    *out = ctx->st;
+    return M1_OK;
+}
+
+const char* m1_last_error(const m1_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// m1_internal.h — host-side launch interface between the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "m1_device.cuh"
+
+namespace m1 {
+
+constexpr int kMaxRestart = 30;  // GMRES(m) basis bound, m <= 30
+
+// ----------------------------------------------------------------- stencils (m1_stencil.cu)
+// time-n face data: lambda+-, alpha on every face of every axis (FP64)
+void launch_faces_time_n(const Dev<double>& g, double* const lam_p[3], double* const lam_m[3],
+                         double* const alpha[3], cudaStream_t s);
+// R(U); optional FP64 partial sums of R^2 per block into partials (nblocks entries)
+void launch_residual_f64(const Dev<double>& g, const double* U, double* R, double* partials, int nblocks,
+                         cudaStream_t s);
+void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s);
+void launch_jv_f32(const Dev<float>& g, const float* U, const float* v, float* Jv, cudaStream_t s);
+void launch_diag_f64(const Dev<double>& g, const double* U, double* blocks, cudaStream_t s);
+void launch_block_inverse(int nu, long long N, const double* blocks, double* binv64, float* binv32,
+                          int* singular, cudaStream_t s);
+void launch_bj_apply_f64(int nu, long long N, const double* binv, const double* r, double* z, cudaStream_t s);
+void launch_bj_apply_f32(int nu, long long N, const float* binv, const float* r, float* z, cudaStream_t s);
+// semi-implicit step: hyperbolic update + exchange -> Unew (E, T) and Fstar
+void launch_explicit_hyp(const Dev<double>& g, double* Unew, double* Fstar, cudaStream_t s);
+// WB source solve along axis b for component b: (I + c dt W_b) F = Fstar
+void launch_wb_lines(const Dev<double>& g, int b, const double* Fstar, double* Fout, double* work,
+                     cudaStream_t s);
+int stencil_blocks(long long N);
+
+// ----------------------------------------------------------------- vectors (m1_vec.cu)
+int reduce_blocks();
+// partial sums of squares of x (FP64) and the final sum into out[0]
+void launch_norm2_f64(const double* x, long long n, double* partials, double* out, cudaStream_t s);
+void launch_norm2_f32(const float* x, long long n, double* partials, double* out, cudaStream_t s);
+void launch_finish_sum(const double* partials, int nparts, int ncols, double* out, cudaStream_t s);
+// h[i] = V_i . w for i <= j (V rows of length n with stride ld), accumulated in FP64
+void launch_multidot_f64(const double* V, long long ld, int j, const double* w, long long n, double* partials,
+                         double* h, cudaStream_t s);
+void launch_multidot_f32(const float* V, long long ld, int j, const float* w, long long n, double* partials,
+                         double* h, cudaStream_t s);
+// w -= sum_{i<=j} h[i] V_i ; if partials != null also the FP64 sum of squares of the new w
+void launch_cgs_update_f64(const double* V, long long ld, int j, const double* h, double* w, long long n,
+                           double* partials, cudaStream_t s);
+void launch_cgs_update_f32(const float* V, long long ld, int j, const double* h, float* w, long long n,
+                           double* partials, cudaStream_t s);
+// y = x * (1 / sqrt(*nrm2)), zero when the norm is zero
+void launch_scale_inv_sqrt_f64(const double* x, const double* nrm2, double* y, long long n, cudaStream_t s);
+void launch_scale_inv_sqrt_f32(const float* x, const double* nrm2, float* y, long long n, cudaStream_t s);
+// x += sum_{i<k} y[i] Z_i
+void launch_lincomb_add_f64(const double* Z, long long ld, int k, const double* y, double* x, long long n,
+                            cudaStream_t s);
+void launch_lincomb_add_f32_to_f64(const float* Z, long long ld, int k, const double* y, double* x, long long n,
+                                   cudaStream_t s);
+void launch_axpy_f64(double a, const double* x, double* y, long long n, cudaStream_t s);  // y += a x
+void launch_axpby_f64(double a, const double* x, double b, const double* y, double* out, long long n,
+                      cudaStream_t s);  // out = a x + b y
+void launch_f64_to_f32(const double* x, float* y, long long n, cudaStream_t s);
+void launch_f32_to_f64(const float* x, double* y, long long n, cudaStream_t s);
+void launch_scale_f64_to_f32(const double* x, const double* nrm2, float* y, long long n, cudaStream_t s);
+// Givens update of Hessenberg column j (device scalars), resid[0] = |g_{j+1}|
+// (hcol = h1 + h2 of the two Gram-Schmidt passes, h2 may be null)
+void launch_givens(double* H, double* cs, double* sn, double* g, const double* h1, const double* h2,
+                   const double* hnorm2, int j, double* resid, cudaStream_t s);
+// back substitution y = H^-1 g on the rotated k x k triangle
+void launch_backsolve(const double* H, const double* g, int k, double* y, cudaStream_t s);
+// count cells with |F| > c E and non-finite entries
+void launch_realizability(const double* U, int dim, long long N, double c, unsigned long long* count,
+                          cudaStream_t s);
+
+}  // namespace m1

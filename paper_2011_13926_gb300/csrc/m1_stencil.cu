@@ -1,0 +1,580 @@
+// m1_stencil.cu — stencil kernels of the grey M1 step (residual, J v, point
+// blocks, time-n face data, block Jacobi, semi-implicit step).
+//
+// One thread per cell (or face, or grid line). All loads of a field are
+// coalesced along x; neighbours along y/z are the same field offset by a row
+// or plane, so a warp's loads stay contiguous.
+#include <stdio.h>
+
+#include "m1_internal.h"
+
+namespace m1 {
+
+static constexpr int kThreads = 256;
+
+int stencil_blocks(long long N) { return (int)((N + kThreads - 1) / kThreads); }
+
+// ------------------------------------------------------------------ time-n faces
+// lambda+-(U^n) and alpha (Eq. asymptoticCorrection with f_{i+1/2} = (f_i + f_{i+1})/2
+// and sigma_{i+1/2} = (sigma_i + sigma_{i+1})/2) on the faces of axis a.
+template <int DIM>
+__global__ void k_faces_time_n(Dev<double> g, int a, double* lam_p, double* lam_m, double* alpha) {
+    const long long nfaces = g.N / g.n[a] * (g.n[a] + 1);
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfaces) return;
+    int fn[3] = {g.n[0], g.n[1], g.n[2]};
+    fn[a] += 1;
+    int coord[3];
+    cell_coord(f, fn[0], fn[1], coord);
+    const int fa = coord[a];
+    LoadPlain<double> ld{g.Un, g.N};
+    // the cell on the right of the face unless the face is the high boundary
+    int cc[3] = {coord[0], coord[1], coord[2]};
+    const bool high = (fa == g.n[a]);
+    cc[a] = high ? g.n[a] - 1 : fa;
+    const long long idx = ((long long)cc[2] * g.n[1] + cc[1]) * g.n[0] + cc[0];
+    St<double, DIM> self = load_state<double, DIM, false>(ld, idx, idx);
+    double sig_nb;
+    bool bnd;
+    St<double, DIM> nb;
+    if (high) {
+        nb = neighbour<double, DIM, false>(g, ld, self, idx, cc, a, 1, sig_nb, bnd);
+    } else if (fa == 0) {
+        nb = neighbour<double, DIM, false>(g, ld, self, idx, cc, a, 0, sig_nb, bnd);
+    } else {
+        const long long j = idx - g.stride[a];
+        nb = load_state<double, DIM, false>(ld, j, idx);
+        sig_nb = g.sig_f[j];
+    }
+    const St<double, DIM>& uL = high ? self : nb;
+    const St<double, DIM>& uR = high ? nb : self;
+    const Cl<double, DIM> kL = closure(uL, g.c), kR = closure(uR, g.c);
+    double lp, lm;
+    if (g.fixed_eigs) {
+        lp = g.c;
+        lm = -g.c;
+    } else {
+        double xL, nL, xR, nR;
+        eigen(kL, a, g.c, xL, nL);
+        eigen(kR, a, g.c, xR, nR);
+        wave_speeds(xL, nL, xR, nR, g.lambda_floor, lp, lm);
+    }
+    lam_p[f] = lp;
+    lam_m[f] = lm;
+    double al = 1.0;
+    if (g.ap) {
+        const double fbar = 0.5 * (sqrt(kL.f2) + sqrt(kR.f2));
+        const double sig = 0.5 * (g.sig_f[idx] + sig_nb);
+        const double den = lp - lm;
+        const double term = den >= Tiny<double>::den() ? lp * lm / (g.c * den) : 0.0;
+        al = 1.0 / (1.0 - 3.0 * sig * g.dx[a] * (1.0 - fbar * fbar) * term);
+    }
+    alpha[f] = al;
+}
+
+void launch_faces_time_n(const Dev<double>& g, double* const lam_p[3], double* const lam_m[3],
+                         double* const alpha[3], cudaStream_t s) {
+    for (int a = 0; a < g.dim; ++a) {
+        const long long nf = g.N / g.n[a] * (g.n[a] + 1);
+        const int nb = (int)((nf + kThreads - 1) / kThreads);
+        switch (g.dim) {
+            case 1: k_faces_time_n<1><<<nb, kThreads, 0, s>>>(g, a, lam_p[a], lam_m[a], alpha[a]); break;
+            case 2: k_faces_time_n<2><<<nb, kThreads, 0, s>>>(g, a, lam_p[a], lam_m[a], alpha[a]); break;
+            default: k_faces_time_n<3><<<nb, kThreads, 0, s>>>(g, a, lam_p[a], lam_m[a], alpha[a]); break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ block reduction helper
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+// ------------------------------------------------------------------ residual
+template <int DIM, bool GAS>
+__global__ void __launch_bounds__(kThreads) k_residual(Dev<double> g, const double* __restrict__ U,
+                                                       double* __restrict__ Rout, double* partials) {
+    constexpr int NU = 1 + DIM + (GAS ? 1 : 0);
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double ss = 0.0;
+    if (idx < g.N) {
+        int coord[3];
+        cell_coord(idx, g.n[0], g.n[1], coord);
+        LoadPlain<double> ld{U, g.N};
+        double out[NU];
+        cell_residual<double, DIM, GAS>(g, ld, idx, coord, out);
+#pragma unroll
+        for (int k = 0; k < NU; ++k) {
+            Rout[k * g.N + idx] = out[k];
+            ss += out[k] * out[k];
+        }
+    }
+    if (partials) {
+        const double t = block_sum(ss);
+        if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    }
+}
+
+// ------------------------------------------------------------------ J v
+template <class R, int DIM, bool GAS>
+__global__ void __launch_bounds__(kThreads) k_jv(Dev<R> g, const R* __restrict__ U, const R* __restrict__ v,
+                                                 R* __restrict__ Jv) {
+    constexpr int NU = 1 + DIM + (GAS ? 1 : 0);
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    int coord[3];
+    cell_coord(idx, g.n[0], g.n[1], coord);
+    LoadDir<R> ld{U, v, g.N};
+    Dual<R> out[NU];
+    cell_residual<Dual<R>, DIM, GAS>(g, ld, idx, coord, out);
+#pragma unroll
+    for (int k = 0; k < NU; ++k) Jv[k * g.N + idx] = out[k].d;
+}
+
+// ------------------------------------------------------------------ point blocks
+template <int DIM, bool GAS>
+__global__ void __launch_bounds__(kThreads) k_diag(Dev<double> g, const double* __restrict__ U,
+                                                   double* __restrict__ blocks) {
+    constexpr int NU = 1 + DIM + (GAS ? 1 : 0);
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    int coord[3];
+    cell_coord(idx, g.n[0], g.n[1], coord);
+    for (int k = 0; k < NU; ++k) {
+        LoadSeed<double> ld{U, g.N, k};
+        Dual<double> out[NU];
+        cell_residual<Dual<double>, DIM, GAS>(g, ld, idx, coord, out);
+#pragma unroll
+        for (int r = 0; r < NU; ++r) blocks[(long long)(r * NU + k) * g.N + idx] = out[r].d;
+    }
+}
+
+#define M1_DISPATCH(DIMV, GASV, CALL) \
+    do {                              \
+        if ((DIMV) == 1) {            \
+            if (GASV) {               \
+                CALL(1, true);        \
+            } else {                  \
+                CALL(1, false);       \
+            }                         \
+        } else if ((DIMV) == 2) {     \
+            if (GASV) {               \
+                CALL(2, true);        \
+            } else {                  \
+                CALL(2, false);       \
+            }                         \
+        } else {                      \
+            if (GASV) {               \
+                CALL(3, true);        \
+            } else {                  \
+                CALL(3, false);       \
+            }                         \
+        }                             \
+    } while (0)
+
+void launch_residual_f64(const Dev<double>& g, const double* U, double* R, double* partials, int nblocks,
+                         cudaStream_t s) {
+    const int nb = stencil_blocks(g.N);
+    (void)nblocks;
+#define CALL(D, G) k_residual<D, G><<<nb, kThreads, 0, s>>>(g, U, R, partials)
+    M1_DISPATCH(g.dim, g.gas, CALL);
+#undef CALL
+}
+
+void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s) {
+    const int nb = stencil_blocks(g.N);
+#define CALL(D, G) k_jv<double, D, G><<<nb, kThreads, 0, s>>>(g, U, v, Jv)
+    M1_DISPATCH(g.dim, g.gas, CALL);
+#undef CALL
+}
+
+void launch_jv_f32(const Dev<float>& g, const float* U, const float* v, float* Jv, cudaStream_t s) {
+    const int nb = stencil_blocks(g.N);
+#define CALL(D, G) k_jv<float, D, G><<<nb, kThreads, 0, s>>>(g, U, v, Jv)
+    M1_DISPATCH(g.dim, g.gas, CALL);
+#undef CALL
+}
+
+void launch_diag_f64(const Dev<double>& g, const double* U, double* blocks, cudaStream_t s) {
+    const int nb = stencil_blocks(g.N);
+#define CALL(D, G) k_diag<D, G><<<nb, kThreads, 0, s>>>(g, U, blocks)
+    M1_DISPATCH(g.dim, g.gas, CALL);
+#undef CALL
+}
+
+// ------------------------------------------------------------------ block inverse / apply
+// Gauss-Jordan with partial pivoting on each cell's NU x NU block (FP64).
+template <int NU>
+__global__ void k_block_inverse(long long N, const double* __restrict__ blocks, double* __restrict__ binv64,
+                                float* __restrict__ binv32, int* singular) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double a[NU][NU], x[NU][NU];
+#pragma unroll
+    for (int r = 0; r < NU; ++r)
+#pragma unroll
+        for (int c = 0; c < NU; ++c) {
+            a[r][c] = blocks[(long long)(r * NU + c) * N + i];
+            x[r][c] = (r == c) ? 1.0 : 0.0;
+        }
+    bool bad = false;
+#pragma unroll
+    for (int col = 0; col < NU; ++col) {
+        int piv = col;
+        double best = fabs(a[col][col]);
+#pragma unroll
+        for (int r = col + 1; r < NU; ++r)
+            if (fabs(a[r][col]) > best) {
+                best = fabs(a[r][col]);
+                piv = r;
+            }
+        if (!(best > 0.0)) bad = true;
+        // swap rows col and piv (predicated, registers only)
+#pragma unroll
+        for (int r = col + 1; r < NU; ++r) {
+            if (r == piv) {
+#pragma unroll
+                for (int c = 0; c < NU; ++c) {
+                    double t = a[col][c];
+                    a[col][c] = a[r][c];
+                    a[r][c] = t;
+                    t = x[col][c];
+                    x[col][c] = x[r][c];
+                    x[r][c] = t;
+                }
+            }
+        }
+        const double inv = bad ? 0.0 : 1.0 / a[col][col];
+#pragma unroll
+        for (int c = 0; c < NU; ++c) {
+            a[col][c] *= inv;
+            x[col][c] *= inv;
+        }
+#pragma unroll
+        for (int r = 0; r < NU; ++r) {
+            if (r == col) continue;
+            const double m = a[r][col];
+#pragma unroll
+            for (int c = 0; c < NU; ++c) {
+                a[r][c] -= m * a[col][c];
+                x[r][c] -= m * x[col][c];
+            }
+        }
+    }
+    if (bad) {
+        atomicAdd(singular, 1);
+#pragma unroll
+        for (int r = 0; r < NU; ++r)
+#pragma unroll
+            for (int c = 0; c < NU; ++c) x[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < NU; ++r)
+#pragma unroll
+        for (int c = 0; c < NU; ++c) {
+            binv64[(long long)(r * NU + c) * N + i] = x[r][c];
+            if (binv32) binv32[(long long)(r * NU + c) * N + i] = (float)x[r][c];
+        }
+}
+
+void launch_block_inverse(int nu, long long N, const double* blocks, double* binv64, float* binv32, int* singular,
+                          cudaStream_t s) {
+    const int nb = stencil_blocks(N);
+    switch (nu) {
+        case 2: k_block_inverse<2><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
+        case 3: k_block_inverse<3><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
+        case 4: k_block_inverse<4><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
+        default: k_block_inverse<5><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
+    }
+}
+
+template <class R, int NU>
+__global__ void k_bj_apply(long long N, const R* __restrict__ binv, const R* __restrict__ r, R* __restrict__ z) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    R rr[NU];
+#pragma unroll
+    for (int c = 0; c < NU; ++c) rr[c] = r[(long long)c * N + i];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) {
+        R acc = R(0);
+#pragma unroll
+        for (int c = 0; c < NU; ++c) acc += binv[(long long)(q * NU + c) * N + i] * rr[c];
+        z[(long long)q * N + i] = acc;
+    }
+}
+
+template <class R>
+static void bj_apply(int nu, long long N, const R* binv, const R* r, R* z, cudaStream_t s) {
+    const int nb = stencil_blocks(N);
+    switch (nu) {
+        case 2: k_bj_apply<R, 2><<<nb, kThreads, 0, s>>>(N, binv, r, z); break;
+        case 3: k_bj_apply<R, 3><<<nb, kThreads, 0, s>>>(N, binv, r, z); break;
+        case 4: k_bj_apply<R, 4><<<nb, kThreads, 0, s>>>(N, binv, r, z); break;
+        default: k_bj_apply<R, 5><<<nb, kThreads, 0, s>>>(N, binv, r, z); break;
+    }
+}
+void launch_bj_apply_f64(int nu, long long N, const double* binv, const double* r, double* z, cudaStream_t s) {
+    bj_apply<double>(nu, N, binv, r, z, s);
+}
+void launch_bj_apply_f32(int nu, long long N, const float* binv, const float* r, float* z, cudaStream_t s) {
+    bj_apply<float>(nu, N, binv, r, z, s);
+}
+
+// ------------------------------------------------------------------ semi-implicit step
+// Hyperbolic update at time n (alpha and lambda at n) and the backward-Euler
+// energy exchange: writes E^{n+1} (and T^{n+1}) into Unew and F* into Fstar.
+template <int DIM, bool GAS>
+__global__ void __launch_bounds__(kThreads) k_explicit_hyp(Dev<double> g, double* __restrict__ Unew,
+                                                           double* __restrict__ Fstar) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    int coord[3];
+    cell_coord(idx, g.n[0], g.n[1], coord);
+    LoadPlain<double> ld{g.Un, g.N};
+    const St<double, DIM> self = load_state<double, DIM, GAS>(ld, idx, idx);
+    const Cl<double, DIM> ks = closure(self, g.c);
+    double divE = 0.0, divF[DIM];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) divF[b] = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            double sig_nb;
+            bool boundary;
+            const St<double, DIM> nb = neighbour<double, DIM, GAS>(g, ld, self, idx, coord, a, side, sig_nb, boundary);
+            const Cl<double, DIM> kn = closure(nb, g.c);
+            const long long fidx = face_index(g.n, coord, a, coord[a] + side);
+            double Fs, Ps[DIM];
+            if (side)
+                hll(self, nb, ks, kn, g.lam_p[a][fidx], g.lam_m[a][fidx], a, g.c, Fs, Ps);
+            else
+                hll(nb, self, kn, ks, g.lam_p[a][fidx], g.lam_m[a][fidx], a, g.c, Fs, Ps);
+            const double w = (side ? 1.0 : -1.0) * g.inv_dx[a];
+            divE += w * g.alpha[a][fidx] * Fs;
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) divF[b] += w * Ps[b];
+        }
+    }
+    double Es = self.E - g.dt * divE;
+    if (g.S) Es += g.dt * g.S[idx];
+    const double k = g.c * g.sig_a[idx] * g.dt;
+    if constexpr (GAS) {
+        // rho c_v (T - T^n) + k/(1+k) (a_r T^4 - E*) = 0: Newton from the upper bound
+        const double w = k / (1.0 + k), rc = g.rho_cv[idx], Tn = self.T;
+        double T = fmax(Tn, sqrt(sqrt(fmax(Es, 0.0) / g.a_r)));
+        for (int it = 0; it < 100; ++it) {
+            const double T3 = T * T * T;
+            const double f = rc * (T - Tn) + w * (g.a_r * T3 * T - Es);
+            const double df = rc + 4.0 * w * g.a_r * T3;
+            const double st = f / df;
+            T -= st;
+            if (fabs(st) <= 1e-15 * fabs(T)) break;
+        }
+        const double T2 = T * T;
+        Unew[idx] = (Es + k * g.a_r * T2 * T2) / (1.0 + k);
+        Unew[(1 + DIM) * g.N + idx] = T;
+    } else {
+        Unew[idx] = (Es + k * (g.B ? g.B[idx] : 0.0)) / (1.0 + k);
+    }
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) Fstar[b * g.N + idx] = self.F[b] - g.dt * divF[b];
+}
+
+void launch_explicit_hyp(const Dev<double>& g, double* Unew, double* Fstar, cudaStream_t s) {
+    const int nb = stencil_blocks(g.N);
+#define CALL(D, G) k_explicit_hyp<D, G><<<nb, kThreads, 0, s>>>(g, Unew, Fstar)
+    M1_DISPATCH(g.dim, g.gas, CALL);
+#undef CALL
+}
+
+// One thread per grid line along axis b: solve (I + c dt W_b) F_b = F*_b, the
+// Appendix B tridiagonal form with r_{j+1/2} = c sigma_{j+1/2} dt / 4 (interior
+// faces), Eq. (boundaryCondition) at time n on non-periodic boundary faces (or
+// the plain face average with the ghost), Thomas' algorithm, and
+// Sherman-Morrison for the cyclic system of a periodic axis.
+template <int DIM>
+__global__ void k_wb_lines(Dev<double> g, int b, const double* __restrict__ Fstar, double* __restrict__ Fout,
+                           double* __restrict__ cp, double* __restrict__ dp, double* __restrict__ zp) {
+    const long long nlines = g.N / g.n[b];
+    const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nlines) return;
+    int ln[3] = {g.n[0], g.n[1], g.n[2]};
+    ln[b] = 1;
+    int coord[3];
+    cell_coord(line, ln[0], ln[1], coord);
+    coord[b] = 0;
+    const long long base = ((long long)coord[2] * g.n[1] + coord[1]) * g.n[0] + coord[0];
+    const long long st = g.stride[b];
+    const int n = g.n[b];
+    const double q = g.c * g.dt * 0.125;  // r_{j+1/2} = q (sigma_j + sigma_{j+1})
+    const double* sig = g.sig_f;
+    const double* rhs = Fstar + (long long)b * g.N;
+    const bool periodic = g.bc[b][0] == BC_PERIODIC;
+
+    if (!g.wb) {  // centred source, Eq. (wb_naive): diagonal
+        for (int j = 0; j < n; ++j) {
+            const long long i = base + j * st;
+            Fout[i] = rhs[i] / (1.0 + g.c * g.dt * sig[i]);
+        }
+        return;
+    }
+    if (periodic && n <= 2) {
+        if (n == 1) {
+            Fout[base] = rhs[base] / (1.0 + 4.0 * 2.0 * q * sig[base]);
+            return;
+        }
+        const long long i0 = base, i1 = base + st;
+        const double r = 2.0 * q * (sig[i0] + sig[i1]);  // two faces, both between cells 0 and 1
+        const double d = 1.0 + r, o = r;
+        const double det = d * d - o * o;
+        Fout[i0] = (d * rhs[i0] - o * rhs[i1]) / det;
+        Fout[i1] = (d * rhs[i1] - o * rhs[i0]) / det;
+        return;
+    }
+    // boundary contributions (non-periodic)
+    double diag0 = 0.0, diagN = 0.0, rhs0 = 0.0, rhsN = 0.0;
+    if (!periodic) {
+        LoadPlain<double> ld{g.Un, g.N};
+        for (int side = 0; side < 2; ++side) {
+            int cc[3] = {coord[0], coord[1], coord[2]};
+            cc[b] = side ? n - 1 : 0;
+            const long long ie = base + (long long)cc[b] * st;
+            double ddiag = 0.0, drhs = 0.0;
+            const int kind = g.bc[b][side];
+            if (g.wb_boundary) {
+                const St<double, DIM> self = load_state<double, DIM, false>(ld, ie, ie);
+                double sig_nb;
+                bool bnd;
+                const St<double, DIM> gh = neighbour<double, DIM, false>(g, ld, self, ie, cc, b, side, sig_nb, bnd);
+                const double Pi = pressure(closure(self, g.c), b, b), Pg = pressure(closure(gh, g.c), b, b);
+                const double phi = side ? -g.c * (Pg - Pi) * g.inv_dx[b] : -g.c * (Pi - Pg) * g.inv_dx[b];
+                drhs = -0.5 * g.c * g.dt * phi;
+            } else {
+                const double r = 2.0 * q * sig[ie];
+                if (kind == BC_OUTFLOW) {
+                    ddiag = 2.0 * r;
+                } else if (kind == BC_DIRICHLET) {
+                    const long long m = bface_cell(g.n, cc, b);
+                    const unsigned char* mk = g.bmask[b][side];
+                    if (mk == nullptr || mk[m]) {
+                        ddiag = r;
+                        drhs = -r * g.bF[b][side][(long long)b * g.bM[b] + m];
+                    } else {
+                        ddiag = 2.0 * r;
+                    }
+                }  // reflect: the face average vanishes
+            }
+            if (side) {
+                diagN = ddiag;
+                rhsN = drhs;
+            } else {
+                diag0 = ddiag;
+                rhs0 = drhs;
+            }
+        }
+    }
+    // coefficients of row j: lower a_j = r_{j-1/2}, upper c_j = r_{j+1/2}, diag 1 + a_j + c_j (+ boundary)
+    auto rface = [&](int j) -> double {  // r between cell j and j+1 (j+1 wrapped)
+        const int jp = (j + 1 == n) ? 0 : j + 1;
+        return q * (sig[base + (long long)j * st] + sig[base + (long long)jp * st]);
+    };
+    const double rwrap = periodic ? rface(n - 1) : 0.0;
+    // Sherman-Morrison pieces (periodic): A = T + u v^T with gamma = -b_0
+    double gamma = 0.0;
+    double prev_c = 0.0, prev_d = 0.0, prev_z = 0.0;
+    double rlo = periodic ? rwrap : 0.0;  // r_{-1/2}
+    for (int j = 0; j < n; ++j) {
+        const long long i = base + (long long)j * st;
+        const double rhi = (j < n - 1) ? rface(j) : (periodic ? rwrap : 0.0);
+        double bj = 1.0 + rlo + rhi;
+        double dj = rhs[i];
+        if (!periodic) {
+            if (j == 0) {
+                bj += diag0;
+                dj += rhs0;
+            }
+            if (j == n - 1) {
+                bj += diagN;
+                dj += rhsN;
+            }
+        }
+        double aj = (j > 0) ? rlo : 0.0;
+        double cj = (j < n - 1) ? rhi : 0.0;
+        double uj = 0.0;
+        if (periodic) {
+            if (j == 0) {
+                gamma = -bj;
+                bj -= gamma;
+                uj = gamma;
+            }
+            if (j == n - 1) {
+                bj -= rwrap * rwrap / gamma;
+                uj = rwrap;
+            }
+        }
+        const double m = (j == 0) ? bj : bj - aj * prev_c;
+        const double cpj = cj / m;
+        const double dpj = (dj - aj * prev_d) / m;
+        const double zpj = (uj - aj * prev_z) / m;
+        cp[i] = cpj;
+        dp[i] = dpj;
+        if (periodic) zp[i] = zpj;
+        prev_c = cpj;
+        prev_d = dpj;
+        prev_z = zpj;
+        rlo = rhi;
+    }
+    // back substitution (y in dp, z in zp)
+    double ny = dp[base + (long long)(n - 1) * st], nz = periodic ? zp[base + (long long)(n - 1) * st] : 0.0;
+    Fout[base + (long long)(n - 1) * st] = ny;
+    if (periodic) zp[base + (long long)(n - 1) * st] = nz;
+    for (int j = n - 2; j >= 0; --j) {
+        const long long i = base + (long long)j * st;
+        ny = dp[i] - cp[i] * ny;
+        Fout[i] = ny;
+        if (periodic) {
+            nz = zp[i] - cp[i] * nz;
+            zp[i] = nz;
+        }
+    }
+    if (periodic) {
+        // x = y - (v.y)/(1 + v.z) z with v = (1, 0, ..., 0, rwrap / gamma)
+        const long long i0 = base, iN = base + (long long)(n - 1) * st;
+        const double vy = Fout[i0] + rwrap / gamma * Fout[iN];
+        const double vz = zp[i0] + rwrap / gamma * zp[iN];
+        const double fac = vy / (1.0 + vz);
+        for (int j = 0; j < n; ++j) {
+            const long long i = base + (long long)j * st;
+            Fout[i] -= fac * zp[i];
+        }
+    }
+}
+
+void launch_wb_lines(const Dev<double>& g, int b, const double* Fstar, double* Fout, double* work, cudaStream_t s) {
+    const long long nlines = g.N / g.n[b];
+    const int nb = (int)((nlines + 127) / 128);
+    double* cp = work;
+    double* dp = work + g.N;
+    double* zp = work + 2 * g.N;
+    switch (g.dim) {
+        case 1: k_wb_lines<1><<<nb, 128, 0, s>>>(g, b, Fstar, Fout, cp, dp, zp); break;
+        case 2: k_wb_lines<2><<<nb, 128, 0, s>>>(g, b, Fstar, Fout, cp, dp, zp); break;
+        default: k_wb_lines<3><<<nb, 128, 0, s>>>(g, b, Fstar, Fout, cp, dp, zp); break;
+    }
+}
+
+}  // namespace m1

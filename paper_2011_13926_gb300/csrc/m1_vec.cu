@@ -1,0 +1,295 @@
+// m1_vec.cu — Krylov vector kernels: norms, fused multi-dot products and
+// Gram-Schmidt updates (warp shuffles + block reductions, FP64 accumulation in
+// a fixed order so that results are reproducible run to run), the Givens
+// update of the Hessenberg matrix and the least-squares back substitution.
+#include "m1_internal.h"
+
+namespace m1 {
+
+static constexpr int kRedThreads = 256;
+static constexpr int kRedBlocks = 608;  // 4 x 152 SMs; fixed so sums are deterministic
+static constexpr int kMaxCols = kMaxRestart + 1;
+
+int reduce_blocks() { return kRedBlocks; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum of partials[b * ncols + c] over b for each column c (one block, fixed order)
+__global__ void k_finish_sum(const double* __restrict__ partials, int nparts, int ncols, double* __restrict__ out) {
+    __shared__ double red[kRedThreads / 32];
+    for (int c = 0; c < ncols; ++c) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < nparts; b += blockDim.x) t += partials[(long long)b * ncols + c];
+        t = warp_sum(t);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double u = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+            u = warp_sum(u);
+            if (threadIdx.x == 0) out[c] = u;
+        }
+        __syncthreads();
+    }
+}
+
+void launch_finish_sum(const double* partials, int nparts, int ncols, double* out, cudaStream_t s) {
+    k_finish_sum<<<1, kRedThreads, 0, s>>>(partials, nparts, ncols, out);
+}
+
+template <class T>
+__global__ void k_norm2(const T* __restrict__ x, long long n, double* __restrict__ partials) {
+    __shared__ double red[kRedThreads / 32];
+    double t = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = (double)x[i];
+        t += v * v;
+    }
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double u = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        u = warp_sum(u);
+        if (threadIdx.x == 0) partials[blockIdx.x] = u;
+    }
+}
+
+void launch_norm2_f64(const double* x, long long n, double* partials, double* out, cudaStream_t s) {
+    k_norm2<double><<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partials);
+    launch_finish_sum(partials, kRedBlocks, 1, out, s);
+}
+void launch_norm2_f32(const float* x, long long n, double* partials, double* out, cudaStream_t s) {
+    k_norm2<float><<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partials);
+    launch_finish_sum(partials, kRedBlocks, 1, out, s);
+}
+
+// h_i = V_i . w for i = 0..j in one pass over w: each thread keeps j+1 FP64
+// accumulators; products of FP32 inputs are exact in FP64.
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const T* __restrict__ V, long long ld, int j,
+                                                          const T* __restrict__ w, long long n,
+                                                          double* __restrict__ partials) {
+    __shared__ double red[kRedThreads / 32][kMaxCols];
+    double acc[kMaxCols];
+#pragma unroll
+    for (int i = 0; i < kMaxCols; ++i) acc[i] = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const double we = (double)w[e];
+#pragma unroll
+        for (int i = 0; i < kMaxCols; ++i)
+            if (i <= j) acc[i] += (double)V[i * ld + e] * we;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kMaxCols; ++i) {
+        if (i <= j) {
+            const double t = warp_sum(acc[i]);
+            if (lane == 0) red[wid][i] = t;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][i];
+        partials[(long long)blockIdx.x * (j + 1) + i] = t;
+    }
+}
+
+void launch_multidot_f64(const double* V, long long ld, int j, const double* w, long long n, double* partials,
+                         double* h, cudaStream_t s) {
+    k_multidot<double><<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j, w, n, partials);
+    launch_finish_sum(partials, kRedBlocks, j + 1, h, s);
+}
+void launch_multidot_f32(const float* V, long long ld, int j, const float* w, long long n, double* partials,
+                         double* h, cudaStream_t s) {
+    k_multidot<float><<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j, w, n, partials);
+    launch_finish_sum(partials, kRedBlocks, j + 1, h, s);
+}
+
+// w -= sum_{i<=j} h_i V_i, optionally with the sum of squares of the new w
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_cgs_update(const T* __restrict__ V, long long ld, int j,
+                                                            const double* __restrict__ h, T* __restrict__ w,
+                                                            long long n, double* __restrict__ partials) {
+    __shared__ double hs[kMaxCols];
+    __shared__ double red[kRedThreads / 32];
+    if (threadIdx.x < kMaxCols) hs[threadIdx.x] = threadIdx.x <= j ? h[threadIdx.x] : 0.0;
+    __syncthreads();
+    double t = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double x = (double)w[e];
+#pragma unroll
+        for (int i = 0; i < kMaxCols; ++i)
+            if (i <= j) x -= hs[i] * (double)V[i * ld + e];
+        const T xt = (T)x;
+        w[e] = xt;
+        t += (double)xt * (double)xt;
+    }
+    if (partials) {
+        t = warp_sum(t);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double u = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+            u = warp_sum(u);
+            if (threadIdx.x == 0) partials[blockIdx.x] = u;
+        }
+    }
+}
+
+void launch_cgs_update_f64(const double* V, long long ld, int j, const double* h, double* w, long long n,
+                           double* partials, cudaStream_t s) {
+    k_cgs_update<double><<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j, h, w, n, partials);
+}
+void launch_cgs_update_f32(const float* V, long long ld, int j, const double* h, float* w, long long n,
+                           double* partials, cudaStream_t s) {
+    k_cgs_update<float><<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j, h, w, n, partials);
+}
+
+template <class T>
+__global__ void k_scale_inv_sqrt(const T* __restrict__ x, const double* __restrict__ nrm2, T* __restrict__ y,
+                                 long long n) {
+    const double nn = nrm2[0];
+    const double s = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (T)((double)x[i] * s);
+}
+void launch_scale_inv_sqrt_f64(const double* x, const double* nrm2, double* y, long long n, cudaStream_t s) {
+    k_scale_inv_sqrt<double><<<kRedBlocks, kRedThreads, 0, s>>>(x, nrm2, y, n);
+}
+void launch_scale_inv_sqrt_f32(const float* x, const double* nrm2, float* y, long long n, cudaStream_t s) {
+    k_scale_inv_sqrt<float><<<kRedBlocks, kRedThreads, 0, s>>>(x, nrm2, y, n);
+}
+
+__global__ void k_scale_f64_to_f32(const double* __restrict__ x, const double* __restrict__ nrm2,
+                                   float* __restrict__ y, long long n) {
+    const double nn = nrm2[0];
+    const double s = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (float)(x[i] * s);
+}
+void launch_scale_f64_to_f32(const double* x, const double* nrm2, float* y, long long n, cudaStream_t s) {
+    k_scale_f64_to_f32<<<kRedBlocks, kRedThreads, 0, s>>>(x, nrm2, y, n);
+}
+
+template <class T>
+__global__ void k_lincomb_add(const T* __restrict__ Z, long long ld, int k, const double* __restrict__ y,
+                              double* __restrict__ x, long long n) {
+    __shared__ double ys[kMaxCols];
+    if (threadIdx.x < kMaxCols) ys[threadIdx.x] = threadIdx.x < k ? y[threadIdx.x] : 0.0;
+    __syncthreads();
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double acc = x[e];
+#pragma unroll
+        for (int i = 0; i < kMaxCols; ++i)
+            if (i < k) acc += ys[i] * (double)Z[i * ld + e];
+        x[e] = acc;
+    }
+}
+void launch_lincomb_add_f64(const double* Z, long long ld, int k, const double* y, double* x, long long n,
+                            cudaStream_t s) {
+    k_lincomb_add<double><<<kRedBlocks, kRedThreads, 0, s>>>(Z, ld, k, y, x, n);
+}
+void launch_lincomb_add_f32_to_f64(const float* Z, long long ld, int k, const double* y, double* x, long long n,
+                                   cudaStream_t s) {
+    k_lincomb_add<float><<<kRedBlocks, kRedThreads, 0, s>>>(Z, ld, k, y, x, n);
+}
+
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* __restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + b * y[i];
+}
+void launch_axpy_f64(double a, const double* x, double* y, long long n, cudaStream_t s) {
+    k_axpby<<<kRedBlocks, kRedThreads, 0, s>>>(a, x, 1.0, y, y, n);
+}
+void launch_axpby_f64(double a, const double* x, double b, const double* y, double* out, long long n,
+                      cudaStream_t s) {
+    k_axpby<<<kRedBlocks, kRedThreads, 0, s>>>(a, x, b, y, out, n);
+}
+
+template <class A, class B>
+__global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (B)x[i];
+}
+void launch_f64_to_f32(const double* x, float* y, long long n, cudaStream_t s) {
+    k_convert<double, float><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n);
+}
+void launch_f32_to_f64(const float* x, double* y, long long n, cudaStream_t s) {
+    k_convert<float, double><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n);
+}
+
+// Column j of the Hessenberg matrix H (column-major, ld = kMaxRestart + 1):
+// H[i][j] = h1_i + h2_i (i <= j), H[j+1][j] = ||w||; apply the previous
+// rotations, form rotation j, rotate g; resid = |g_{j+1}|.
+__global__ void k_givens(double* H, double* cs, double* sn, double* g, const double* h1, const double* h2,
+                         const double* hnorm2, int j, double* resid) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int ldh = kMaxRestart + 1;
+    double* col = H + (long long)j * ldh;
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + (h2 ? h2[i] : 0.0);
+    col[j + 1] = sqrt(fmax(hnorm2[0], 0.0));
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double den = hypot(a, b);
+    const double c = den > 0.0 ? a / den : 1.0;
+    const double s = den > 0.0 ? b / den : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    resid[0] = fabs(g[j + 1]);
+    resid[1] = den;
+}
+
+void launch_givens(double* H, double* cs, double* sn, double* g, const double* h1, const double* h2,
+                   const double* hnorm2, int j, double* resid, cudaStream_t s) {
+    k_givens<<<1, 32, 0, s>>>(H, cs, sn, g, h1, h2, hnorm2, j, resid);
+}
+
+__global__ void k_backsolve(const double* H, const double* g, int k, double* y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int ldh = kMaxRestart + 1;
+    for (int i = k - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int q = i + 1; q < k; ++q) t -= H[(long long)q * ldh + i] * y[q];
+        const double d = H[(long long)i * ldh + i];
+        y[i] = d != 0.0 ? t / d : 0.0;
+    }
+}
+void launch_backsolve(const double* H, const double* g, int k, double* y, cudaStream_t s) {
+    k_backsolve<<<1, 32, 0, s>>>(H, g, k, y);
+}
+
+__global__ void k_realizability(const double* __restrict__ U, int dim, long long N, double c,
+                                unsigned long long* count) {
+    unsigned long long local = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const double E = U[i];
+        double F2 = 0.0;
+        for (int b = 0; b < dim; ++b) {
+            const double f = U[(1 + b) * N + i];
+            F2 += f * f;
+        }
+        if (sqrt(F2) > c * E || !(E == E)) ++local;
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+void launch_realizability(const double* U, int dim, long long N, double c, unsigned long long* count,
+                          cudaStream_t s) {
+    k_realizability<<<kRedBlocks, kRedThreads, 0, s>>>(U, dim, N, c, count);
+}
+
+}  // namespace m1

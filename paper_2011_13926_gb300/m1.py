@@ -1,0 +1,367 @@
+"""Thin ctypes binding of libm1.so (include/m1.h): argument marshalling only.
+
+Every step of the M1 path runs in the CUDA library; this module converts
+numpy arrays / torch tensors to (pointer, m1_mem) pairs, fills the C structs
+and turns status codes into exceptions. There is no CPU fallback: importing a
+missing or stale library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libm1.so")
+
+M1_OK, M1_ERR_ARG, M1_ERR_CUDA, M1_ERR_NOMEM, M1_ERR_NOT_CONVERGED, M1_ERR_NONFINITE, M1_ERR_TIMEOUT, \
+    M1_ERR_STATE = range(8)
+STATUS_NAMES = ["M1_OK", "M1_ERR_ARG", "M1_ERR_CUDA", "M1_ERR_NOMEM", "M1_ERR_NOT_CONVERGED",
+                "M1_ERR_NONFINITE", "M1_ERR_TIMEOUT", "M1_ERR_STATE"]
+BC = {"outflow": 0, "periodic": 1, "reflect": 2, "dirichlet": 3}
+MEM_HOST, MEM_DEVICE = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+PRECOND_NONE, PRECOND_BJ = 0, 1
+
+EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "m1_set_state", "m1_get_state",
+            "m1_get_solution", "m1_set_boundary", "m1_set_emission", "m1_set_source", "m1_explicit_step",
+            "m1_implicit_step", "m1_residual", "m1_jv", "m1_diag_blocks", "m1_gmres_solve", "m1_stats",
+            "m1_last_error"]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("bc", (C.c_int * 2) * 3), ("c", C.c_double), ("a_r", C.c_double),
+                ("gas_coupling", C.c_int), ("well_balanced", C.c_int), ("ap_correction", C.c_int),
+                ("fixed_eigs", C.c_int), ("lambda_floor", C.c_double), ("wb_boundary", C.c_int),
+                ("implicit_eigs", C.c_int)]
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("restart", C.c_int),
+                ("gmres_max", C.c_int), ("gmres_rtol", C.c_double), ("precision", C.c_int),
+                ("precond", C.c_int), ("line_search", C.c_int), ("advance", C.c_int),
+                ("refine_max", C.c_int)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("converged", C.c_int), ("newton_iters", C.c_int), ("gmres_iters", C.c_int),
+                ("refinements", C.c_int), ("res0", C.c_double), ("res", C.c_double),
+                ("realizability_violations", C.c_longlong), ("time_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("converged", C.c_int), ("iters", C.c_int), ("res0", C.c_double), ("res", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_longlong), ("gmres_iters", C.c_longlong), ("jv_calls", C.c_longlong),
+                ("residual_calls", C.c_longlong), ("precond_builds", C.c_longlong),
+                ("explicit_steps", C.c_longlong), ("implicit_steps", C.c_longlong),
+                ("kernel_launches", C.c_longlong), ("bytes_per_jv", C.c_double),
+                ("bytes_per_residual", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libm1.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2011_13926_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, D, I, V = C.c_void_p, C.c_double, C.c_int, None
+    sig = {
+        "m1_default_opts": (V, [C.POINTER(SolverOpts)]),
+        "m1_init_grid": (I, [C.POINTER(GridDesc), P, C.POINTER(P)]),
+        "m1_destroy": (I, [P]),
+        "m1_set_opacity": (I, [P, P, P, I]),
+        "m1_set_state": (I, [P, P, P, P, P, I]),
+        "m1_get_state": (I, [P, P, P, P, I]),
+        "m1_get_solution": (I, [P, P, I]),
+        "m1_set_boundary": (I, [P, I, I, P, P, P, I]),
+        "m1_set_emission": (I, [P, P, I]),
+        "m1_set_source": (I, [P, P, I]),
+        "m1_explicit_step": (I, [P, D]),
+        "m1_implicit_step": (I, [P, D, C.POINTER(SolverOpts), C.POINTER(StepInfo)]),
+        "m1_residual": (I, [P, D, P, P, I]),
+        "m1_jv": (I, [P, D, P, P, P, I, I]),
+        "m1_diag_blocks": (I, [P, D, P, P, I]),
+        "m1_gmres_solve": (I, [P, D, P, P, P, C.POINTER(SolverOpts), C.POINTER(SolveInfo), I]),
+        "m1_stats": (I, [P, C.POINTER(Stats)]),
+        "m1_last_error": (C.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class M1Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def default_opts(**kw) -> SolverOpts:
+    o = SolverOpts()
+    load().m1_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(x, dtype=np.float64, allow_none=True):
+    """(pointer, mem, keepalive) of a numpy array or torch tensor."""
+    if x is None:
+        if not allow_none:
+            raise ValueError("array required")
+        return None, MEM_HOST, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            want = torch.float64 if dtype == np.float64 else torch.uint8
+            if x.dtype != want:
+                raise TypeError(f"expected {want}, got {x.dtype}")
+            if not x.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            if x.is_cuda:
+                return x.data_ptr(), MEM_DEVICE, x
+            a = x.numpy()
+            return a.ctypes.data, MEM_HOST, a
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, MEM_HOST, a
+
+
+def _check_mem(*mems):
+    ms = {m for m in mems if m is not None}
+    if len(ms) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return ms.pop() if ms else MEM_HOST
+
+
+class Context:
+    """One grid on the current CUDA device (m1_ctx)."""
+
+    def __init__(self, desc: GridDesc, stream: Optional[int] = None):
+        self.lib = load()
+        self.desc = desc
+        h = C.c_void_p()
+        st = self.lib.m1_init_grid(C.byref(desc), C.c_void_p(stream or 0), C.byref(h))
+        if st != M1_OK:
+            raise M1Error(st, "m1_init_grid failed")
+        self.h = h
+        self.dim = desc.dim
+        self.N = desc.n[0] * desc.n[1] * desc.n[2]
+        self.nu = 1 + desc.dim + (1 if desc.gas_coupling else 0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.m1_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, *args):
+        st = getattr(self.lib, name)(self.h, *args)
+        if st != M1_OK:
+            raise M1Error(st, self.lib.m1_last_error(self.h).decode())
+        return st
+
+    def _call_status(self, name, *args):
+        return getattr(self.lib, name)(self.h, *args)
+
+    def last_error(self) -> str:
+        return self.lib.m1_last_error(self.h).decode()
+
+    # ---------------------------------------------------------------- inputs
+    def set_opacity(self, sigma_a, sigma_f=None):
+        pa, ma, ka = _ptr(sigma_a)
+        pf, mf, kf = _ptr(sigma_f)
+        self._call("m1_set_opacity", pa, pf, _check_mem(ma, mf if pf else None))
+
+    def set_state(self, E, F, T=None, rho_cv=None):
+        pe, me, ke = _ptr(E)
+        pF, mF, kF = _ptr(F)
+        pt, mt, kt = _ptr(T)
+        pr, mr, kr = _ptr(rho_cv)
+        mem = _check_mem(me, mF, mt if pt else None, mr if pr else None)
+        self._call("m1_set_state", pe, pF, pt, pr, mem)
+
+    def set_boundary(self, axis, side, E, F, mask=None):
+        pe, me, ke = _ptr(E)
+        pF, mF, kF = _ptr(F)
+        pm, mm, km = _ptr(mask, dtype=np.uint8)
+        self._call("m1_set_boundary", axis, side, pe, pF, pm, _check_mem(me, mF, mm if pm else None))
+
+    def set_emission(self, B):
+        p, m, k = _ptr(B)
+        self._call("m1_set_emission", p, m)
+
+    def set_source(self, S):
+        p, m, k = _ptr(S)
+        self._call("m1_set_source", p, m)
+
+    # ---------------------------------------------------------------- outputs
+    def get_state(self, out=None):
+        """(E, F, T) as numpy arrays (or into device tensors given in ``out``)."""
+        if out is None:
+            E = np.empty(self.N)
+            F = np.empty(self.dim * self.N)
+            T = np.empty(self.N) if self.nu == 2 + self.dim else None
+            self._call("m1_get_state", E.ctypes.data, F.ctypes.data, T.ctypes.data if T is not None else None,
+                       MEM_HOST)
+            return E, F, T
+        E, F, T = out
+        pe, me, _ = _ptr(E)
+        pF, mF, _ = _ptr(F)
+        pt, mt, _ = _ptr(T)
+        self._call("m1_get_state", pe, pF, pt, _check_mem(me, mF, mt if pt else None))
+        return out
+
+    def get_solution(self, out=None):
+        if out is None:
+            out = np.empty(self.nu * self.N)
+        p, m, k = _ptr(out)
+        self._call("m1_get_solution", p, m)
+        return out
+
+    # ---------------------------------------------------------------- steps
+    def explicit_step(self, dt: float):
+        self._call("m1_explicit_step", C.c_double(dt))
+
+    def implicit_step(self, dt: float, opts: Optional[SolverOpts] = None, raise_on_fail: bool = True):
+        info = StepInfo()
+        o = opts if opts is not None else default_opts()
+        st = self.lib.m1_implicit_step(self.h, C.c_double(dt), C.byref(o), C.byref(info))
+        if st != M1_OK and raise_on_fail:
+            raise M1Error(st, self.last_error())
+        return st, info
+
+    def residual(self, dt: float, U, out=None):
+        pu, mu, ku = _ptr(U)
+        if out is None:
+            out = np.empty(self.nu * self.N) if mu == MEM_HOST else None
+        po, mo, ko = _ptr(out)
+        self._call("m1_residual", C.c_double(dt), pu, po, _check_mem(mu, mo))
+        return out
+
+    def jv(self, dt: float, U, v, out=None, precision: int = PREC_FP64):
+        pu, mu, ku = _ptr(U)
+        pv, mv, kv = _ptr(v)
+        if out is None:
+            out = np.empty(self.nu * self.N)
+        po, mo, ko = _ptr(out)
+        self._call("m1_jv", C.c_double(dt), pu, pv, po, precision, _check_mem(mu, mv, mo))
+        return out
+
+    def diag_blocks(self, dt: float, U, out=None):
+        pu, mu, ku = _ptr(U)
+        if out is None:
+            out = np.empty(self.nu * self.nu * self.N)
+        po, mo, ko = _ptr(out)
+        self._call("m1_diag_blocks", C.c_double(dt), pu, po, _check_mem(mu, mo))
+        return out
+
+    def gmres_solve(self, dt: float, b, U=None, out=None, opts: Optional[SolverOpts] = None,
+                    raise_on_fail: bool = True):
+        pu, mu, ku = _ptr(U)
+        pb, mb, kb = _ptr(b)
+        if out is None:
+            out = np.empty(self.nu * self.N)
+        po, mo, ko = _ptr(out)
+        info = SolveInfo()
+        o = opts if opts is not None else default_opts()
+        st = self.lib.m1_gmres_solve(self.h, C.c_double(dt), pu, pb, po, C.byref(o), C.byref(info),
+                                     _check_mem(mu if pu else None, mb, mo))
+        if st != M1_OK and raise_on_fail:
+            raise M1Error(st, self.last_error())
+        return out, info
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._call("m1_stats", C.byref(s))
+        return s.as_dict()
+
+
+def grid_desc(dim, n, lo=None, hi=None, bc=None, c=1.0, a_r=1.0, gas=False, well_balanced=True,
+              ap_correction=True, fixed_eigs=False, lambda_floor=0.0, wb_boundary=True,
+              implicit_eigs=True) -> GridDesc:
+    d = GridDesc()
+    d.dim = dim
+    n3 = list(n) + [1] * (3 - len(n))
+    lo = list(lo or [0.0] * dim) + [0.0] * (3 - dim)
+    hi = list(hi or [1.0] * dim) + [1.0] * (3 - dim)
+    bc = list(bc or [("outflow", "outflow")] * dim) + [("outflow", "outflow")] * (3 - dim)
+    for a in range(3):
+        d.n[a] = int(n3[a])
+        d.lo[a] = float(lo[a])
+        d.hi[a] = float(hi[a])
+        for s in range(2):
+            d.bc[a][s] = BC[bc[a][s]] if isinstance(bc[a][s], str) else int(bc[a][s])
+    d.c, d.a_r = float(c), float(a_r)
+    d.gas_coupling = int(bool(gas))
+    d.well_balanced = int(bool(well_balanced))
+    d.ap_correction = int(bool(ap_correction))
+    d.fixed_eigs = int(bool(fixed_eigs))
+    d.lambda_floor = float(lambda_floor)
+    d.wb_boundary = int(bool(wb_boundary))
+    d.implicit_eigs = int(bool(implicit_eigs))
+    return d
+
+
+def context_from_problem(p, stream: Optional[int] = None, device: bool = False) -> Context:
+    """Context for a problem object with the attributes of seeded_inputs.Problem
+    (duck-typed: dim, n, lo, hi, bc, c, a_r, flags, fields, boundary)."""
+    d = grid_desc(p.dim, p.n[:p.dim], p.lo[:p.dim], p.hi[:p.dim], p.bc, p.c, p.a_r, p.gas, p.well_balanced,
+                  p.ap_correction, p.fixed_eigs, p.lambda_floor, p.wb_boundary, p.implicit_eigs)
+    ctx = Context(d, stream)
+
+    def put(x):
+        if x is None:
+            return None
+        a = np.ascontiguousarray(x, dtype=np.float64).ravel()
+        if device:
+            import torch
+            return torch.from_numpy(a).cuda()
+        return a
+
+    ctx.set_opacity(put(p.sigma_a), put(p.sigma_f))
+    ctx.set_state(put(p.E), put(p.F), put(p.T) if p.gas else None, put(p.rho_cv) if p.gas else None)
+    if not p.gas and p.B is not None:
+        ctx.set_emission(put(p.B))
+    if p.S is not None:
+        ctx.set_source(put(p.S))
+    for (a, side), (Eg, Fg, mask) in p.boundary.items():
+        M = ctx.N // p.n[a]
+        Eg = np.broadcast_to(np.asarray(Eg, float), (M,)) if np.ndim(Eg) == 0 else np.asarray(Eg, float).ravel()
+        Fg = np.asarray(Fg, float).reshape(p.dim, -1)
+        Fg = np.broadcast_to(Fg, (p.dim, M)) if Fg.shape[1] == 1 else Fg
+        mask = None if mask is None else np.broadcast_to(np.asarray(mask, np.uint8).ravel(), (M,))
+        ctx.set_boundary(a, side, np.ascontiguousarray(Eg), np.ascontiguousarray(Fg),
+                         None if mask is None else np.ascontiguousarray(mask))
+    return ctx

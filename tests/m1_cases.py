@@ -1,0 +1,58 @@
+"""Shared small workloads for the GPU parity tests (seeded, span several
+256-thread tiles with ragged tails)."""
+import numpy as np
+
+import seeded_inputs as si
+
+
+def perturbed_state(p, seed, scale=0.05):
+    """U^n with a multiplicative perturbation (a generic Newton iterate)."""
+    rng = np.random.default_rng(seed)
+    u = p.state_vector()
+    return u * (1.0 + scale * rng.standard_normal(u.size))
+
+
+def gas_3d(n=(13, 11, 9), seed=3):
+    rng = np.random.default_rng(seed)
+    p = si.make_problem(3, n, bc=[("dirichlet", "outflow"), ("periodic", "periodic"), ("reflect", "outflow")],
+                        gas=True, dt_factor=20)
+    p.E = rng.uniform(0.5, 2.0, p.shape)
+    dirs = rng.standard_normal((3,) + p.shape)
+    dirs /= np.linalg.norm(dirs, axis=0, keepdims=True)
+    p.F = p.c * p.E * rng.uniform(0, 0.8, p.shape) * dirs
+    p.T = rng.uniform(0.7, 1.3, p.shape)
+    p.rho_cv = rng.uniform(0.5, 2.0, p.shape)
+    p.sigma_a = 10.0 ** rng.uniform(-1, 2, p.shape)
+    p.sigma_f = 10.0 ** rng.uniform(-1, 2, p.shape)
+    face = p.shape[:-1]
+    Eg = rng.uniform(0.5, 1.5, face)
+    Fg = np.zeros((3,) + face)
+    Fg[0] = 0.6 * Eg
+    p.boundary[(0, 0)] = (Eg, Fg, (rng.uniform(size=face) < 0.5).astype(np.uint8))
+    p.S = rng.uniform(0, 1, p.shape)
+    return p
+
+
+def smooth_2d(n=(40, 33), seed=11):
+    """Periodic 2D state away from vacuum with wave speeds at the new time
+    level (the Newton system of Sect. 3.3.1 with lambda(U^{n+1}))."""
+    p = si.make_problem(2, n, bc=[("periodic", "periodic")] * 2, dt_factor=10.0)
+    rng = np.random.default_rng(seed)
+    X, Y = p.mesh()
+    p.E = 0.1 + np.exp(-((X - 0.4) ** 2 + (Y - 0.6) ** 2) / (2 * 0.1 ** 2))
+    p.F = 0.2 * p.E * rng.uniform(-1, 1, (2,) + p.shape)
+    p.sigma_a = si.opacity_span(p.shape, 4.0, seed, 1e-1, 1e2, p.dx[0])
+    p.sigma_f = p.sigma_a.copy()
+    p.B = np.full(p.shape, 0.1)
+    p.implicit_eigs = True
+    return p
+
+
+def cases():
+    """name -> problem factory"""
+    return {
+        "slab1d": lambda: si.two_slab_1d(300, dt_factor=50.0),
+        "beam2d": lambda: si.beam_lognormal_2d(70, 45, dt_factor=10.0),
+        "smooth2d_implicit_eigs": smooth_2d,
+        "gas3d": gas_3d,
+    }
