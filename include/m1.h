@@ -87,6 +87,8 @@ typedef struct {
     int refine_max;       /* mixed precision: max FP64 refinement sweeps per Newton step (4) */
 } m1_solver_opts;
 
+#define M1_HIST 64  /* length of the per-Newton-iteration histories */
+
 typedef struct {
     int converged;        /* 1 when ||R|| <= newton_rtol * ||R^0|| */
     int newton_iters;
@@ -95,6 +97,11 @@ typedef struct {
     double res0, res;     /* ||R(U^n)||_2 and the final ||R||_2 */
     long long realizability_violations; /* cells with |F| > c E in the result (Sect. 3.1.3) */
     double time_ms;       /* wall time of the step measured on the stream */
+    /* per Newton iteration k < min(newton_iters, M1_HIST): ||R|| after the
+     * update, Arnoldi iterations of its linear solve, line-search theta */
+    double res_hist[M1_HIST];
+    int gmres_hist[M1_HIST];
+    double theta_hist[M1_HIST];
 } m1_step_info;
 
 typedef struct {
@@ -103,10 +110,29 @@ typedef struct {
     double res0, res;     /* ||b|| and the true ||b - J x|| at exit */
 } m1_solve_info;
 
+/* kernel classes of the per-class timers (m1_profile) */
+typedef enum {
+    M1_K_RESIDUAL = 0,   /* FP64 residual stencil */
+    M1_K_JV64 = 1,       /* FP64 J v stencil */
+    M1_K_JV32 = 2,       /* FP32 J v stencil */
+    M1_K_PC_BUILD = 3,   /* point-block extraction + inversion */
+    M1_K_PC_APPLY = 4,   /* block-Jacobi apply */
+    M1_K_ORTHO = 5,      /* Gram-Schmidt dots, updates, norms, Givens */
+    M1_K_VECTOR = 6,     /* other vector kernels (axpy, conversions) */
+    M1_K_EXPLICIT = 7,   /* semi-implicit step kernels */
+    M1_K_CLASSES = 8
+} m1_kernel_class;
+
 typedef struct {
     long long newton_iters, gmres_iters, jv_calls, residual_calls, precond_builds;
     long long explicit_steps, implicit_steps, kernel_launches;
-    double bytes_per_jv, bytes_per_residual;  /* algorithmic bytes of one launch */
+    double bytes_per_jv, bytes_per_residual;  /* algorithmic bytes of one launch (FP64) */
+    double bytes_per_jv32;                     /* algorithmic bytes of one FP32 J v launch */
+    /* with profiling on (m1_profile): device time (CUDA events on the
+     * context's stream) and launch count per m1_kernel_class */
+    double kernel_ms[M1_K_CLASSES];
+    long long kernel_count[M1_K_CLASSES];
+    double ortho_bytes;   /* algorithmic bytes moved by the Gram-Schmidt kernels so far */
 } m1_stats_t;
 
 typedef struct m1_ctx m1_ctx;
@@ -182,6 +208,10 @@ m1_status m1_gmres_solve(m1_ctx* ctx, double dt, const double* U, const double* 
 
 /* Cumulative counters of the context. */
 m1_status m1_stats(const m1_ctx* ctx, m1_stats_t* out);
+
+/* Turn the per-kernel-class event timers on (1) or off (0) and reset them.
+ * Timers add two event records per timed launch on the context's stream. */
+m1_status m1_profile(m1_ctx* ctx, int enable);
 
 /* Message of the last failed call on this context (never NULL). */
 const char* m1_last_error(const m1_ctx* ctx);

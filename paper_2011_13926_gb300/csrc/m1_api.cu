@@ -74,12 +74,20 @@ struct m1_ctx {
     float *binv32 = nullptr, *V32 = nullptr, *w32 = nullptr, *z32 = nullptr, *U32 = nullptr, *tmp32 = nullptr;
     double *Fstar = nullptr, *linework = nullptr;
     double* partials = nullptr;
+    double* ar_partials = nullptr;
+    unsigned* ar_counter = nullptr;
+    int* ar_reorth = nullptr;
     Scal sc{};
     double* scal_base = nullptr;
     int* singular = nullptr;
     unsigned long long* viol = nullptr;
     double* hpin = nullptr;  // pinned host scalars
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // per-kernel-class timers (m1_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> evs;
+    std::vector<int> ev_cls;
+    int ev_used = 0;
     m1_stats_t st{};
     std::string err = "no error";
 };
@@ -126,11 +134,44 @@ m1_status copy_out(m1_ctx* ctx, void* dst, const void* src, size_t bytes, m1_mem
                        ctx->s));
     return M1_OK;
 }
+// fold the recorded event pairs into the per-class totals (stream must be idle)
+void resolve_timers(m1_ctx* ctx) {
+    for (int i = 0; i < ctx->ev_used / 2; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->evs[2 * i], ctx->evs[2 * i + 1]) == cudaSuccess) {
+            ctx->st.kernel_ms[ctx->ev_cls[i]] += ms;
+            ctx->st.kernel_count[ctx->ev_cls[i]] += 1;
+        }
+    }
+    ctx->ev_used = 0;
+}
+
 m1_status sync(m1_ctx* ctx) {
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->s));
+    if (ctx->prof) resolve_timers(ctx);
     return M1_OK;
 }
+
+// Scoped timer of one kernel class: event records around the enclosed launches.
+struct TK {
+    m1_ctx* c;
+    int slot = -1;
+    TK(m1_ctx* ctx, int cls) : c(ctx) {
+        if (!c->prof) return;
+        if (c->ev_used + 2 > (int)c->evs.size()) {
+            cudaStreamSynchronize(c->s);
+            resolve_timers(c);
+        }
+        slot = c->ev_used;
+        c->ev_used += 2;
+        c->ev_cls[slot / 2] = cls;
+        cudaEventRecord(c->evs[slot], c->s);
+    }
+    ~TK() {
+        if (slot >= 0) cudaEventRecord(c->evs[slot + 1], c->s);
+    }
+};
 
 void count(m1_ctx* ctx, int k) { ctx->st.kernel_launches += k; }
 
@@ -209,7 +250,10 @@ Dev<float> dev32(const m1_ctx* ctx, double dt) {
     return g;
 }
 
-// recompute the time-n face data and the FP32 copies after any input changed
+m1_status refresh(m1_ctx* ctx);
+
+// validate the inputs; recompute the time-n face data and the FP32 copies
+// after any input changed
 m1_status prepare(m1_ctx* ctx) {
     if (!ctx->has_state) return fail(ctx, M1_ERR_STATE, "no state: call m1_set_state first");
     if (!ctx->has_opacity) return fail(ctx, M1_ERR_STATE, "no opacity: call m1_set_opacity first");
@@ -218,7 +262,14 @@ m1_status prepare(m1_ctx* ctx) {
             if (ctx->d.bc[a][sd] == M1_BC_DIRICHLET && !ctx->bE[a][sd])
                 return fail(ctx, M1_ERR_STATE, "Dirichlet boundary without data: call m1_set_boundary");
     if (!ctx->dirty) return M1_OK;
+    return refresh(ctx);
+}
+
+// time-n face data (lambda+-, alpha) and the FP32 copies of every input
+m1_status refresh(m1_ctx* ctx) {
     Dev<double> g = dev64(ctx, 0.0);
+    {
+    TK t(ctx, M1_K_VECTOR);
     launch_faces_time_n(g, ctx->f64.lam_p, ctx->f64.lam_m, ctx->f64.alpha, ctx->s);
     count(ctx, ctx->dim);
     const long long N = ctx->N;
@@ -237,6 +288,7 @@ m1_status prepare(m1_ctx* ctx) {
                 launch_f64_to_f32(ctx->bE[a][sd], ctx->bE32[a][sd], ctx->bM[a], ctx->s);
                 launch_f64_to_f32(ctx->bF[a][sd], ctx->bF32[a][sd], ctx->bM[a] * ctx->dim, ctx->s);
             }
+    }
     }
     ctx->dirty = false;
     return sync(ctx);
@@ -278,7 +330,10 @@ m1_status ensure_work32(m1_ctx* ctx) {
 
 // ||x||_2 read back to the host (FP64 accumulation)
 m1_status norm_f64(m1_ctx* ctx, const double* x, double* out) {
-    launch_norm2_f64(x, ctx->n, ctx->partials, ctx->sc.nrm2, ctx->s);
+    {
+        TK t(ctx, M1_K_ORTHO);
+        launch_norm2_f64(x, ctx->n, ctx->partials, ctx->sc.nrm2, ctx->s);
+    }
     count(ctx, 2);
     CK(cudaMemcpyAsync(ctx->hpin, ctx->sc.nrm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
     CKS(sync(ctx));
@@ -289,8 +344,11 @@ m1_status norm_f64(m1_ctx* ctx, const double* x, double* out) {
 // R = R(U) and its norm
 m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g, const double* U, double* R, double* nrm) {
     const int nb = stencil_blocks(ctx->N);
-    launch_residual_f64(g, U, R, ctx->partials, nb, ctx->s);
-    launch_finish_sum(ctx->partials, nb, 1, ctx->sc.nrm2, ctx->s);
+    {
+        TK t(ctx, M1_K_RESIDUAL);
+        launch_residual_f64(g, U, R, ctx->partials, nb, ctx->s);
+        launch_finish_sum(ctx->partials, nb, 1, ctx->sc.nrm2, ctx->s);
+    }
     count(ctx, 2);
     ctx->st.residual_calls++;
     CK(cudaMemcpyAsync(ctx->hpin, ctx->sc.nrm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
@@ -300,6 +358,7 @@ m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g, const double* U, doub
 }
 
 m1_status build_precond(m1_ctx* ctx, const Dev<double>& g, const double* U) {
+    TK t(ctx, M1_K_PC_BUILD);
     launch_diag_f64(g, U, ctx->blocks, ctx->s);
     CK(cudaMemsetAsync(ctx->singular, 0, sizeof(int), ctx->s));
     launch_block_inverse(ctx->nu, ctx->N, ctx->blocks, ctx->binv, ctx->binv32, ctx->singular, ctx->s);
@@ -318,11 +377,13 @@ struct Ops64 {
     const double* U;
     bool precond;
     void A(const double* in, double* out) {
+        TK t(ctx, M1_K_JV64);
         launch_jv_f64(g, U, in, out, ctx->s);
         count(ctx, 1);
         ctx->st.jv_calls++;
     }
     void M(const double* in, double* out) {
+        TK t(ctx, M1_K_PC_APPLY);
         if (precond) {
             launch_bj_apply_f64(ctx->nu, ctx->N, ctx->binv, in, out, ctx->s);
         } else {
@@ -337,11 +398,13 @@ struct Ops32 {
     const float* U;
     bool precond;
     void A(const float* in, float* out) {
+        TK t(ctx, M1_K_JV32);
         launch_jv_f32(g, U, in, out, ctx->s);
         count(ctx, 1);
         ctx->st.jv_calls++;
     }
     void M(const float* in, float* out) {
+        TK t(ctx, M1_K_PC_APPLY);
         if (precond) {
             launch_bj_apply_f32(ctx->nu, ctx->N, ctx->binv32, in, out, ctx->s);
         } else {
@@ -350,6 +413,31 @@ struct Ops32 {
         count(ctx, 1);
     }
 };
+
+ArnoldiDev arnoldi_dev(m1_ctx* ctx) {
+    ArnoldiDev K;
+    K.n = ctx->n;
+    K.ld = ctx->n;
+    K.blocks = reduce_blocks();
+    K.H = ctx->sc.H;
+    K.cs = ctx->sc.cs;
+    K.sn = ctx->sc.sn;
+    K.g = ctx->sc.g;
+    K.resid = ctx->sc.resid;
+    K.h1 = ctx->sc.h1;
+    K.h2 = ctx->sc.h2;
+    K.nrm2 = ctx->sc.nrm2;
+    K.partials = ctx->ar_partials;
+    K.counter = ctx->ar_counter;
+    K.reorth = ctx->ar_reorth;
+    return K;
+}
+inline void arnoldi_step(const ArnoldiDev& K, double* V, double* w, int j, cudaStream_t s) {
+    launch_arnoldi_step_f64(K, V, w, j, s);
+}
+inline void arnoldi_step(const ArnoldiDev& K, float* V, float* w, int j, cudaStream_t s) {
+    launch_arnoldi_step_f32(K, V, w, j, s);
+}
 
 inline void multidot(const double* V, long long ld, int j, const double* w, long long n, double* p, double* h,
                      cudaStream_t s) {
@@ -409,19 +497,19 @@ m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, doub
         T* Vj = V + (long long)j * n;
         ops.M(Vj, z);
         ops.A(z, w);
-        multidot(V, n, j, w, n, ctx->partials, sc.h1, s);
-        cgs_update(V, n, j, sc.h1, w, n, nullptr, s);
-        multidot(V, n, j, w, n, ctx->partials, sc.h2, s);
-        cgs_update(V, n, j, sc.h2, w, n, ctx->partials, s);
-        launch_finish_sum(ctx->partials, reduce_blocks(), 1, sc.nrm2 + 1, s);
-        launch_givens(sc.H, sc.cs, sc.sn, sc.g, sc.h1, sc.h2, sc.nrm2 + 1, j, sc.resid, s);
-        scale_inv_sqrt(w, sc.nrm2 + 1, V + (long long)(j + 1) * n, n, s);
-        count(ctx, 10);
-        CK(cudaMemcpyAsync(ctx->hpin, sc.resid, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        {
+            TK t(ctx, M1_K_ORTHO);
+            arnoldi_step(arnoldi_dev(ctx), V, w, j, s);
+        }
+        count(ctx, 4);
+        CK(cudaMemcpyAsync(ctx->hpin, sc.resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CKS(sync(ctx));
         k = j + 1;
         e = ctx->hpin[0];
         ctx->st.gmres_iters++;
+        // per Gram-Schmidt pass: dots read V_0..V_j and w, the update reads them
+        // again and writes one vector
+        ctx->st.ortho_bytes += (double)sizeof(T) * n * (2.0 * (j + 1) + 3.0) * (1.0 + ctx->hpin[2]);
         if (!(e == e)) return fail(ctx, M1_ERR_NONFINITE, "non-finite GMRES residual estimate");
         if (e <= target || ctx->hpin[1] == 0.0) break;
     }
@@ -678,10 +766,13 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
         AL(ctx->f32.lam_m[a], ctx->nfaces[a]);
     }
     AL(ctx->partials, (size_t)reduce_blocks() * kPartCols + stencil_blocks(N));
-    const size_t nscal = 4 + 4 * kPartCols + (size_t)kHLd * kMaxRestart + 2 * kMaxRestart + 2;
+    const size_t nscal = 4 + 4 * kPartCols + (size_t)kHLd * kMaxRestart + 2 * kMaxRestart + 4;
     AL(ctx->scal_base, nscal);
     AL(ctx->singular, 1);
     AL(ctx->viol, 1);
+    AL(ctx->ar_partials, (size_t)reduce_blocks() * (kPartCols + 1));
+    AL(ctx->ar_counter, 1);
+    AL(ctx->ar_reorth, 1);
 #undef AL
     double* p = ctx->scal_base;
     ctx->sc.nrm2 = p;
@@ -705,11 +796,23 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
     if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
         return cleanup(M1_ERR_CUDA);
     if (cudaMemsetAsync(ctx->scal_base, 0, nscal * sizeof(double), ctx->s) != cudaSuccess) return cleanup(M1_ERR_CUDA);
+    if (cudaMemsetAsync(ctx->ar_counter, 0, sizeof(unsigned), ctx->s) != cudaSuccess ||
+        cudaMemsetAsync(ctx->ar_reorth, 0, sizeof(int), ctx->s) != cudaSuccess)
+        return cleanup(M1_ERR_CUDA);
     if (!desc->gas_coupling && cudaMemsetAsync(ctx->B, 0, N * sizeof(double), ctx->s) != cudaSuccess)
         return cleanup(M1_ERR_CUDA);
     if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cleanup(M1_ERR_CUDA);
-    ctx->st.bytes_per_jv = (double)N * (8.0 * (2 * ctx->nu + ctx->nu) + 8.0 * 2 + 8.0 * ctx->dim);
-    ctx->st.bytes_per_residual = (double)N * (8.0 * (3 * ctx->nu) + 8.0 * 3 + 8.0 * ctx->dim);
+    {
+        // minimal traffic per launch: J v reads U, v, sigma_a, sigma_f, alpha (one
+        // face per cell and axis), the time-n wave speeds when they are frozen
+        // (two per face), rho c_v with gas; writes J v. The residual also reads
+        // U^n and the emission (or T^n) and the source.
+        const double nu = ctx->nu, dim = ctx->dim;
+        const double fields = 2.0 + dim + (desc->implicit_eigs ? 0.0 : 2.0 * dim) + (desc->gas_coupling ? 1.0 : 0.0);
+        ctx->st.bytes_per_jv = (double)N * 8.0 * (3.0 * nu + fields);
+        ctx->st.bytes_per_jv32 = (double)N * 4.0 * (3.0 * nu + fields);
+        ctx->st.bytes_per_residual = (double)N * 8.0 * (3.0 * nu + fields + (desc->gas_coupling ? 0.0 : 1.0));
+    }
     *out = ctx;
     return M1_OK;
 }
@@ -721,7 +824,8 @@ m1_status m1_destroy(m1_ctx* ctx) {
                     ctx->sig_f32, ctx->B32, ctx->S32, ctx->rho_cv32, ctx->Un32, ctx->U, ctx->R, ctx->Ut, ctx->Rt,
                     ctx->delta, ctx->rhs, ctx->w, ctx->z, ctx->tmp, ctx->V, ctx->xacc, ctx->blocks, ctx->binv,
                     ctx->binv32, ctx->V32, ctx->w32, ctx->z32, ctx->U32, ctx->tmp32, ctx->Fstar, ctx->linework,
-                    ctx->partials, ctx->scal_base, ctx->singular, ctx->viol};
+                    ctx->partials, ctx->scal_base, ctx->singular, ctx->viol, ctx->ar_partials,
+                    ctx->ar_counter, ctx->ar_reorth};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int a = 0; a < 3; ++a) {
@@ -738,6 +842,7 @@ m1_status m1_destroy(m1_ctx* ctx) {
     if (ctx->hpin) cudaFreeHost(ctx->hpin);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
     delete ctx;
     return M1_OK;
 }
@@ -850,11 +955,14 @@ m1_status m1_explicit_step(m1_ctx* ctx, double dt) {
         ctx->expl_ok = true;
     }
     Dev<double> g = dev64(ctx, dt);
-    launch_explicit_hyp(g, ctx->Unew, ctx->Fstar, ctx->s);
-    count(ctx, 1);
-    for (int b = 0; b < ctx->dim; ++b) {
-        launch_wb_lines(g, b, ctx->Fstar, ctx->Unew + (1 + b) * ctx->N, ctx->linework, ctx->s);
+    {
+        TK t(ctx, M1_K_EXPLICIT);
+        launch_explicit_hyp(g, ctx->Unew, ctx->Fstar, ctx->s);
         count(ctx, 1);
+        for (int b = 0; b < ctx->dim; ++b) {
+            launch_wb_lines(g, b, ctx->Fstar, ctx->Unew + (1 + b) * ctx->N, ctx->linework, ctx->s);
+            count(ctx, 1);
+        }
     }
     CK(cudaMemcpyAsync(ctx->Un, ctx->Unew, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s));
     ctx->dirty = true;
@@ -974,6 +1082,8 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
     m1_step_info inf{};
     cudaStream_t s = ctx->s;
     CK(cudaEventRecord(ctx->ev0, s));
+    // alpha and the time-n wave speeds are the first stage of every step
+    CKS(refresh(ctx));
     const long long n = ctx->n;
     Dev<double> g = dev64(ctx, dt);
     CK(cudaMemcpyAsync(ctx->U, ctx->Un, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -1011,6 +1121,11 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
         std::swap(ctx->U, ctx->Ut);
         std::swap(ctx->R, ctx->Rt);
         rn = rt;
+        if (inf.newton_iters < M1_HIST) {
+            inf.res_hist[inf.newton_iters] = rn;
+            inf.gmres_hist[inf.newton_iters] = it;
+            inf.theta_hist[inf.newton_iters] = theta;
+        }
         inf.newton_iters++;
         ctx->st.newton_iters++;
         if (!(rn == rn) || isinf(rn)) {
@@ -1042,6 +1157,24 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
     if (ctx->dirty) CKS(prepare(ctx));
     if (result != M1_OK) return result;
     if (!inf.converged) return fail(ctx, M1_ERR_NOT_CONVERGED, "Newton did not converge");
+    return M1_OK;
+}
+
+m1_status m1_profile(m1_ctx* ctx, int enable) {
+    if (!ctx) return M1_ERR_ARG;
+    CKS(sync(ctx));
+    if (enable && ctx->evs.empty()) {
+        const int pairs = 2048;
+        ctx->evs.resize(2 * pairs);
+        ctx->ev_cls.resize(pairs);
+        for (auto& e : ctx->evs) CK(cudaEventCreate(&e));
+    }
+    ctx->prof = enable != 0;
+    ctx->ev_used = 0;
+    for (int k = 0; k < M1_K_CLASSES; ++k) {
+        ctx->st.kernel_ms[k] = 0.0;
+        ctx->st.kernel_count[k] = 0;
+    }
     return M1_OK;
 }
 

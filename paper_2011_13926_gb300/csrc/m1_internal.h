@@ -30,6 +30,19 @@ void launch_wb_lines(const Dev<double>& g, int b, const double* Fstar, double* F
                      cudaStream_t s);
 int stencil_blocks(long long N);
 
+// ----------------------------------------------------------------- Arnoldi (m1_arnoldi.cu)
+// device scalars and scratch of one fused Arnoldi step (CGS with selective
+// reorthogonalisation, Givens on the FP64 Hessenberg column in the last block)
+struct ArnoldiDev {
+    long long n, ld;     // vector length, basis stride
+    int blocks;          // grid size of the dot/update kernels (partials has blocks * (kMaxRestart + 2))
+    double *H, *cs, *sn, *g, *resid, *h1, *h2, *nrm2, *partials;
+    unsigned* counter;   // arrival counter of the last-block reduction (kept at 0 between launches)
+    int* reorth;         // 1 when the second Gram-Schmidt pass runs
+};
+void launch_arnoldi_step_f64(const ArnoldiDev& K, double* V, double* w, int j, cudaStream_t s);
+void launch_arnoldi_step_f32(const ArnoldiDev& K, float* V, float* w, int j, cudaStream_t s);
+
 // ----------------------------------------------------------------- vectors (m1_vec.cu)
 int reduce_blocks();
 // partial sums of squares of x (FP64) and the final sum into out[0]

@@ -28,7 +28,7 @@ PRECOND_NONE, PRECOND_BJ = 0, 1
 EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "m1_set_state", "m1_get_state",
             "m1_get_solution", "m1_set_boundary", "m1_set_emission", "m1_set_source", "m1_explicit_step",
             "m1_implicit_step", "m1_residual", "m1_jv", "m1_diag_blocks", "m1_gmres_solve", "m1_stats",
-            "m1_last_error"]
+            "m1_profile", "m1_last_error"]
 
 
 class GridDesc(C.Structure):
@@ -46,13 +46,25 @@ class SolverOpts(C.Structure):
                 ("refine_max", C.c_int)]
 
 
+M1_HIST = 64
+KERNEL_CLASSES = ["residual", "jv64", "jv32", "pc_build", "pc_apply", "ortho", "vector", "explicit"]
+
+
 class StepInfo(C.Structure):
     _fields_ = [("converged", C.c_int), ("newton_iters", C.c_int), ("gmres_iters", C.c_int),
                 ("refinements", C.c_int), ("res0", C.c_double), ("res", C.c_double),
-                ("realizability_violations", C.c_longlong), ("time_ms", C.c_double)]
+                ("realizability_violations", C.c_longlong), ("time_ms", C.c_double),
+                ("res_hist", C.c_double * M1_HIST), ("gmres_hist", C.c_int * M1_HIST),
+                ("theta_hist", C.c_double * M1_HIST)]
 
-    def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+    def as_dict(self, history: bool = False):
+        out = {k: getattr(self, k) for k, _ in self._fields_[:8]}
+        if history:
+            k = min(self.newton_iters, M1_HIST)
+            out["res_hist"] = list(self.res_hist[:k])
+            out["gmres_hist"] = list(self.gmres_hist[:k])
+            out["theta_hist"] = list(self.theta_hist[:k])
+        return out
 
 
 class SolveInfo(C.Structure):
@@ -67,10 +79,15 @@ class Stats(C.Structure):
                 ("residual_calls", C.c_longlong), ("precond_builds", C.c_longlong),
                 ("explicit_steps", C.c_longlong), ("implicit_steps", C.c_longlong),
                 ("kernel_launches", C.c_longlong), ("bytes_per_jv", C.c_double),
-                ("bytes_per_residual", C.c_double)]
+                ("bytes_per_residual", C.c_double), ("bytes_per_jv32", C.c_double),
+                ("kernel_ms", C.c_double * 8), ("kernel_count", C.c_longlong * 8), ("ortho_bytes", C.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {k: getattr(self, k) for k, _ in self._fields_[:11]}
+        out["ortho_bytes"] = self.ortho_bytes
+        out["kernel_ms"] = dict(zip(KERNEL_CLASSES, list(self.kernel_ms)))
+        out["kernel_count"] = dict(zip(KERNEL_CLASSES, list(self.kernel_count)))
+        return out
 
 
 _lib = None
@@ -103,6 +120,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_diag_blocks": (I, [P, D, P, P, I]),
         "m1_gmres_solve": (I, [P, D, P, P, P, C.POINTER(SolverOpts), C.POINTER(SolveInfo), I]),
         "m1_stats": (I, [P, C.POINTER(Stats)]),
+        "m1_profile": (I, [P, I]),
         "m1_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -301,6 +319,9 @@ class Context:
         if st != M1_OK and raise_on_fail:
             raise M1Error(st, self.last_error())
         return out, info
+
+    def profile(self, enable: bool = True):
+        self._call("m1_profile", int(bool(enable)))
 
     def stats(self) -> dict:
         s = Stats()

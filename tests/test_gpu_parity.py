@@ -88,8 +88,10 @@ def test_diag_blocks(m1mod, name):
     got = ctx.diag_blocks(p.dt, u).reshape(s.nu, s.nu, s.N)  # [row, col, cell]
     ref = s.diag_blocks(u)  # [cell, row, col]
     ref = np.transpose(ref, (1, 2, 0))
-    scale = np.abs(ref).max(axis=2, keepdims=True)
-    assert np.all(np.abs(got - ref) <= 1e-12 * np.maximum(scale, 1e-300) + 1e-300)
+    # relative to each cell's block: entries that cancel exactly in one rounding
+    # order leave a few ulps of the block's scale in the other
+    scale = np.abs(ref).max(axis=(0, 1), keepdims=True)
+    assert np.all(np.abs(got - ref) <= 1e-12 * np.maximum(scale, 1e-300))
 
 
 @pytest.mark.parametrize("name", ["slab1d", "beam2d", "gas3d"])
@@ -105,9 +107,15 @@ def test_explicit_step(m1mod, name, wb):
     fields = [(E, ref[0])] + [(F[b * p.ncell:(b + 1) * p.ncell], ref[1 + b]) for b in range(p.dim)]
     if p.gas:
         fields.append((T, ref[1 + p.dim]))
-    for got, want in fields:
+    # flux components are compared in units of c max|E| (a component that stays
+    # zero in one rounding order keeps a few ulps of the transverse terms in the other)
+    scaleE = np.abs(ref[0]).max()
+    for k, (got, want) in enumerate(fields):
         want = np.asarray(want).ravel()
-        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+        scale = np.abs(want).max()
+        if 1 <= k <= p.dim:
+            scale = max(scale, p.c * scaleE)
+        assert np.abs(got - want).max() <= 1e-12 * scale
 
 
 def test_explicit_step_periodic_and_degenerate(m1mod):
@@ -123,10 +131,12 @@ def test_explicit_step_periodic_and_degenerate(m1mod):
         ctx = ctx_for(m1mod, p)
         ctx.explicit_step(p.dt)
         E, F, _ = ctx.get_state()
-        assert np.abs(E - ref[0].ravel()).max() <= 1e-12 * np.abs(ref[0]).max()
+        scaleE = np.abs(ref[0]).max()
+        assert np.abs(E - ref[0].ravel()).max() <= 1e-12 * scaleE
         for b in range(2):
             want = ref[1 + b].ravel()
-            assert np.abs(F[b * p.ncell:(b + 1) * p.ncell] - want).max() <= 1e-12 * np.abs(want).max()
+            scale = max(np.abs(want).max(), p.c * scaleE)
+            assert np.abs(F[b * p.ncell:(b + 1) * p.ncell] - want).max() <= 1e-12 * scale
 
 
 @pytest.mark.parametrize("shape", [(8,), (4, 4), (3, 3, 3)])
