@@ -52,6 +52,7 @@ struct m1_ctx {
     cudaStream_t s = nullptr;
     int dim = 1, nu = 2;
     long long N = 0, n = 0;
+    long long ld = 0;  // Krylov basis stride: n rounded up to 64 elements (256-byte rows)
     long long nfaces[3] = {0, 0, 0};
     long long bM[3] = {0, 0, 0};
     // FP64 fields
@@ -308,7 +309,7 @@ m1_status ensure_work(m1_ctx* ctx) {
     CKS(dalloc(ctx, &ctx->z, n));
     CKS(dalloc(ctx, &ctx->tmp, n));
     CKS(dalloc(ctx, &ctx->xacc, n));
-    CKS(dalloc(ctx, &ctx->V, (size_t)n * (kMaxRestart + 1)));
+    CKS(dalloc(ctx, &ctx->V, (size_t)ctx->ld * (kMaxRestart + 1)));
     CKS(dalloc(ctx, &ctx->blocks, (size_t)nu * nu * N));
     CKS(dalloc(ctx, &ctx->binv, (size_t)nu * nu * N));
     CKS(dalloc(ctx, &ctx->binv32, (size_t)nu * nu * N));
@@ -319,7 +320,7 @@ m1_status ensure_work(m1_ctx* ctx) {
 m1_status ensure_work32(m1_ctx* ctx) {
     if (ctx->work32_ok) return M1_OK;
     const long long n = ctx->n;
-    CKS(dalloc(ctx, &ctx->V32, (size_t)n * (kMaxRestart + 1)));
+    CKS(dalloc(ctx, &ctx->V32, (size_t)ctx->ld * (kMaxRestart + 1)));
     CKS(dalloc(ctx, &ctx->w32, n));
     CKS(dalloc(ctx, &ctx->z32, n));
     CKS(dalloc(ctx, &ctx->U32, n));
@@ -417,7 +418,7 @@ struct Ops32 {
 ArnoldiDev arnoldi_dev(m1_ctx* ctx) {
     ArnoldiDev K;
     K.n = ctx->n;
-    K.ld = ctx->n;
+    K.ld = ctx->ld;
     K.blocks = reduce_blocks();
     K.H = ctx->sc.H;
     K.cs = ctx->sc.cs;
@@ -493,8 +494,9 @@ m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, doub
     CK(cudaMemcpyAsync(sc.g, g0.data(), sizeof(double) * kPartCols, cudaMemcpyHostToDevice, s));
     int k = 0;
     double e = beta;
+    const long long ld = ctx->ld;
     for (int j = 0; j < maxk; ++j) {
-        T* Vj = V + (long long)j * n;
+        T* Vj = V + (long long)j * ld;
         ops.M(Vj, z);
         ops.A(z, w);
         {
@@ -515,7 +517,7 @@ m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, doub
     }
     launch_backsolve(sc.H, sc.g, k, sc.y, s);
     CK(cudaMemsetAsync(ctx->tmp, 0, sizeof(double) * n, s));
-    lincomb_add(V, n, k, sc.y, ctx->tmp, n, s);
+    lincomb_add(V, ld, k, sc.y, ctx->tmp, n, s);
     count(ctx, 2);
     *kout = k;
     *est = e;
@@ -728,6 +730,7 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
     ctx->nu = 1 + desc->dim + (desc->gas_coupling ? 1 : 0);
     ctx->N = (long long)desc->n[0] * desc->n[1] * desc->n[2];
     ctx->n = ctx->N * ctx->nu;
+    ctx->ld = (ctx->n + 63) / 64 * 64;
     for (int a = 0; a < 3; ++a) {
         ctx->nfaces[a] = ctx->N / desc->n[a] * (desc->n[a] + 1);
         ctx->bM[a] = ctx->N / desc->n[a];
@@ -1022,17 +1025,27 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
     if (o->restart < 1 || o->restart > kMaxRestart)
         return fail(ctx, M1_ERR_ARG, "restart must be in [1, 30]");
     Dev<double> g = dev64(ctx, dt);
-    if (pre) CKS(build_precond(ctx, g, Ud));
     Ops64 ops{ctx, g, Ud, pre};
     *refinements = 0;
     if (o->precision == M1_PREC_MIXED) {
         CKS(ensure_work32(ctx));
         launch_f64_to_f32(Ud, ctx->U32, ctx->n, ctx->s);
         count(ctx, 1);
-        Ops32 ops32{ctx, dev32(ctx, dt), ctx->U32, pre};
+        const Dev<float> g32 = dev32(ctx, dt);
+        if (pre) {  // FP32 point blocks, inverted in FP64
+            TK t(ctx, M1_K_PC_BUILD);
+            launch_diag_f32(g32, ctx->U32, reinterpret_cast<float*>(ctx->blocks), ctx->s);
+            CK(cudaMemsetAsync(ctx->singular, 0, sizeof(int), ctx->s));
+            launch_block_inverse_f32(ctx->nu, ctx->N, reinterpret_cast<const float*>(ctx->blocks), ctx->binv,
+                                     ctx->binv32, ctx->singular, ctx->s);
+            count(ctx, 2);
+            ctx->st.precond_builds++;
+        }
+        Ops32 ops32{ctx, g32, ctx->U32, pre};
         return gmres_mixed(ctx, ops, ops32, b, x, o->gmres_rtol, o->restart, o->gmres_max, o->refine_max, iters,
                            refinements, bnorm, res, conv);
     }
+    if (pre) CKS(build_precond(ctx, g, Ud));
     return gmres64(ctx, ops, b, x, o->gmres_rtol, o->restart, o->gmres_max, iters, bnorm, res, conv);
 }
 

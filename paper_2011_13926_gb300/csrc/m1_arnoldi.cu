@@ -85,10 +85,32 @@ __device__ void givens_column(const ArnoldiDev& K, const double* h, double beta,
     K.nrm2[1] = beta * beta;
 }
 
+// 16-byte vectors of the basis element type (rows of V start on 256-byte
+// boundaries: the basis stride is a multiple of 64 elements)
+template <class T> struct Vec;
+template <> struct Vec<float> {
+    using type = float4;
+    static constexpr int W = 4;
+};
+template <> struct Vec<double> {
+    using type = double2;
+    static constexpr int W = 2;
+};
+__device__ __forceinline__ float comp(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+__device__ __forceinline__ double comp(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+__device__ __forceinline__ void setc(float4& v, int k, float x) {
+    if (k == 0) v.x = x; else if (k == 1) v.y = x; else if (k == 2) v.z = x; else v.w = x;
+}
+__device__ __forceinline__ void setc(double2& v, int k, double x) {
+    if (k == 0) v.x = x; else v.y = x;
+}
+
 template <class T>
 __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const T* __restrict__ V,
                                                              const T* __restrict__ w, int j, int pass) {
     if (pass == 2 && *K.reorth == 0) return;
+    using VT = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
     __shared__ double red[kArThreads / 32][kCols + 1];
     __shared__ bool last;
     Acc<T> acc[kCols];
@@ -97,12 +119,28 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
     for (int i = 0; i < kCols; ++i) acc[i].zero();
     ww.zero();
     const long long n = K.n, ld = K.ld;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const T we = w[e];
-        ww.add_prod(we, we);
+    const long long nv = n / W;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += stride) {
+        const VT wv = reinterpret_cast<const VT*>(w)[q];
+#pragma unroll
+        for (int k = 0; k < W; ++k) ww.add_prod(comp(wv, k), comp(wv, k));
 #pragma unroll
         for (int i = 0; i < kCols; ++i)
-            if (i <= j) acc[i].add_prod(V[i * ld + e], we);
+            if (i <= j) {
+                const VT vv = reinterpret_cast<const VT*>(V + i * ld)[q];
+#pragma unroll
+                for (int k = 0; k < W; ++k) acc[i].add_prod(comp(vv, k), comp(wv, k));
+            }
+    }
+    if (blockIdx.x == 0) {  // scalar tail
+        for (long long e = nv * W + threadIdx.x; e < n; e += blockDim.x) {
+            const T we = w[e];
+            ww.add_prod(we, we);
+#pragma unroll
+            for (int i = 0; i < kCols; ++i)
+                if (i <= j) acc[i].add_prod(V[i * ld + e], we);
+        }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -169,6 +207,8 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_update(ArnoldiDev K, T* 
                                                                int j, int pass) {
     const int reorth = *K.reorth;
     if (pass == 2 && reorth == 0) return;
+    using VT = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
     __shared__ T hs[kCols];
     const double* h = pass == 1 ? K.h1 : K.h2;
     if (threadIdx.x < kCols) hs[threadIdx.x] = threadIdx.x <= j ? (T)h[threadIdx.x] : T(0);
@@ -178,12 +218,29 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_update(ArnoldiDev K, T* 
     const T inv = final_pass ? (b2 > 0.0 ? (T)(1.0 / sqrt(b2)) : T(0)) : T(1);
     T* out = final_pass ? V + (long long)(j + 1) * K.ld : w;
     const long long n = K.n, ld = K.ld;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        T x = w[e];
+    const long long nv = n / W;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += stride) {
+        VT x = reinterpret_cast<const VT*>(w)[q];
 #pragma unroll
         for (int i = 0; i < kCols; ++i)
-            if (i <= j) x = fma(-hs[i], V[i * ld + e], x);
-        out[e] = x * inv;
+            if (i <= j) {
+                const VT vv = reinterpret_cast<const VT*>(V + i * ld)[q];
+#pragma unroll
+                for (int k = 0; k < W; ++k) setc(x, k, fma(-hs[i], comp(vv, k), comp(x, k)));
+            }
+#pragma unroll
+        for (int k = 0; k < W; ++k) setc(x, k, comp(x, k) * inv);
+        reinterpret_cast<VT*>(out)[q] = x;
+    }
+    if (blockIdx.x == 0) {
+        for (long long e = nv * W + threadIdx.x; e < n; e += blockDim.x) {
+            T x = w[e];
+#pragma unroll
+            for (int i = 0; i < kCols; ++i)
+                if (i <= j) x = fma(-hs[i], V[i * ld + e], x);
+            out[e] = x * inv;
+        }
     }
 }
 

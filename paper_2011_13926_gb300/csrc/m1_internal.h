@@ -21,6 +21,10 @@ void launch_jv_f32(const Dev<float>& g, const float* U, const float* v, float* J
 void launch_diag_f64(const Dev<double>& g, const double* U, double* blocks, cudaStream_t s);
 void launch_block_inverse(int nu, long long N, const double* blocks, double* binv64, float* binv32,
                           int* singular, cudaStream_t s);
+// FP32 point blocks (the mixed-precision preconditioner), inverted in FP64
+void launch_diag_f32(const Dev<float>& g, const float* U, float* blocks, cudaStream_t s);
+void launch_block_inverse_f32(int nu, long long N, const float* blocks, double* binv64, float* binv32,
+                              int* singular, cudaStream_t s);
 void launch_bj_apply_f64(int nu, long long N, const double* binv, const double* r, double* z, cudaStream_t s);
 void launch_bj_apply_f32(int nu, long long N, const float* binv, const float* r, float* z, cudaStream_t s);
 // semi-implicit step: hyperbolic update + exchange -> Unew (E, T) and Fstar

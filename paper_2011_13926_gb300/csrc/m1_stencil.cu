@@ -144,18 +144,17 @@ __global__ void __launch_bounds__(kThreads) k_jv(Dev<R> g, const R* __restrict__
 }
 
 // ------------------------------------------------------------------ point blocks
-template <int DIM, bool GAS>
-__global__ void __launch_bounds__(kThreads) k_diag(Dev<double> g, const double* __restrict__ U,
-                                                   double* __restrict__ blocks) {
+template <class R, int DIM, bool GAS>
+__global__ void __launch_bounds__(kThreads) k_diag(Dev<R> g, const R* __restrict__ U, R* __restrict__ blocks) {
     constexpr int NU = 1 + DIM + (GAS ? 1 : 0);
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
     int coord[3];
     cell_coord(idx, g.n[0], g.n[1], coord);
     for (int k = 0; k < NU; ++k) {
-        LoadSeed<double> ld{U, g.N, k};
-        Dual<double> out[NU];
-        cell_residual<Dual<double>, DIM, GAS>(g, ld, idx, coord, out);
+        LoadSeed<R> ld{U, g.N, k};
+        Dual<R> out[NU];
+        cell_residual<Dual<R>, DIM, GAS>(g, ld, idx, coord, out);
 #pragma unroll
         for (int r = 0; r < NU; ++r) blocks[(long long)(r * NU + k) * g.N + idx] = out[r].d;
     }
@@ -209,15 +208,22 @@ void launch_jv_f32(const Dev<float>& g, const float* U, const float* v, float* J
 
 void launch_diag_f64(const Dev<double>& g, const double* U, double* blocks, cudaStream_t s) {
     const int nb = stencil_blocks(g.N);
-#define CALL(D, G) k_diag<D, G><<<nb, kThreads, 0, s>>>(g, U, blocks)
+#define CALL(D, G) k_diag<double, D, G><<<nb, kThreads, 0, s>>>(g, U, blocks)
+    M1_DISPATCH(g.dim, g.gas, CALL);
+#undef CALL
+}
+
+void launch_diag_f32(const Dev<float>& g, const float* U, float* blocks, cudaStream_t s) {
+    const int nb = stencil_blocks(g.N);
+#define CALL(D, G) k_diag<float, D, G><<<nb, kThreads, 0, s>>>(g, U, blocks)
     M1_DISPATCH(g.dim, g.gas, CALL);
 #undef CALL
 }
 
 // ------------------------------------------------------------------ block inverse / apply
 // Gauss-Jordan with partial pivoting on each cell's NU x NU block (FP64).
-template <int NU>
-__global__ void k_block_inverse(long long N, const double* __restrict__ blocks, double* __restrict__ binv64,
+template <int NU, class B>
+__global__ void k_block_inverse(long long N, const B* __restrict__ blocks, double* __restrict__ binv64,
                                 float* __restrict__ binv32, int* singular) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -226,7 +232,7 @@ __global__ void k_block_inverse(long long N, const double* __restrict__ blocks, 
     for (int r = 0; r < NU; ++r)
 #pragma unroll
         for (int c = 0; c < NU; ++c) {
-            a[r][c] = blocks[(long long)(r * NU + c) * N + i];
+            a[r][c] = (double)blocks[(long long)(r * NU + c) * N + i];
             x[r][c] = (r == c) ? 1.0 : 0.0;
         }
     bool bad = false;
@@ -289,15 +295,24 @@ __global__ void k_block_inverse(long long N, const double* __restrict__ blocks, 
         }
 }
 
-void launch_block_inverse(int nu, long long N, const double* blocks, double* binv64, float* binv32, int* singular,
+template <class B>
+static void block_inverse(int nu, long long N, const B* blocks, double* binv64, float* binv32, int* singular,
                           cudaStream_t s) {
     const int nb = stencil_blocks(N);
     switch (nu) {
-        case 2: k_block_inverse<2><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
-        case 3: k_block_inverse<3><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
-        case 4: k_block_inverse<4><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
-        default: k_block_inverse<5><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
+        case 2: k_block_inverse<2, B><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
+        case 3: k_block_inverse<3, B><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
+        case 4: k_block_inverse<4, B><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
+        default: k_block_inverse<5, B><<<nb, kThreads, 0, s>>>(N, blocks, binv64, binv32, singular); break;
     }
+}
+void launch_block_inverse(int nu, long long N, const double* blocks, double* binv64, float* binv32, int* singular,
+                          cudaStream_t s) {
+    block_inverse<double>(nu, N, blocks, binv64, binv32, singular, s);
+}
+void launch_block_inverse_f32(int nu, long long N, const float* blocks, double* binv64, float* binv32,
+                              int* singular, cudaStream_t s) {
+    block_inverse<float>(nu, N, blocks, binv64, binv32, singular, s);
 }
 
 template <class R, int NU>
