@@ -213,6 +213,54 @@ m1_status m1_stats(const m1_ctx* ctx, m1_stats_t* out);
  * Timers add two event records per timed launch on the context's stream. */
 m1_status m1_profile(m1_ctx* ctx, int enable);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free residual.
+ *
+ * The paper has no counterpart of this entry point. It serves callers that
+ * cannot allocate device memory at the point of the call: code running inside
+ * a memory pool or arena that forbids cudaMalloc/cudaFree, a host thread that
+ * must not trigger the implicit synchronisation of an allocation, or a
+ * framework that owns all allocations itself. It computes the same R(U) as
+ * m1_residual, but without a context: every input and output is a device
+ * pointer passed by the caller, and the working memory (the time-n face data
+ * and the reduction partials) lives in one file-scope __device__ array of the
+ * library, sized for at most M1_NOALLOC_MAX_CELLS cells. Every GPU that loads
+ * the library holds that array (about 9.4 MB) until the process exits.
+ *
+ * Rules:
+ *   - N = n[0]*n[1]*n[2] above M1_NOALLOC_MAX_CELLS is rejected with
+ *     M1_ERR_ARG before anything is launched.
+ *   - The call allocates nothing (no cudaMalloc, cudaFree or allocating
+ *     library routine). Its first call on a device looks up the array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that first
+ *     call before any stream capture.
+ *   - Every call shares the one array, which keeps the last call's contents:
+ *     the call clears what must start at zero, but calls that overlap on the
+ *     GPU (different streams, or different host threads on one device) race.
+ *     Serialise them.
+ *   - The call is asynchronous on cuda_stream: R and *norm2 are valid once the
+ *     stream has reached this point. Only launch errors are reported.
+ * ------------------------------------------------------------------------- */
+#define M1_NOALLOC_MAX_CELLS 65536
+
+typedef struct {
+    const double* Un;        /* time-n state, n_u*N (device) */
+    const double* sigma_a;   /* N (device) */
+    const double* sigma_f;   /* N (device), NULL = sigma_a */
+    const double* B;         /* N frozen emission without gas coupling, NULL = 0 */
+    const double* S;         /* N source, NULL = none */
+    const double* rho_cv;    /* N, required with gas coupling */
+    const double* bE[3][2];  /* Dirichlet ghost data of each face, as m1_set_boundary (device) */
+    const double* bF[3][2];
+    const unsigned char* bmask[3][2];
+} m1_device_fields;
+
+/* R(U) of the backward-Euler step of size dt (same result as m1_residual for
+ * the same inputs) and its squared 2-norm into *norm2 (a device double; NULL
+ * = not wanted). U and R: n_u*N device doubles. */
+m1_status m1_residual_noalloc(const m1_grid_desc* desc, double dt, const m1_device_fields* fields,
+                              const double* U, double* R, double* norm2, void* cuda_stream);
+
 /* Message of the last failed call on this context (never NULL). */
 const char* m1_last_error(const m1_ctx* ctx);
 

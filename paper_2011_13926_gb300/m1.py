@@ -28,7 +28,7 @@ PRECOND_NONE, PRECOND_BJ = 0, 1
 EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "m1_set_state", "m1_get_state",
             "m1_get_solution", "m1_set_boundary", "m1_set_emission", "m1_set_source", "m1_explicit_step",
             "m1_implicit_step", "m1_residual", "m1_jv", "m1_diag_blocks", "m1_gmres_solve", "m1_stats",
-            "m1_profile", "m1_last_error"]
+            "m1_profile", "m1_last_error", "m1_residual_noalloc"]
 
 
 class GridDesc(C.Structure):
@@ -90,6 +90,16 @@ class Stats(C.Structure):
         return out
 
 
+NOALLOC_MAX_CELLS = 65536
+
+
+class DeviceFields(C.Structure):
+    """m1_device_fields: device pointers of one grid's inputs."""
+    _fields_ = [("Un", C.c_void_p), ("sigma_a", C.c_void_p), ("sigma_f", C.c_void_p), ("B", C.c_void_p),
+                ("S", C.c_void_p), ("rho_cv", C.c_void_p), ("bE", (C.c_void_p * 2) * 3),
+                ("bF", (C.c_void_p * 2) * 3), ("bmask", (C.c_void_p * 2) * 3)]
+
+
 _lib = None
 
 
@@ -122,6 +132,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_stats": (I, [P, C.POINTER(Stats)]),
         "m1_profile": (I, [P, I]),
         "m1_last_error": (C.c_char_p, [P]),
+        "m1_residual_noalloc": (I, [C.POINTER(GridDesc), D, C.POINTER(DeviceFields), P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -386,3 +397,11 @@ def context_from_problem(p, stream: Optional[int] = None, device: bool = False) 
         ctx.set_boundary(a, side, np.ascontiguousarray(Eg), np.ascontiguousarray(Fg),
                          None if mask is None else np.ascontiguousarray(mask))
     return ctx
+
+
+def residual_noalloc(desc: GridDesc, dt: float, fields: DeviceFields, U: int, R: int, norm2: int = 0,
+                     stream: int = 0) -> int:
+    """m1_residual_noalloc with raw device pointers; returns the status code
+    (asynchronous on ``stream``)."""
+    return load().m1_residual_noalloc(C.byref(desc), C.c_double(dt), C.byref(fields), C.c_void_p(U),
+                                      C.c_void_p(R), C.c_void_p(norm2 or None), C.c_void_p(stream or None))
