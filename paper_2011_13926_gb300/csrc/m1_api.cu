@@ -419,7 +419,7 @@ ArnoldiDev arnoldi_dev(m1_ctx* ctx) {
     ArnoldiDev K;
     K.n = ctx->n;
     K.ld = ctx->ld;
-    K.blocks = reduce_blocks();
+    K.blocks = 2 * 152;  // two resident blocks per SM, one wave
     K.H = ctx->sc.H;
     K.cs = ctx->sc.cs;
     K.sn = ctx->sc.sn;

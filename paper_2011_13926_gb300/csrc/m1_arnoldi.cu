@@ -105,7 +105,9 @@ __device__ __forceinline__ void setc(double2& v, int k, double x) {
     if (k == 0) v.x = x; else v.y = x;
 }
 
-template <class T>
+// JMAX accumulators per thread (the smallest bucket >= j + 1 is launched, so
+// early Arnoldi steps keep their registers low and their occupancy high)
+template <class T, int JMAX>
 __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const T* __restrict__ V,
                                                              const T* __restrict__ w, int j, int pass) {
     if (pass == 2 && *K.reorth == 0) return;
@@ -113,20 +115,41 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
     constexpr int W = Vec<T>::W;
     __shared__ double red[kArThreads / 32][kCols + 1];
     __shared__ bool last;
-    Acc<T> acc[kCols];
+    Acc<T> acc[JMAX];
     Acc<T> ww;
 #pragma unroll
-    for (int i = 0; i < kCols; ++i) acc[i].zero();
+    for (int i = 0; i < JMAX; ++i) acc[i].zero();
     ww.zero();
     const long long n = K.n, ld = K.ld;
     const long long nv = n / W;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += stride) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; q + stride < nv; q += 2 * stride) {  // two vectors in flight per row
+        const VT wa = reinterpret_cast<const VT*>(w)[q];
+        const VT wb = reinterpret_cast<const VT*>(w)[q + stride];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            ww.add_prod(comp(wa, k), comp(wa, k));
+            ww.add_prod(comp(wb, k), comp(wb, k));
+        }
+#pragma unroll
+        for (int i = 0; i < JMAX; ++i)
+            if (i <= j) {
+                const VT va = reinterpret_cast<const VT*>(V + i * ld)[q];
+                const VT vb = reinterpret_cast<const VT*>(V + i * ld)[q + stride];
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    acc[i].add_prod(comp(va, k), comp(wa, k));
+                    acc[i].add_prod(comp(vb, k), comp(wb, k));
+                }
+            }
+    }
+    for (; q < nv; q += stride) {
         const VT wv = reinterpret_cast<const VT*>(w)[q];
 #pragma unroll
         for (int k = 0; k < W; ++k) ww.add_prod(comp(wv, k), comp(wv, k));
 #pragma unroll
-        for (int i = 0; i < kCols; ++i)
+        for (int i = 0; i < JMAX; ++i)
             if (i <= j) {
                 const VT vv = reinterpret_cast<const VT*>(V + i * ld)[q];
 #pragma unroll
@@ -138,13 +161,13 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
             const T we = w[e];
             ww.add_prod(we, we);
 #pragma unroll
-            for (int i = 0; i < kCols; ++i)
+            for (int i = 0; i < JMAX; ++i)
                 if (i <= j) acc[i].add_prod(V[i * ld + e], we);
         }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < kCols; ++i) {
+    for (int i = 0; i < JMAX; ++i) {
         if (i <= j) {
             const double t = warp_sum_d(acc[i].get());
             if (lane == 0) red[wid][i] = t;
@@ -202,7 +225,7 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
     }
 }
 
-template <class T>
+template <class T, int JMAX>
 __global__ void __launch_bounds__(kArThreads) k_arnoldi_update(ArnoldiDev K, T* __restrict__ V, T* __restrict__ w,
                                                                int j, int pass) {
     const int reorth = *K.reorth;
@@ -220,10 +243,33 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_update(ArnoldiDev K, T* 
     const long long n = K.n, ld = K.ld;
     const long long nv = n / W;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += stride) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; q + stride < nv; q += 2 * stride) {  // two vectors in flight per row
+        VT xa = reinterpret_cast<const VT*>(w)[q];
+        VT xb = reinterpret_cast<const VT*>(w)[q + stride];
+#pragma unroll
+        for (int i = 0; i < JMAX; ++i)
+            if (i <= j) {
+                const VT va = reinterpret_cast<const VT*>(V + i * ld)[q];
+                const VT vb = reinterpret_cast<const VT*>(V + i * ld)[q + stride];
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    setc(xa, k, fma(-hs[i], comp(va, k), comp(xa, k)));
+                    setc(xb, k, fma(-hs[i], comp(vb, k), comp(xb, k)));
+                }
+            }
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            setc(xa, k, comp(xa, k) * inv);
+            setc(xb, k, comp(xb, k) * inv);
+        }
+        reinterpret_cast<VT*>(out)[q] = xa;
+        reinterpret_cast<VT*>(out)[q + stride] = xb;
+    }
+    for (; q < nv; q += stride) {
         VT x = reinterpret_cast<const VT*>(w)[q];
 #pragma unroll
-        for (int i = 0; i < kCols; ++i)
+        for (int i = 0; i < JMAX; ++i)
             if (i <= j) {
                 const VT vv = reinterpret_cast<const VT*>(V + i * ld)[q];
 #pragma unroll
@@ -237,25 +283,39 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_update(ArnoldiDev K, T* 
         for (long long e = nv * W + threadIdx.x; e < n; e += blockDim.x) {
             T x = w[e];
 #pragma unroll
-            for (int i = 0; i < kCols; ++i)
+            for (int i = 0; i < JMAX; ++i)
                 if (i <= j) x = fma(-hs[i], V[i * ld + e], x);
             out[e] = x * inv;
         }
     }
 }
 
-void launch_arnoldi_step_f64(const ArnoldiDev& K, double* V, double* w, int j, cudaStream_t s) {
+template <class T, int JMAX>
+static void arnoldi_pass(const ArnoldiDev& K, T* V, T* w, int j, int pass, cudaStream_t s) {
+    k_arnoldi_dots<T, JMAX><<<K.blocks, kArThreads, 0, s>>>(K, V, w, j, pass);
+    k_arnoldi_update<T, JMAX><<<K.blocks, kArThreads, 0, s>>>(K, V, w, j, pass);
+}
+
+template <class T>
+static void arnoldi_step(const ArnoldiDev& K, T* V, T* w, int j, cudaStream_t s) {
     for (int pass = 1; pass <= 2; ++pass) {
-        k_arnoldi_dots<double><<<K.blocks, kArThreads, 0, s>>>(K, V, w, j, pass);
-        k_arnoldi_update<double><<<K.blocks, kArThreads, 0, s>>>(K, V, w, j, pass);
+        if (j < 4)
+            arnoldi_pass<T, 4>(K, V, w, j, pass, s);
+        else if (j < 8)
+            arnoldi_pass<T, 8>(K, V, w, j, pass, s);
+        else if (j < 16)
+            arnoldi_pass<T, 16>(K, V, w, j, pass, s);
+        else
+            arnoldi_pass<T, kCols>(K, V, w, j, pass, s);
     }
 }
 
+void launch_arnoldi_step_f64(const ArnoldiDev& K, double* V, double* w, int j, cudaStream_t s) {
+    arnoldi_step<double>(K, V, w, j, s);
+}
+
 void launch_arnoldi_step_f32(const ArnoldiDev& K, float* V, float* w, int j, cudaStream_t s) {
-    for (int pass = 1; pass <= 2; ++pass) {
-        k_arnoldi_dots<float><<<K.blocks, kArThreads, 0, s>>>(K, V, w, j, pass);
-        k_arnoldi_update<float><<<K.blocks, kArThreads, 0, s>>>(K, V, w, j, pass);
-    }
+    arnoldi_step<float>(K, V, w, j, s);
 }
 
 }  // namespace m1
