@@ -55,7 +55,7 @@ typedef enum {
 typedef enum { M1_BC_OUTFLOW = 0, M1_BC_PERIODIC = 1, M1_BC_REFLECT = 2, M1_BC_DIRICHLET = 3 } m1_bc;
 typedef enum { M1_MEM_HOST = 0, M1_MEM_DEVICE = 1 } m1_mem;
 typedef enum { M1_PREC_FP64 = 0, M1_PREC_MIXED = 1 } m1_precision;
-typedef enum { M1_PRECOND_NONE = 0, M1_PRECOND_BJ = 1 } m1_precond;
+typedef enum { M1_PRECOND_NONE = 0, M1_PRECOND_BJ = 1, M1_PRECOND_LEARNED = 2 } m1_precond;
 
 /* Grid and discretisation flags (one context per grid). */
 typedef struct {
@@ -81,7 +81,7 @@ typedef struct {
     int gmres_max;        /* 3000 total Arnoldi iterations per linear solve */
     double gmres_rtol;    /* 1e-4: forcing term ||J d + R|| <= rtol ||R|| */
     int precision;        /* m1_precision: FP64, or FP32 inner FGMRES under FP64 refinement */
-    int precond;          /* m1_precond */
+    int precond;          /* m1_precond; M1_PRECOND_LEARNED needs M1_PREC_MIXED and m1_set_preconditioner */
     int line_search;      /* 1: halve theta up to 6 times until the Armijo decrease holds */
     int advance;          /* 1: on success U^n <- U^{n+1}; 0: keep U^n (result in m1_get_solution) */
     int refine_max;       /* mixed precision: max FP64 refinement sweeps per Newton step (4) */
@@ -177,6 +177,16 @@ m1_status m1_set_emission(m1_ctx* ctx, const double* B, m1_mem mem);
 /* External energy source S added to dE/dt (N doubles, NULL = none). */
 m1_status m1_set_source(m1_ctx* ctx, const double* S, m1_mem mem);
 
+/* Prescribed gas velocity on the faces (gas coupling only): u[a] holds the
+ * normal velocity of every face of axis a (N / n_a * (n_a + 1) doubles, the
+ * face index runs fastest along x as for cells, with n_a + 1 faces along a). */
+m1_status m1_set_velocity(m1_ctx* ctx, const double* ux, const double* uy, const double* uz, m1_mem mem);
+
+/* Explicit first-order upwind transport of the gas internal energy rho c_v T by
+ * the prescribed velocity over dt (the frozen-hydrodynamics step of the
+ * operator split of Sect. 3.2); updates T of the current state. */
+m1_status m1_advect(m1_ctx* ctx, double dt);
+
 /* One semi-implicit step of size dt (Sect. 3.1): HLL fluxes and alpha at time n,
  * backward-Euler exchange and flux source (tridiagonal WB solves along each
  * component's own axis, Appendix B form). Advances the state. */
@@ -212,6 +222,62 @@ m1_status m1_stats(const m1_ctx* ctx, m1_stats_t* out);
 /* Turn the per-kernel-class event timers on (1) or off (0) and reset them.
  * Timers add two event records per timed launch on the context's stream. */
 m1_status m1_profile(m1_ctx* ctx, int enable);
+
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner (not in the paper; the library's own addition).
+ *
+ * A 3-level 2D U-Net (63,443 parameters; 3x3 convolutions 4-16-16 | 16-32-32 |
+ * 32-32-32 | 64-32-16 | 32-16-3, ReLU, 2x2 average pooling, nearest 2x
+ * upsampling with skip concatenation) maps a Krylov vector v of a 2D
+ * radiation-only grid (channels E, F_x, F_y, scaled by s = ||v|| / sqrt(n)) and
+ * the normalised log opacity (log10(sigma_f dx) - 0.5) / 2.5 to a correction.
+ * As the right preconditioner of flexible GMRES it applies
+ *     z = J_bj^-1 v + s * N(v / s, log sigma),
+ * the point-block Jacobi result plus the learned correction. Weights are FP32
+ * masters with a BF16 copy; the forward pass uses the BF16 weights, FP32
+ * accumulation, BF16 activations in inference and FP32 activations in training.
+ * Tensors are NHWC float arrays: inputs B*H*W*4, outputs/targets B*H*W*3.
+ * ------------------------------------------------------------------------- */
+typedef struct m1_nn m1_nn;
+
+typedef struct {
+    int epochs;           /* passes over the pairs */
+    double lr;            /* Adam step size (beta1 0.9, beta2 0.999, eps 1e-8) */
+    double lr_decay;      /* lr *= lr_decay each epoch (0 or 1: constant) */
+    unsigned long long seed; /* shuffle seed (SplitMix64) */
+} m1_train_opts;
+
+typedef struct {
+    int steps;            /* Adam steps taken */
+    double first_loss, final_loss; /* batch loss of the first step, mean loss of the last epoch */
+} m1_train_info;
+
+size_t m1_nn_num_params(void);
+/* Network for batches of `batch` H x W images (H, W multiples of 4) on cuda_stream. */
+m1_status m1_nn_create(int H, int W, int batch, void* cuda_stream, m1_nn** out);
+m1_status m1_nn_destroy(m1_nn* nn);
+/* FP32 parameters in layer order (weights W[ky][kx][ci][co] then biases); resets Adam. */
+m1_status m1_nn_set_params(m1_nn* nn, const float* theta, m1_mem mem);
+m1_status m1_nn_get_params(const m1_nn* nn, float* theta, m1_mem mem);
+/* y = N(x) for one batch; bf16 = 1 stores activations in BF16 (inference path). */
+m1_status m1_nn_forward(m1_nn* nn, const float* x, float* y, int bf16, m1_mem mem);
+/* Loss (1/B) sum_b ||N(x_b) - t_b||^2 / ||t_b||^2 and its gradient (FP32 activations). */
+m1_status m1_nn_loss_grad(m1_nn* nn, const float* x, const float* t, double* loss, float* grad, m1_mem mem);
+/* Adam on npairs (x, t) pairs held as consecutive images; batches of the network's size. */
+m1_status m1_nn_train(m1_nn* nn, const float* X, const float* T, int npairs, const m1_train_opts* opts,
+                      m1_train_info* info, m1_mem mem);
+const char* m1_nn_last_error(const m1_nn* nn);
+
+/* One training pair from the context's own Jacobian (2D, radiation only):
+ * r = J(U) e (U NULL = the time-n state), s = ||r|| / sqrt(n), x = [r / s, log sigma]
+ * (NHWC, 4 channels), t = (e - J_bj(U)^-1 r) / s (NHWC, 3 channels): the part of
+ * the exact inverse that point-block Jacobi misses. */
+m1_status m1_nn_make_pair(m1_ctx* ctx, double dt, const double* U, const double* e, float* x, float* t,
+                          m1_mem mem);
+
+/* Attach (nn != NULL) or detach the learned preconditioner. The network must be
+ * built for batch 1 and the grid's n[1] x n[0]; the context does not own it. */
+m1_status m1_set_preconditioner(m1_ctx* ctx, m1_nn* nn);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free residual.

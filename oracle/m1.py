@@ -465,6 +465,24 @@ class Scheme:
         x = spla.spsolve(A.tocsc(), rhs.ravel())
         return x.reshape(self.shape)
 
+    # ------------------------------------------------------------ advection by the gas flow
+    def advect_internal_energy(self, u_faces):
+        """Explicit first-order upwind transport of e = rho c_v T by prescribed face
+        velocities (the frozen-hydrodynamics stand-in of the operator split of
+        Sect. 3.2, step 1): e* = e - dt sum_a (u e_up)_{+} - (u e_up)_{-} / dx_a,
+        e_up the upwind cell value (ghost rules of the state: copy / wrap).
+        Returns T* = e* / (rho c_v)."""
+        p, d = self.p, self.d
+        e = p.rho_cv * self.Un[1 + d]
+        div = 0.0
+        for a in range(d):
+            ep = self.pad_sigma(e, a)  # copy (outflow/reflect/Dirichlet) or wrap (periodic)
+            eL, eR = self.LR(ep, a)
+            u = np.asarray(u_faces[a])
+            flux = np.where(u > 0.0, u * eL, u * eR)
+            div = div + self.diff(flux, a) / self.dx[a]
+        return (e - self.dt * div) / p.rho_cv
+
     # ------------------------------------------------------------ diagnostics
     def realizability_violations(self, u) -> int:
         """Number of cells with |F| > c E (admissibility is not guaranteed, Sect. 3.1.3)."""

@@ -74,6 +74,11 @@ struct m1_ctx {
     double *blocks = nullptr, *binv = nullptr;
     float *binv32 = nullptr, *V32 = nullptr, *w32 = nullptr, *z32 = nullptr, *U32 = nullptr, *tmp32 = nullptr;
     double *Fstar = nullptr, *linework = nullptr;
+    m1_nn* nn = nullptr;        // learned preconditioner (not owned)
+    float* logsig = nullptr;    // its opacity channel
+    float* Z32 = nullptr;       // flexible-GMRES basis of preconditioned vectors
+    float *pair_x = nullptr, *pair_t = nullptr;  // staging of one training pair (4N and 3N floats)
+    double* vel[3] = {nullptr, nullptr, nullptr};  // prescribed face velocities (gas advection)
     double* partials = nullptr;
     double* ar_partials = nullptr;
     unsigned* ar_counter = nullptr;
@@ -290,6 +295,8 @@ m1_status refresh(m1_ctx* ctx) {
                 launch_f64_to_f32(ctx->bF[a][sd], ctx->bF32[a][sd], ctx->bM[a] * ctx->dim, ctx->s);
             }
     }
+    if (ctx->nn && ctx->logsig)
+        launch_logsig(ctx->sig_f, N, (ctx->d.hi[0] - ctx->d.lo[0]) / ctx->d.n[0], ctx->logsig, ctx->s);
     }
     ctx->dirty = false;
     return sync(ctx);
@@ -398,6 +405,7 @@ struct Ops32 {
     Dev<float> g;
     const float* U;
     bool precond;
+    bool learned = false;
     void A(const float* in, float* out) {
         TK t(ctx, M1_K_JV32);
         launch_jv_f32(g, U, in, out, ctx->s);
@@ -412,6 +420,10 @@ struct Ops32 {
             cudaMemcpyAsync(out, in, sizeof(float) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s);
         }
         count(ctx, 1);
+        if (learned) {  // + s N(v / s): the Krylov vectors have unit norm, s = 1 / sqrt(n)
+            nn_apply_add(ctx->nn, in, ctx->N, ctx->logsig, (float)(1.0 / sqrt((double)ctx->n)), out, ctx->s);
+            count(ctx, 24);
+        }
     }
 };
 
@@ -483,7 +495,7 @@ inline void norm2(const float* x, long long n, double* p, double* out, cudaStrea
 // residual estimate |g_k|.
 template <class T, class Ops>
 m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, double beta, double target, int maxk,
-                      int* kout, double* est) {
+                      int* kout, double* est, T* Z = nullptr) {
     const long long n = ctx->n;
     cudaStream_t s = ctx->s;
     const Scal& sc = ctx->sc;
@@ -497,8 +509,9 @@ m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, doub
     const long long ld = ctx->ld;
     for (int j = 0; j < maxk; ++j) {
         T* Vj = V + (long long)j * ld;
-        ops.M(Vj, z);
-        ops.A(z, w);
+        T* zj = Z ? Z + (long long)j * ld : z;  // flexible GMRES keeps every preconditioned vector
+        ops.M(Vj, zj);
+        ops.A(zj, w);
         {
             TK t(ctx, M1_K_ORTHO);
             arnoldi_step(arnoldi_dev(ctx), V, w, j, s);
@@ -517,7 +530,7 @@ m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, doub
     }
     launch_backsolve(sc.H, sc.g, k, sc.y, s);
     CK(cudaMemsetAsync(ctx->tmp, 0, sizeof(double) * n, s));
-    lincomb_add(V, ld, k, sc.y, ctx->tmp, n, s);
+    lincomb_add(Z ? Z : V, ld, k, sc.y, ctx->tmp, n, s);  // flexible: tmp = Z y, else V y
     count(ctx, 2);
     *kout = k;
     *est = e;
@@ -577,6 +590,7 @@ m1_status gmres64(m1_ctx* ctx, Ops64& ops, const double* b, double* x, double rt
 m1_status gmres_mixed(m1_ctx* ctx, Ops64& ops64, Ops32& ops32, const double* b, double* x, double rtol,
                       int restart, int maxit, int refine_max, int* iters, int* refinements, double* bnorm_out,
                       double* res_out, bool* conv) {
+    const bool flexible = ops32.learned;
     const long long n = ctx->n;
     cudaStream_t s = ctx->s;
     double bnorm;
@@ -631,10 +645,14 @@ m1_status gmres_mixed(m1_ctx* ctx, Ops64& ops64, Ops32& ops32, const double* b, 
             double est;
             const int maxk = std::min(restart, maxit - *iters);
             CKS(gmres_cycle<float>(ctx, ops32, ctx->V32, ctx->z32 /*w*/, ctx->tmp32 /*z*/, ctx->tmp32, beta,
-                                   inner_rtol, maxk, &k, &est));
+                                   inner_rtol, maxk, &k, &est, flexible ? ctx->Z32 : nullptr));
             *iters += k;
-            ops64.M(ctx->tmp, ctx->z);
-            launch_axpy_f64(1.0, ctx->z, ctx->xacc, n, s);
+            if (flexible) {  // tmp = Z y already holds the preconditioned combination
+                launch_axpy_f64(1.0, ctx->tmp, ctx->xacc, n, s);
+            } else {
+                ops64.M(ctx->tmp, ctx->z);
+                launch_axpy_f64(1.0, ctx->z, ctx->xacc, n, s);
+            }
             count(ctx, 1);
         }
         // x += ||r|| xacc ; r = b - J64 x
@@ -828,7 +846,7 @@ m1_status m1_destroy(m1_ctx* ctx) {
                     ctx->delta, ctx->rhs, ctx->w, ctx->z, ctx->tmp, ctx->V, ctx->xacc, ctx->blocks, ctx->binv,
                     ctx->binv32, ctx->V32, ctx->w32, ctx->z32, ctx->U32, ctx->tmp32, ctx->Fstar, ctx->linework,
                     ctx->partials, ctx->scal_base, ctx->singular, ctx->viol, ctx->ar_partials,
-                    ctx->ar_counter, ctx->ar_reorth};
+                    ctx->ar_counter, ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int a = 0; a < 3; ++a) {
@@ -842,6 +860,8 @@ m1_status m1_destroy(m1_ctx* ctx) {
                 if (q) cudaFree(q);
         }
     }
+    for (int a = 0; a < 3; ++a)
+        if (ctx->vel[a]) cudaFree(ctx->vel[a]);
     if (ctx->hpin) cudaFreeHost(ctx->hpin);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -948,6 +968,36 @@ m1_status m1_set_source(m1_ctx* ctx, const double* S, m1_mem mem) {
     return sync(ctx);
 }
 
+m1_status m1_set_velocity(m1_ctx* ctx, const double* ux, const double* uy, const double* uz, m1_mem mem) {
+    if (!ctx) return M1_ERR_ARG;
+    if (!ctx->d.gas_coupling) return fail(ctx, M1_ERR_ARG, "advection needs gas coupling");
+    const double* u[3] = {ux, uy, uz};
+    for (int a = 0; a < ctx->dim; ++a) {
+        if (!u[a]) return fail(ctx, M1_ERR_ARG, "a velocity component is missing");
+        CKS(dalloc(ctx, &ctx->vel[a], ctx->nfaces[a]));
+        CKS(copy_in(ctx, ctx->vel[a], u[a], sizeof(double) * ctx->nfaces[a], mem));
+    }
+    return sync(ctx);
+}
+
+m1_status m1_advect(m1_ctx* ctx, double dt) {
+    if (!ctx) return M1_ERR_ARG;
+    if (!(dt > 0.0)) return fail(ctx, M1_ERR_ARG, "dt must be positive");
+    if (!ctx->vel[0]) return fail(ctx, M1_ERR_STATE, "no velocity: call m1_set_velocity");
+    CKS(prepare(ctx));
+    Dev<double> g = dev64(ctx, dt);
+    double* Tn = ctx->Un + (1 + ctx->dim) * ctx->N;
+    double* Tnew = ctx->Unew + (1 + ctx->dim) * ctx->N;
+    {
+        TK t(ctx, M1_K_EXPLICIT);
+        launch_advect(g, ctx->vel, Tnew, ctx->s);
+        count(ctx, 1);
+    }
+    CK(cudaMemcpyAsync(Tn, Tnew, sizeof(double) * ctx->N, cudaMemcpyDeviceToDevice, ctx->s));
+    ctx->dirty = true;
+    return sync(ctx);
+}
+
 m1_status m1_explicit_step(m1_ctx* ctx, double dt) {
     if (!ctx) return M1_ERR_ARG;
     if (!(dt > 0.0)) return fail(ctx, M1_ERR_ARG, "dt must be positive");
@@ -1021,9 +1071,13 @@ m1_status m1_diag_blocks(m1_ctx* ctx, double dt, const double* U, double* blocks
 static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const double* b, double* x,
                               const m1_solver_opts* o, int* iters, int* refinements, double* bnorm, double* res,
                               bool* conv) {
-    const bool pre = o->precond == M1_PRECOND_BJ;
+    const bool learned = o->precond == M1_PRECOND_LEARNED;
+    const bool pre = o->precond == M1_PRECOND_BJ || learned;
     if (o->restart < 1 || o->restart > kMaxRestart)
         return fail(ctx, M1_ERR_ARG, "restart must be in [1, 30]");
+    if (learned && (o->precision != M1_PREC_MIXED || !ctx->nn))
+        return fail(ctx, M1_ERR_ARG, "the learned preconditioner needs M1_PREC_MIXED and m1_set_preconditioner");
+    if (learned) CKS(dalloc(ctx, &ctx->Z32, (size_t)ctx->ld * (kMaxRestart + 1)));
     Dev<double> g = dev64(ctx, dt);
     Ops64 ops{ctx, g, Ud, pre};
     *refinements = 0;
@@ -1042,6 +1096,7 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
             ctx->st.precond_builds++;
         }
         Ops32 ops32{ctx, g32, ctx->U32, pre};
+        ops32.learned = learned;
         return gmres_mixed(ctx, ops, ops32, b, x, o->gmres_rtol, o->restart, o->gmres_max, o->refine_max, iters,
                            refinements, bnorm, res, conv);
     }
@@ -1171,6 +1226,64 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
     if (result != M1_OK) return result;
     if (!inf.converged) return fail(ctx, M1_ERR_NOT_CONVERGED, "Newton did not converge");
     return M1_OK;
+}
+
+m1_status m1_set_preconditioner(m1_ctx* ctx, m1_nn* nn) {
+    if (!ctx) return M1_ERR_ARG;
+    if (!nn) {
+        ctx->nn = nullptr;
+        return M1_OK;
+    }
+    if (ctx->dim != 2 || ctx->d.gas_coupling)
+        return fail(ctx, M1_ERR_ARG, "the learned preconditioner is 2D radiation-only");
+    if (nn_height(nn) != ctx->d.n[1] || nn_width(nn) != ctx->d.n[0])
+        return fail(ctx, M1_ERR_ARG, "network size differs from the grid (build it for n[1] x n[0], batch 1)");
+    CKS(dalloc(ctx, &ctx->logsig, ctx->N));
+    ctx->nn = nn;
+    ctx->dirty = true;
+    return M1_OK;
+}
+
+m1_status m1_nn_make_pair(m1_ctx* ctx, double dt, const double* U, const double* e, float* x, float* t,
+                          m1_mem mem) {
+    if (!ctx || !e || !x || !t) return M1_ERR_ARG;
+    if (ctx->dim != 2 || ctx->d.gas_coupling) return fail(ctx, M1_ERR_ARG, "pairs are 2D radiation-only");
+    CKS(dalloc(ctx, &ctx->logsig, ctx->N));
+    CKS(prepare(ctx));
+    CKS(ensure_work(ctx));
+    launch_logsig(ctx->sig_f, ctx->N, (ctx->d.hi[0] - ctx->d.lo[0]) / ctx->d.n[0], ctx->logsig, ctx->s);
+    if (U)
+        CKS(copy_in(ctx, ctx->U, U, sizeof(double) * ctx->n, mem));
+    else
+        CK(cudaMemcpyAsync(ctx->U, ctx->Un, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s));
+    CKS(copy_in(ctx, ctx->delta, e, sizeof(double) * ctx->n, mem));
+    Dev<double> g = dev64(ctx, dt);
+    launch_jv_f64(g, ctx->U, ctx->delta, ctx->w, ctx->s);  // r = J e
+    CKS(build_precond(ctx, g, ctx->U));
+    launch_bj_apply_f64(ctx->nu, ctx->N, ctx->binv, ctx->w, ctx->z, ctx->s);  // J_bj^-1 r
+    launch_axpby_f64(1.0, ctx->delta, -1.0, ctx->z, ctx->tmp, ctx->n, ctx->s);  // e - J_bj^-1 r
+    count(ctx, 4);
+    double rn;
+    CKS(norm_f64(ctx, ctx->w, &rn));
+    const double scale = rn > 0.0 ? rn / sqrt((double)ctx->n) : 1.0;
+    float* xd = nullptr;
+    float* td = nullptr;
+    if (mem == M1_MEM_DEVICE) {
+        xd = x;
+        td = t;
+    } else {
+        CKS(dalloc(ctx, &ctx->pair_x, 4 * ctx->N));
+        CKS(dalloc(ctx, &ctx->pair_t, 3 * ctx->N));
+        xd = ctx->pair_x;
+        td = ctx->pair_t;
+    }
+    launch_pack_pair(ctx->w, ctx->tmp, ctx->N, ctx->logsig, scale, xd, td, ctx->s);
+    count(ctx, 1);
+    if (mem != M1_MEM_DEVICE) {
+        CK(cudaMemcpyAsync(x, xd, sizeof(float) * 4 * ctx->N, cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaMemcpyAsync(t, td, sizeof(float) * 3 * ctx->N, cudaMemcpyDeviceToHost, ctx->s));
+    }
+    return sync(ctx);
 }
 
 m1_status m1_profile(m1_ctx* ctx, int enable) {

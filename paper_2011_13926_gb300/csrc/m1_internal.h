@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/m1.h"
 #include "m1_device.cuh"
 
 namespace m1 {
@@ -33,6 +34,8 @@ void launch_explicit_hyp(const Dev<double>& g, double* Unew, double* Fstar, cuda
 void launch_wb_lines(const Dev<double>& g, int b, const double* Fstar, double* Fout, double* work,
                      cudaStream_t s);
 int stencil_blocks(long long N);
+// upwind transport of rho c_v T by face velocities u[a] (gas coupling): T* into Tout
+void launch_advect(const Dev<double>& g, const double* const u[3], double* Tout, cudaStream_t s);
 
 // ----------------------------------------------------------------- Arnoldi (m1_arnoldi.cu)
 // device scalars and scratch of one fused Arnoldi step (CGS with selective
@@ -86,5 +89,14 @@ void launch_backsolve(const double* H, const double* g, int k, double* y, cudaSt
 // count cells with |F| > c E and non-finite entries
 void launch_realizability(const double* U, int dim, long long N, double c, unsigned long long* count,
                           cudaStream_t s);
+
+// ----------------------------------------------------------------- learned preconditioner (m1_unet.cu)
+m1_status nn_apply_add(m1_nn* nn, const float* v, long long N, const float* logsig, float scale, float* z,
+                       cudaStream_t s);
+int nn_height(const m1_nn* nn);
+int nn_width(const m1_nn* nn);
+void launch_logsig(const double* sig, long long N, double dx, float* out, cudaStream_t s);
+void launch_pack_pair(const double* r, const double* tt, long long N, const float* logsig, double scale, float* x,
+                      float* t, cudaStream_t s);
 
 }  // namespace m1

@@ -143,6 +143,142 @@ __global__ void __launch_bounds__(kThreads) k_jv(Dev<R> g, const R* __restrict__
     for (int k = 0; k < NU; ++k) Jv[k * g.N + idx] = out[k].d;
 }
 
+// ------------------------------------------------------------------ J v, 2D tiled
+// 2D J v with the closure of every cell computed once per CTA: a 32 x 8 tile
+// plus a one-cell halo (axis neighbours only; ghosts by the boundary rules) is
+// staged in shared memory as dual numbers (E, F, P), then each thread forms
+// its four HLL faces and sources. For frozen (time-n) or fixed wave speeds.
+constexpr int kTX = 32, kTY = 8;
+
+template <class R>
+struct CellD {
+    Dual<R> E, Fx, Fy, Pxx, Pxy, Pyy;
+};
+
+template <class R, bool GAS>
+__global__ void __launch_bounds__(kTX* kTY) k_jv2d_tiled(Dev<R> g, const R* __restrict__ U, const R* __restrict__ v,
+                                                        R* __restrict__ Jv) {
+    __shared__ CellD<R> cs[kTY + 2][kTX + 2];
+    const int nx = g.n[0], ny = g.n[1];
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    LoadDir<R> ld{U, v, g.N};
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    for (int t = tid; t < (kTX + 2) * (kTY + 2); t += kTX * kTY) {
+        const int hx = t % (kTX + 2), hy = t / (kTX + 2);
+        int gx = x0 + hx - 1, gy = y0 + hy - 1;
+        const bool in_x = gx >= 0 && gx < nx, in_y = gy >= 0 && gy < ny;
+        if (!(in_x || in_y)) continue;              // corner: no face needs it
+        if (gx > nx || gy > ny) continue;           // beyond the last ghost of a ragged tile
+        if ((hx == 0 || hx == kTX + 1) && (hy == 0 || hy == kTY + 1)) continue;  // tile corners
+        St<Dual<R>, 2> u;
+        if (in_x && in_y) {
+            const long long idx = (long long)gy * nx + gx;
+            u = load_state<Dual<R>, 2, false>(ld, idx, idx);
+        } else {
+            // ghost of the adjacent boundary cell along the axis that left the domain
+            const int a = in_x ? 1 : 0;
+            const int side = a == 0 ? (gx < 0 ? 0 : 1) : (gy < 0 ? 0 : 1);
+            int cc[3] = {a == 0 ? (gx < 0 ? 0 : nx - 1) : gx, a == 1 ? (gy < 0 ? 0 : ny - 1) : gy, 0};
+            const long long idx = (long long)cc[1] * nx + cc[0];
+            const St<Dual<R>, 2> self = load_state<Dual<R>, 2, false>(ld, idx, idx);
+            R sig_nb;
+            bool bnd;
+            u = neighbour<Dual<R>, 2, false>(g, ld, self, idx, cc, a, side, sig_nb, bnd);
+        }
+        const Cl<Dual<R>, 2> k = closure(u, g.c);
+        CellD<R> c;
+        c.E = u.E;
+        c.Fx = u.F[0];
+        c.Fy = u.F[1];
+        c.Pxx = pressure(k, 0, 0);
+        c.Pxy = pressure(k, 0, 1);
+        c.Pyy = pressure(k, 1, 1);
+        cs[hy][hx] = c;
+    }
+    __syncthreads();
+    const int ix = x0 + threadIdx.x, iy = y0 + threadIdx.y;
+    if (ix >= nx || iy >= ny) return;
+    const long long idx = (long long)iy * nx + ix;
+    const int coord[3] = {ix, iy, 0};
+    const CellD<R>& me = cs[threadIdx.y + 1][threadIdx.x + 1];
+    const R sig_self = g.sig_f[idx];
+    const R dt = g.dt, c = g.c, c2 = g.c * g.c;
+    Dual<R> RE = me.E, RFx = me.Fx, RFy = me.Fy;  // the identity part of J (U - U^n)
+    Dual<R> phi[2] = {cst<Dual<R>>(R(0)), cst<Dual<R>>(R(0))};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int hx = threadIdx.x + 1 + (a == 0 ? (side ? 1 : -1) : 0);
+            const int hy = threadIdx.y + 1 + (a == 1 ? (side ? 1 : -1) : 0);
+            const CellD<R>& nb = cs[hy][hx];
+            const CellD<R>& L = side ? me : nb;
+            const CellD<R>& Rr = side ? nb : me;
+            const int ca = coord[a] + (side ? 1 : -1);
+            const bool inside = ca >= 0 && ca < g.n[a];
+            const bool periodic = g.bc[a][side] == BC_PERIODIC;
+            const bool boundary = !inside && !periodic;
+            R sig_nb = sig_self;
+            if (inside)
+                sig_nb = g.sig_f[idx + (side ? g.stride[a] : -g.stride[a])];
+            else if (periodic)
+                sig_nb = g.sig_f[idx + (side ? -(long long)(g.n[a] - 1) : (long long)(g.n[a] - 1)) * g.stride[a]];
+            const long long fidx = face_index(g.n, coord, a, coord[a] + side);
+            R lp, lm;
+            if (g.fixed_eigs) {
+                lp = c;
+                lm = -c;
+            } else {
+                lp = g.lam_p[a][fidx];
+                lm = g.lam_m[a][fidx];
+            }
+            const R den = lp - lm;
+            const R inv = den >= Tiny<R>::den() ? R(1) / den : R(0);
+            const R pm = lp * lm * inv;
+            const Dual<R> FaL = a == 0 ? L.Fx : L.Fy, FaR = a == 0 ? Rr.Fx : Rr.Fy;
+            const Dual<R> Fs = (lp * FaL - lm * FaR) * inv + pm * (Rr.E - L.E);
+            // P*_b = c^2 (lp P_ab,L - lm P_ab,R) inv + pm (F_b,R - F_b,L)
+            const Dual<R> PaxL = a == 0 ? L.Pxx : L.Pxy, PaxR = a == 0 ? Rr.Pxx : Rr.Pxy;
+            const Dual<R> PayL = a == 0 ? L.Pxy : L.Pyy, PayR = a == 0 ? Rr.Pxy : Rr.Pyy;
+            const Dual<R> Psx = c2 * (lp * PaxL - lm * PaxR) * inv + pm * (Rr.Fx - L.Fx);
+            const Dual<R> Psy = c2 * (lp * PayL - lm * PayR) * inv + pm * (Rr.Fy - L.Fy);
+            const R w = (side ? dt : -dt) * g.inv_dx[a];
+            RE = RE + (w * g.alpha[a][fidx]) * Fs;
+            RFx = RFx + w * Psx;
+            RFy = RFy + w * Psy;
+            if (g.wb) {
+                if (boundary && g.wb_boundary) {
+                    const Dual<R> PR = a == 0 ? Rr.Pxx : Rr.Pyy, PL = a == 0 ? L.Pxx : L.Pyy;
+                    phi[a] = phi[a] - c * g.inv_dx[a] * (PR - PL);
+                } else {
+                    phi[a] = phi[a] + (R(0.25) * (sig_self + sig_nb)) * (FaL + FaR);
+                }
+            }
+        }
+    }
+    const R cdt = c * dt;
+    if (g.wb) {
+        RFx = RFx + cdt * (R(0.5) * phi[0]);
+        RFy = RFy + cdt * (R(0.5) * phi[1]);
+    } else {
+        RFx = RFx + cdt * (sig_self * me.Fx);
+        RFy = RFy + cdt * (sig_self * me.Fy);
+    }
+    const R ka = cdt * g.sig_a[idx];
+    if constexpr (GAS) {
+        const Dual<R> T = ld.get(3, idx, idx);
+        const Dual<R> T2 = T * T;
+        const Dual<R> exch = ka * (g.a_r * (T2 * T2) - me.E);
+        RE = RE - exch;
+        Jv[3 * g.N + idx] = (g.rho_cv[idx] * T + exch).d;
+    } else {
+        RE = RE + ka * me.E;  // -c sigma_a dt (B - E): only E varies
+    }
+    Jv[idx] = RE.d;
+    Jv[g.N + idx] = RFx.d;
+    Jv[2 * g.N + idx] = RFy.d;
+}
+
 // ------------------------------------------------------------------ point blocks
 template <class R, int DIM, bool GAS>
 __global__ void __launch_bounds__(kThreads) k_diag(Dev<R> g, const R* __restrict__ U, R* __restrict__ blocks) {
@@ -192,7 +328,19 @@ void launch_residual_f64(const Dev<double>& g, const double* U, double* R, doubl
 #undef CALL
 }
 
+template <class R>
+static bool jv_tiled(const Dev<R>& g, const R* U, const R* v, R* Jv, cudaStream_t s) {
+    if (g.dim != 2 || (g.implicit_eigs && !g.fixed_eigs)) return false;
+    dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
+    if (g.gas)
+        k_jv2d_tiled<R, true><<<grid, block, 0, s>>>(g, U, v, Jv);
+    else
+        k_jv2d_tiled<R, false><<<grid, block, 0, s>>>(g, U, v, Jv);
+    return true;
+}
+
 void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s) {
+    if (jv_tiled(g, U, v, Jv, s)) return;
     const int nb = stencil_blocks(g.N);
 #define CALL(D, G) k_jv<double, D, G><<<nb, kThreads, 0, s>>>(g, U, v, Jv)
     M1_DISPATCH(g.dim, g.gas, CALL);
@@ -200,6 +348,7 @@ void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, doubl
 }
 
 void launch_jv_f32(const Dev<float>& g, const float* U, const float* v, float* Jv, cudaStream_t s) {
+    if (jv_tiled(g, U, v, Jv, s)) return;
     const int nb = stencil_blocks(g.N);
 #define CALL(D, G) k_jv<float, D, G><<<nb, kThreads, 0, s>>>(g, U, v, Jv)
     M1_DISPATCH(g.dim, g.gas, CALL);
@@ -414,6 +563,50 @@ void launch_explicit_hyp(const Dev<double>& g, double* Unew, double* Fstar, cuda
 #define CALL(D, G) k_explicit_hyp<D, G><<<nb, kThreads, 0, s>>>(g, Unew, Fstar)
     M1_DISPATCH(g.dim, g.gas, CALL);
 #undef CALL
+}
+
+// Explicit first-order upwind transport of the gas internal energy e = rho c_v T
+// by prescribed face velocities (frozen-hydrodynamics step of the operator
+// split): e* = e - dt sum_a ((u e_up)_{+} - (u e_up)_{-}) / dx_a, ghosts copy
+// the boundary cell (wrap when periodic). Writes T* into Tout.
+template <int DIM>
+__global__ void k_advect(Dev<double> g, const double* __restrict__ u0, const double* __restrict__ u1,
+                         const double* __restrict__ u2, double* __restrict__ Tout) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    int coord[3];
+    cell_coord(idx, g.n[0], g.n[1], coord);
+    const double* Tn = g.Un + (1 + DIM) * g.N;
+    const double e = g.rho_cv[idx] * Tn[idx];
+    const double* uf[3] = {u0, u1, u2};
+    double div = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int ca = coord[a] + (side ? 1 : -1);
+            long long j = idx;
+            if (ca >= 0 && ca < g.n[a])
+                j = idx + (side ? g.stride[a] : -g.stride[a]);
+            else if (g.bc[a][side] == BC_PERIODIC)
+                j = idx + (side ? -(long long)(g.n[a] - 1) : (long long)(g.n[a] - 1)) * g.stride[a];
+            const double en = g.rho_cv[j] * Tn[j];
+            const double u = uf[a][face_index(g.n, coord, a, coord[a] + side)];
+            const double eL = side ? e : en, eR = side ? en : e;
+            const double flux = u > 0.0 ? u * eL : u * eR;
+            div += (side ? flux : -flux) * g.inv_dx[a];
+        }
+    }
+    Tout[idx] = (e - g.dt * div) / g.rho_cv[idx];
+}
+
+void launch_advect(const Dev<double>& g, const double* const u[3], double* Tout, cudaStream_t s) {
+    const int nb = stencil_blocks(g.N);
+    switch (g.dim) {
+        case 1: k_advect<1><<<nb, kThreads, 0, s>>>(g, u[0], u[1], u[2], Tout); break;
+        case 2: k_advect<2><<<nb, kThreads, 0, s>>>(g, u[0], u[1], u[2], Tout); break;
+        default: k_advect<3><<<nb, kThreads, 0, s>>>(g, u[0], u[1], u[2], Tout); break;
+    }
 }
 
 // One thread per grid line along axis b: solve (I + c dt W_b) F_b = F*_b, the

@@ -23,12 +23,15 @@ STATUS_NAMES = ["M1_OK", "M1_ERR_ARG", "M1_ERR_CUDA", "M1_ERR_NOMEM", "M1_ERR_NO
 BC = {"outflow": 0, "periodic": 1, "reflect": 2, "dirichlet": 3}
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
-PRECOND_NONE, PRECOND_BJ = 0, 1
+PRECOND_NONE, PRECOND_BJ, PRECOND_LEARNED = 0, 1, 2
 
 EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "m1_set_state", "m1_get_state",
             "m1_get_solution", "m1_set_boundary", "m1_set_emission", "m1_set_source", "m1_explicit_step",
             "m1_implicit_step", "m1_residual", "m1_jv", "m1_diag_blocks", "m1_gmres_solve", "m1_stats",
-            "m1_profile", "m1_last_error", "m1_residual_noalloc"]
+            "m1_profile", "m1_last_error", "m1_residual_noalloc", "m1_nn_num_params", "m1_nn_create",
+            "m1_nn_destroy", "m1_nn_set_params", "m1_nn_get_params", "m1_nn_forward", "m1_nn_loss_grad",
+            "m1_nn_train", "m1_nn_last_error", "m1_nn_make_pair", "m1_set_preconditioner", "m1_set_velocity",
+            "m1_advect"]
 
 
 class GridDesc(C.Structure):
@@ -93,6 +96,17 @@ class Stats(C.Structure):
 NOALLOC_MAX_CELLS = 65536
 
 
+class TrainOpts(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("lr", C.c_double), ("lr_decay", C.c_double), ("seed", C.c_ulonglong)]
+
+
+class TrainInfo(C.Structure):
+    _fields_ = [("steps", C.c_int), ("first_loss", C.c_double), ("final_loss", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class DeviceFields(C.Structure):
     """m1_device_fields: device pointers of one grid's inputs."""
     _fields_ = [("Un", C.c_void_p), ("sigma_a", C.c_void_p), ("sigma_f", C.c_void_p), ("B", C.c_void_p),
@@ -133,6 +147,19 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_profile": (I, [P, I]),
         "m1_last_error": (C.c_char_p, [P]),
         "m1_residual_noalloc": (I, [C.POINTER(GridDesc), D, C.POINTER(DeviceFields), P, P, P, P]),
+        "m1_nn_num_params": (C.c_size_t, []),
+        "m1_nn_create": (I, [I, I, I, P, C.POINTER(P)]),
+        "m1_nn_destroy": (I, [P]),
+        "m1_nn_set_params": (I, [P, P, I]),
+        "m1_nn_get_params": (I, [P, P, I]),
+        "m1_nn_forward": (I, [P, P, P, I, I]),
+        "m1_nn_loss_grad": (I, [P, P, P, C.POINTER(D), P, I]),
+        "m1_nn_train": (I, [P, P, P, I, C.POINTER(TrainOpts), C.POINTER(TrainInfo), I]),
+        "m1_nn_last_error": (C.c_char_p, [P]),
+        "m1_nn_make_pair": (I, [P, D, P, P, P, P, I]),
+        "m1_set_preconditioner": (I, [P, P]),
+        "m1_set_velocity": (I, [P, P, P, P, I]),
+        "m1_advect": (I, [P, D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -167,7 +194,7 @@ def _ptr(x, dtype=np.float64, allow_none=True):
     try:
         import torch
         if isinstance(x, torch.Tensor):
-            want = torch.float64 if dtype == np.float64 else torch.uint8
+            want = {np.float64: torch.float64, np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
             if x.dtype != want:
                 raise TypeError(f"expected {want}, got {x.dtype}")
             if not x.is_contiguous():
@@ -331,6 +358,32 @@ class Context:
             raise M1Error(st, self.last_error())
         return out, info
 
+    def set_velocity(self, ux, uy=None, uz=None):
+        ps = [_ptr(u) for u in (ux, uy, uz)]
+        self._call("m1_set_velocity", ps[0][0], ps[1][0], ps[2][0],
+                   _check_mem(*[q[1] for q in ps if q[0] is not None]))
+
+    def advect(self, dt: float):
+        self._call("m1_advect", C.c_double(dt))
+
+    def set_preconditioner(self, net):
+        self._call("m1_set_preconditioner", net.h if net is not None else None)
+        self._net = net  # keep the network alive while attached
+
+    def make_pair(self, dt: float, e, U=None, out=None):
+        """(x, t) NHWC float32 training pair from this context's Jacobian."""
+        pe, me, ke = _ptr(e)
+        pu, mu, ku = _ptr(U)
+        if out is None:
+            x = np.empty(4 * self.N, dtype=np.float32)
+            t = np.empty(3 * self.N, dtype=np.float32)
+        else:
+            x, t = out
+        px, mx, kx = _ptr(x, dtype=np.float32)
+        pt, mt, kt = _ptr(t, dtype=np.float32)
+        self._call("m1_nn_make_pair", C.c_double(dt), pu, pe, px, pt, _check_mem(me, mu if pu else None, mx, mt))
+        return x, t
+
     def profile(self, enable: bool = True):
         self._call("m1_profile", int(bool(enable)))
 
@@ -405,3 +458,71 @@ def residual_noalloc(desc: GridDesc, dt: float, fields: DeviceFields, U: int, R:
     (asynchronous on ``stream``)."""
     return load().m1_residual_noalloc(C.byref(desc), C.c_double(dt), C.byref(fields), C.c_void_p(U),
                                       C.c_void_p(R), C.c_void_p(norm2 or None), C.c_void_p(stream or None))
+
+
+class Net:
+    """m1_nn: the learned preconditioner network (batches of H x W images)."""
+
+    def __init__(self, H: int, W: int, batch: int = 1, stream: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.m1_nn_create(H, W, batch, C.c_void_p(stream or None), C.byref(h))
+        if st != M1_OK:
+            raise M1Error(st, "m1_nn_create failed")
+        self.h, self.H, self.W, self.B = h, H, W, batch
+        self.nparams = int(self.lib.m1_nn_num_params())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.m1_nn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, *args):
+        st = getattr(self.lib, name)(self.h, *args)
+        if st != M1_OK:
+            raise M1Error(st, self.lib.m1_nn_last_error(self.h).decode())
+
+    def set_params(self, theta):
+        p, m, k = _ptr(theta, dtype=np.float32)
+        self._call("m1_nn_set_params", p, m)
+
+    def get_params(self):
+        out = np.empty(self.nparams, dtype=np.float32)
+        self._call("m1_nn_get_params", out.ctypes.data, MEM_HOST)
+        return out
+
+    def forward(self, x, bf16: bool = False):
+        px, mx, kx = _ptr(x, dtype=np.float32)
+        y = np.empty(self.B * self.H * self.W * 3, dtype=np.float32)
+        if mx == MEM_DEVICE:
+            import torch
+            y = torch.empty(y.size, dtype=torch.float32, device="cuda")
+        py, my, ky = _ptr(y, dtype=np.float32)
+        self._call("m1_nn_forward", px, py, int(bf16), _check_mem(mx, my))
+        return y
+
+    def loss_grad(self, x, t):
+        px, mx, kx = _ptr(x, dtype=np.float32)
+        pt, mt, kt = _ptr(t, dtype=np.float32)
+        g = np.empty(self.nparams, dtype=np.float32)
+        loss = C.c_double()
+        if mx == MEM_DEVICE:
+            import torch
+            g = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        pg, mg, kg = _ptr(g, dtype=np.float32)
+        self._call("m1_nn_loss_grad", px, pt, C.byref(loss), pg, _check_mem(mx, mt, mg))
+        return loss.value, g
+
+    def train(self, X, T, npairs: int, epochs: int = 1, lr: float = 1e-3, lr_decay: float = 1.0, seed: int = 1):
+        px, mx, kx = _ptr(X, dtype=np.float32)
+        pt, mt, kt = _ptr(T, dtype=np.float32)
+        o = TrainOpts(epochs, lr, lr_decay, seed)
+        info = TrainInfo()
+        self._call("m1_nn_train", px, pt, int(npairs), C.byref(o), C.byref(info), _check_mem(mx, mt))
+        return info.as_dict()

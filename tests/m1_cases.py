@@ -48,6 +48,27 @@ def smooth_2d(n=(40, 33), seed=11):
     return p
 
 
+def gas_2d(n=(37, 21), seed=5):
+    """2D gas-coupled case with frozen wave speeds, Dirichlet/outflow in x and
+    reflecting walls in y (exercises the tiled 2D J v with gas coupling)."""
+    rng = np.random.default_rng(seed)
+    p = si.make_problem(2, n, bc=[("dirichlet", "outflow"), ("reflect", "reflect")], gas=True, dt_factor=20)
+    p.E = rng.uniform(0.5, 2.0, p.shape)
+    dirs = rng.standard_normal((2,) + p.shape)
+    dirs /= np.linalg.norm(dirs, axis=0, keepdims=True)
+    p.F = p.c * p.E * rng.uniform(0, 0.8, p.shape) * dirs
+    p.T = rng.uniform(0.7, 1.3, p.shape)
+    p.rho_cv = rng.uniform(0.5, 2.0, p.shape)
+    p.sigma_a = 10.0 ** rng.uniform(-1, 2, p.shape)
+    p.sigma_f = p.sigma_a.copy()
+    Eg = rng.uniform(0.5, 1.5, (n[1],))
+    Fg = np.zeros((2, n[1]))
+    Fg[0] = 0.6 * Eg
+    p.boundary[(0, 0)] = (Eg, Fg, (rng.uniform(size=n[1]) < 0.5).astype(np.uint8))
+    p.implicit_eigs = False
+    return p
+
+
 def cases():
     """name -> problem factory"""
     return {
@@ -55,4 +76,5 @@ def cases():
         "beam2d": lambda: si.beam_lognormal_2d(70, 45, dt_factor=10.0),
         "smooth2d_implicit_eigs": smooth_2d,
         "gas3d": gas_3d,
+        "gas2d_frozen": gas_2d,
     }

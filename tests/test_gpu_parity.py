@@ -223,3 +223,20 @@ def test_nonfinite_input_reported(m1mod):
     ctx = ctx_for(m1mod, p)
     st, info = ctx.implicit_step(p.dt, m1mod.default_opts(), raise_on_fail=False)
     assert st == m1mod.M1_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("name", ["gas3d", "gas2d_frozen"])
+def test_advection(m1mod, name):
+    p = CASES[name]()
+    rng = np.random.default_rng(12)
+    u = []
+    for a in range(p.dim):
+        shp = list(p.shape)
+        shp[p.dim - 1 - a] += 1
+        u.append(rng.uniform(-0.5, 0.5, shp))
+    ref = Scheme(p).advect_internal_energy(u)
+    ctx = ctx_for(m1mod, p)
+    ctx.set_velocity(*[np.ascontiguousarray(x).ravel() for x in u])
+    ctx.advect(p.dt)
+    _, _, T = ctx.get_state()
+    assert np.abs(T - ref.ravel()).max() <= 1e-12 * np.abs(ref).max()

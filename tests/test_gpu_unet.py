@@ -1,0 +1,142 @@
+"""GPU checks of the learned preconditioner network against the FP64 oracle
+(oracle/unet.py), of its training pairs against the oracle's Jacobian, and of
+flexible GMRES with the trained network (A/B against point-block Jacobi).
+
+Tolerances: the GPU forward pass uses BF16-rounded weights (the oracle is given
+the same rounded weights) and FP32 accumulation: FP32 activations 1e-5
+relative, BF16 activations 3e-2; gradients 1e-4 relative in the 2-norm.
+"""
+import numpy as np
+import pytest
+
+import seeded_inputs as si
+from oracle import Scheme, newton_solve, unet
+from oracle.solvers import block_jacobi
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32)
+
+
+@pytest.fixture(scope="module")
+def m1mod():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2011_13926_gb300 import m1
+    return m1
+
+
+def _net_case(m1, B=2, H=8, W=12, seed=0):
+    net = m1.Net(H, W, B)
+    theta = unet.init_params(seed).astype(np.float32)
+    net.set_params(theta)
+    rng = np.random.default_rng(seed + 1)
+    x = rng.standard_normal((B, H, W, 4)).astype(np.float32)
+    t = rng.standard_normal((B, H, W, 3)).astype(np.float32)
+    return net, bf16_round(theta).astype(np.float64), x, t
+
+
+def test_forward_fp32_matches_oracle(m1mod):
+    net, th, x, _ = _net_case(m1mod)
+    y = net.forward(x.ravel()).reshape(2, 8, 12, 3)
+    ref = unet.forward(th, x.astype(np.float64))
+    assert np.linalg.norm(y - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_forward_bf16_matches_oracle(m1mod):
+    net, th, x, _ = _net_case(m1mod, seed=3)
+    y = net.forward(x.ravel(), bf16=True).reshape(2, 8, 12, 3)
+    ref = unet.forward(th, bf16_round(x).astype(np.float64))
+    assert np.linalg.norm(y - ref) <= 3e-2 * np.linalg.norm(ref)
+
+
+def test_gradient_matches_oracle(m1mod):
+    net, th, x, t = _net_case(m1mod, seed=5)
+    L, g = net.loss_grad(x.ravel(), t.ravel())
+    Lr, gr = unet.grad(th, x.astype(np.float64), t.astype(np.float64))
+    assert L == pytest.approx(Lr, rel=1e-5)
+    assert np.linalg.norm(g - gr) <= 1e-4 * np.linalg.norm(gr)
+    # layer by layer, so that one wrong layer cannot hide behind the others
+    k = 0
+    for name, shp in unet.param_shapes():
+        m = int(np.prod(shp))
+        a, b = g[k:k + m], gr[k:k + m]
+        k += m
+        assert np.linalg.norm(a - b) <= 1e-4 * max(np.linalg.norm(b), 1e-12), name
+
+
+def test_make_pair_matches_oracle(m1mod):
+    p = si.gaussian_lognormal_2d(16, 31, dt_factor=20.0)
+    s = Scheme(p)
+    u = p.state_vector()
+    e = np.random.default_rng(4).standard_normal(u.size)
+    ctx = m1mod.context_from_problem(p)
+    x, t = ctx.make_pair(p.dt, e)
+    r = s.jv(u, e)
+    Minv = block_jacobi(s.diag_blocks(u), s.N, s.nu)
+    tt = e - Minv(r)
+    scale = np.linalg.norm(r) / np.sqrt(r.size)
+    N = s.N
+    xr = np.stack([r[k * N:(k + 1) * N] / scale for k in range(3)]
+                  + [(np.log10(p.sigma_f.ravel() * p.dx[0]) - 0.5) / 2.5], axis=1)
+    tr = np.stack([tt[k * N:(k + 1) * N] / scale for k in range(3)], axis=1)
+    assert np.abs(x.reshape(N, 4) - xr).max() <= 1e-5 * np.abs(xr).max()
+    assert np.abs(t.reshape(N, 3) - tr).max() <= 1e-5 * np.abs(tr).max()
+
+
+def test_training_and_learned_fgmres(m1mod):
+    """Train on pairs from the plain solver's Jacobians of seeded problems,
+    then solve a held-out step with FGMRES + the network; the result must meet
+    the same parity bar as the other implicit paths."""
+    n = 32
+    pairs_x, pairs_t = [], []
+    for k in range(6):
+        p = si.gaussian_lognormal_2d(n, 1000 + k, dt_factor=50.0)
+        ctx = m1mod.context_from_problem(p)
+        st, info = ctx.implicit_step(p.dt, m1mod.default_opts(advance=0, precision=m1mod.PREC_MIXED))
+        u1 = ctx.get_solution()
+        u0 = p.state_vector()
+        rng = np.random.default_rng(2000 + k)
+        for U in (u0, u1):
+            for e in (u1 - u0, si.smooth_periodic(rng.standard_normal((3, n, n)), 2.0).ravel()):
+                x, t = ctx.make_pair(p.dt, e, U=U)
+                pairs_x.append(x)
+                pairs_t.append(t)
+    X = np.concatenate(pairs_x)
+    T = np.concatenate(pairs_t)
+    npairs = len(pairs_x)
+    net = m1mod.Net(n, n, 4)
+    net.set_params(unet.init_params(0).astype(np.float32))
+    info = net.train(X, T, npairs, epochs=30, lr=2e-3, seed=7)
+    assert info["final_loss"] < info["first_loss"]
+    # held-out problem: FGMRES with the learned preconditioner vs point-block Jacobi
+    p = si.gaussian_lognormal_2d(n, 1999, dt_factor=50.0)
+    s = Scheme(p)
+    ref = newton_solve(s, rtol=1e-10, gmres_rtol=1e-8)
+    infer = m1mod.Net(n, n, 1)
+    infer.set_params(net.get_params())
+    out = {}
+    for kind in ("bj", "learned"):
+        ctx = m1mod.context_from_problem(p)
+        opts = m1mod.default_opts(newton_rtol=1e-10, gmres_rtol=1e-8, advance=0, precision=m1mod.PREC_MIXED)
+        if kind == "learned":
+            ctx.set_preconditioner(infer)
+            opts.precond = m1mod.PRECOND_LEARNED
+        st, inf = ctx.implicit_step(p.dt, opts)
+        assert inf.converged
+        u = ctx.get_solution()
+        assert np.linalg.norm(s.residual(u)) <= 1e-8 * ref.res0
+        N = s.N
+        for c in range(3):
+            a, b = u[c * N:(c + 1) * N], ref.u[c * N:(c + 1) * N]
+            assert np.abs(a - b).max() <= 1e-7 * max(np.abs(b).max(), 1e-300)
+        out[kind] = inf.gmres_iters
+    print("gmres iterations (bj, learned):", out["bj"], out["learned"])

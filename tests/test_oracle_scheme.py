@@ -315,3 +315,35 @@ def test_newton_quadratic_tail():
     assert len(tail) >= 2, h
     for a, b in tail:
         assert b <= 1e2 * a * a + 1e-14
+
+
+# --------------------------------------------------------------------- gas advection (frozen flow)
+
+def test_advection_divergence_free_keeps_uniform_and_conserves():
+    n = 8
+    p = si.make_problem(3, (n, n, n), bc=[("periodic", "periodic")] * 3, gas=True, dt_factor=1.0)
+    p.T = np.full(p.shape, 2.0)
+    p.rho_cv = np.full(p.shape, 1.5)
+    u = si.divergence_free_velocity_3d(n, seed=4, umax=0.3)
+    # discrete divergence of the face field vanishes to round-off
+    div = (np.diff(u[0], axis=2) + np.diff(u[1], axis=1) + np.diff(u[2], axis=0))
+    assert np.abs(div).max() < 1e-15
+    T = Scheme(p).advect_internal_energy(u)
+    assert np.allclose(T, 2.0, rtol=1e-14)
+    rng = np.random.default_rng(6)
+    p.T = rng.uniform(0.5, 1.5, p.shape)
+    p.rho_cv = rng.uniform(0.5, 2.0, p.shape)
+    e0 = (p.rho_cv * p.T).sum()
+    T = Scheme(p).advect_internal_energy(u)
+    assert (p.rho_cv * T).sum() == pytest.approx(e0, rel=1e-14)
+
+
+def test_advection_upwind_shift():
+    n = 16
+    p = si.make_problem(1, (n,), bc=[("periodic", "periodic")], gas=True)
+    p.T = np.random.default_rng(7).uniform(0.5, 1.5, n)
+    p.rho_cv = np.ones(n)
+    p.dt = 0.25
+    u = np.full(n + 1, p.dx[0] / p.dt)  # CFL 1 to the right: e moves one cell
+    T = Scheme(p).advect_internal_energy([u])
+    assert np.allclose(T, np.roll(p.T, 1), rtol=1e-14)
