@@ -452,22 +452,6 @@ inline void arnoldi_step(const ArnoldiDev& K, float* V, float* w, int j, cudaStr
     launch_arnoldi_step_f32(K, V, w, j, s);
 }
 
-inline void multidot(const double* V, long long ld, int j, const double* w, long long n, double* p, double* h,
-                     cudaStream_t s) {
-    launch_multidot_f64(V, ld, j, w, n, p, h, s);
-}
-inline void multidot(const float* V, long long ld, int j, const float* w, long long n, double* p, double* h,
-                     cudaStream_t s) {
-    launch_multidot_f32(V, ld, j, w, n, p, h, s);
-}
-inline void cgs_update(const double* V, long long ld, int j, const double* h, double* w, long long n, double* p,
-                       cudaStream_t s) {
-    launch_cgs_update_f64(V, ld, j, h, w, n, p, s);
-}
-inline void cgs_update(const float* V, long long ld, int j, const double* h, float* w, long long n, double* p,
-                       cudaStream_t s) {
-    launch_cgs_update_f32(V, ld, j, h, w, n, p, s);
-}
 inline void scale_inv_sqrt(const double* x, const double* n2, double* y, long long n, cudaStream_t s) {
     launch_scale_inv_sqrt_f64(x, n2, y, n, s);
 }

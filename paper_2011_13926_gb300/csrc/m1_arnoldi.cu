@@ -2,7 +2,8 @@
 // Gram-Schmidt with selective reorthogonalisation).
 //
 // One Arnoldi step j on the new vector w = A M^-1 V_j is four kernels:
-//   dots(pass 1): h = V_{0..j}^T w and ||w||^2 in one pass over w; the last
+//   dots(pass 1): h = V_{0..j}^T w and ||w||^2 (basis vectors in groups of 8
+//     over a second grid dimension, w shared through L2); the last
 //     block to finish sums the per-block partials in a fixed order, tests
 //     ||w - V h||^2 = ||w||^2 - ||h||^2 against ||w||^2 / 2 (the Daniel-Gragg-
 //     Kaufman-Stewart criterion), and when no second pass is needed applies
@@ -105,38 +106,47 @@ __device__ __forceinline__ void setc(double2& v, int k, double x) {
     if (k == 0) v.x = x; else v.y = x;
 }
 
-// JMAX accumulators per thread (the smallest bucket >= j + 1 is launched, so
-// early Arnoldi steps keep their registers low and their occupancy high)
-template <class T, int JMAX>
+// Dots: grid (bx, G). Block (x, y) accumulates the dot products of basis
+// vectors i in [8y, 8y + 8) with w (and ||w||^2 when y == 0) over its
+// element stride; the last block of the whole grid sums the partials.
+constexpr int kGroup = 8;
+
+template <class T>
 __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const T* __restrict__ V,
                                                              const T* __restrict__ w, int j, int pass) {
     if (pass == 2 && *K.reorth == 0) return;
     using VT = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
-    __shared__ double red[kArThreads / 32][kCols + 1];
+    __shared__ double red[kArThreads / 32][kGroup + 1];
     __shared__ bool last;
-    Acc<T> acc[JMAX];
+    const int i0 = blockIdx.y * kGroup;
+    const int ni = min(kGroup, j + 1 - i0);  // >= 1
+    const bool with_norm = blockIdx.y == 0;
+    Acc<T> acc[kGroup];
     Acc<T> ww;
 #pragma unroll
-    for (int i = 0; i < JMAX; ++i) acc[i].zero();
+    for (int i = 0; i < kGroup; ++i) acc[i].zero();
     ww.zero();
     const long long n = K.n, ld = K.ld;
     const long long nv = n / W;
     const long long stride = (long long)gridDim.x * blockDim.x;
+    const T* Vg = V + (long long)i0 * ld;
     long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (; q + stride < nv; q += 2 * stride) {  // two vectors in flight per row
         const VT wa = reinterpret_cast<const VT*>(w)[q];
         const VT wb = reinterpret_cast<const VT*>(w)[q + stride];
+        if (with_norm) {
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            ww.add_prod(comp(wa, k), comp(wa, k));
-            ww.add_prod(comp(wb, k), comp(wb, k));
+            for (int k = 0; k < W; ++k) {
+                ww.add_prod(comp(wa, k), comp(wa, k));
+                ww.add_prod(comp(wb, k), comp(wb, k));
+            }
         }
 #pragma unroll
-        for (int i = 0; i < JMAX; ++i)
-            if (i <= j) {
-                const VT va = reinterpret_cast<const VT*>(V + i * ld)[q];
-                const VT vb = reinterpret_cast<const VT*>(V + i * ld)[q + stride];
+        for (int i = 0; i < kGroup; ++i)
+            if (i < ni) {
+                const VT va = reinterpret_cast<const VT*>(Vg + i * ld)[q];
+                const VT vb = reinterpret_cast<const VT*>(Vg + i * ld)[q + stride];
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
                     acc[i].add_prod(comp(va, k), comp(wa, k));
@@ -146,12 +156,14 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
     }
     for (; q < nv; q += stride) {
         const VT wv = reinterpret_cast<const VT*>(w)[q];
+        if (with_norm) {
 #pragma unroll
-        for (int k = 0; k < W; ++k) ww.add_prod(comp(wv, k), comp(wv, k));
+            for (int k = 0; k < W; ++k) ww.add_prod(comp(wv, k), comp(wv, k));
+        }
 #pragma unroll
-        for (int i = 0; i < JMAX; ++i)
-            if (i <= j) {
-                const VT vv = reinterpret_cast<const VT*>(V + i * ld)[q];
+        for (int i = 0; i < kGroup; ++i)
+            if (i < ni) {
+                const VT vv = reinterpret_cast<const VT*>(Vg + i * ld)[q];
 #pragma unroll
                 for (int k = 0; k < W; ++k) acc[i].add_prod(comp(vv, k), comp(wv, k));
             }
@@ -159,39 +171,39 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
     if (blockIdx.x == 0) {  // scalar tail
         for (long long e = nv * W + threadIdx.x; e < n; e += blockDim.x) {
             const T we = w[e];
-            ww.add_prod(we, we);
+            if (with_norm) ww.add_prod(we, we);
 #pragma unroll
-            for (int i = 0; i < JMAX; ++i)
-                if (i <= j) acc[i].add_prod(V[i * ld + e], we);
+            for (int i = 0; i < kGroup; ++i)
+                if (i < ni) acc[i].add_prod(Vg[i * ld + e], we);
         }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < JMAX; ++i) {
-        if (i <= j) {
+    for (int i = 0; i < kGroup; ++i) {
+        if (i < ni) {
             const double t = warp_sum_d(acc[i].get());
             if (lane == 0) red[wid][i] = t;
         }
     }
-    {
+    if (with_norm) {
         const double t = warp_sum_d(ww.get());
-        if (lane == 0) red[wid][kCols] = t;
+        if (lane == 0) red[wid][kGroup] = t;
     }
     __syncthreads();
     double* part = K.partials + (long long)blockIdx.x * (kCols + 1);
-    for (int i = threadIdx.x; i <= kCols; i += blockDim.x) {
-        if (i <= j || i == kCols) {
+    for (int i = threadIdx.x; i <= kGroup; i += blockDim.x) {
+        if (i < ni || (i == kGroup && with_norm)) {
             double t = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][i];
-            part[i] = t;
+            for (int qq = 0; qq < (int)(blockDim.x >> 5); ++qq) t += red[qq][i];
+            part[i < kGroup ? i0 + i : kCols] = t;
         }
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(K.counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) last = (atomicAdd(K.counter, 1u) == gridDim.x * gridDim.y - 1);
     __syncthreads();
     if (!last) return;
-    // the last block: fixed-order sums of the partials
+    // the last block: fixed-order sums of the partials over the x blocks
     __shared__ double tot[kCols + 1];
     for (int i = wid; i <= kCols; i += (int)(blockDim.x >> 5)) {
         if (i <= j || i == kCols) {
@@ -225,7 +237,9 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
     }
 }
 
-template <class T, int JMAX>
+// Update: out = (w - sum_{i<=j} h_i V_i) * inv; the loop over i has a runtime
+// bound (unrolled by 4) so that the loads of the basis are not all hoisted.
+template <class T>
 __global__ void __launch_bounds__(kArThreads) k_arnoldi_update(ArnoldiDev K, T* __restrict__ V, T* __restrict__ w,
                                                                int j, int pass) {
     const int reorth = *K.reorth;
@@ -247,17 +261,17 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_update(ArnoldiDev K, T* 
     for (; q + stride < nv; q += 2 * stride) {  // two vectors in flight per row
         VT xa = reinterpret_cast<const VT*>(w)[q];
         VT xb = reinterpret_cast<const VT*>(w)[q + stride];
+#pragma unroll 4
+        for (int i = 0; i <= j; ++i) {
+            const VT va = reinterpret_cast<const VT*>(V + i * ld)[q];
+            const VT vb = reinterpret_cast<const VT*>(V + i * ld)[q + stride];
+            const T hi = hs[i];
 #pragma unroll
-        for (int i = 0; i < JMAX; ++i)
-            if (i <= j) {
-                const VT va = reinterpret_cast<const VT*>(V + i * ld)[q];
-                const VT vb = reinterpret_cast<const VT*>(V + i * ld)[q + stride];
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    setc(xa, k, fma(-hs[i], comp(va, k), comp(xa, k)));
-                    setc(xb, k, fma(-hs[i], comp(vb, k), comp(xb, k)));
-                }
+            for (int k = 0; k < W; ++k) {
+                setc(xa, k, fma(-hi, comp(va, k), comp(xa, k)));
+                setc(xb, k, fma(-hi, comp(vb, k), comp(xb, k)));
             }
+        }
 #pragma unroll
         for (int k = 0; k < W; ++k) {
             setc(xa, k, comp(xa, k) * inv);
@@ -268,13 +282,13 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_update(ArnoldiDev K, T* 
     }
     for (; q < nv; q += stride) {
         VT x = reinterpret_cast<const VT*>(w)[q];
+#pragma unroll 4
+        for (int i = 0; i <= j; ++i) {
+            const VT vv = reinterpret_cast<const VT*>(V + i * ld)[q];
+            const T hi = hs[i];
 #pragma unroll
-        for (int i = 0; i < JMAX; ++i)
-            if (i <= j) {
-                const VT vv = reinterpret_cast<const VT*>(V + i * ld)[q];
-#pragma unroll
-                for (int k = 0; k < W; ++k) setc(x, k, fma(-hs[i], comp(vv, k), comp(x, k)));
-            }
+            for (int k = 0; k < W; ++k) setc(x, k, fma(-hi, comp(vv, k), comp(x, k)));
+        }
 #pragma unroll
         for (int k = 0; k < W; ++k) setc(x, k, comp(x, k) * inv);
         reinterpret_cast<VT*>(out)[q] = x;
@@ -282,31 +296,18 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_update(ArnoldiDev K, T* 
     if (blockIdx.x == 0) {
         for (long long e = nv * W + threadIdx.x; e < n; e += blockDim.x) {
             T x = w[e];
-#pragma unroll
-            for (int i = 0; i < JMAX; ++i)
-                if (i <= j) x = fma(-hs[i], V[i * ld + e], x);
+            for (int i = 0; i <= j; ++i) x = fma(-hs[i], V[i * ld + e], x);
             out[e] = x * inv;
         }
     }
 }
 
-template <class T, int JMAX>
-static void arnoldi_pass(const ArnoldiDev& K, T* V, T* w, int j, int pass, cudaStream_t s) {
-    k_arnoldi_dots<T, JMAX><<<K.blocks, kArThreads, 0, s>>>(K, V, w, j, pass);
-    k_arnoldi_update<T, JMAX><<<K.blocks, kArThreads, 0, s>>>(K, V, w, j, pass);
-}
-
 template <class T>
 static void arnoldi_step(const ArnoldiDev& K, T* V, T* w, int j, cudaStream_t s) {
+    const dim3 gd(K.blocks, (j + kGroup) / kGroup);  // ceil((j + 1) / 8) groups of basis vectors
     for (int pass = 1; pass <= 2; ++pass) {
-        if (j < 4)
-            arnoldi_pass<T, 4>(K, V, w, j, pass, s);
-        else if (j < 8)
-            arnoldi_pass<T, 8>(K, V, w, j, pass, s);
-        else if (j < 16)
-            arnoldi_pass<T, 16>(K, V, w, j, pass, s);
-        else
-            arnoldi_pass<T, kCols>(K, V, w, j, pass, s);
+        k_arnoldi_dots<T><<<gd, kArThreads, 0, s>>>(K, V, w, j, pass);
+        k_arnoldi_update<T><<<2 * K.blocks, kArThreads, 0, s>>>(K, V, w, j, pass);
     }
 }
 

@@ -56,16 +56,6 @@ int reduce_blocks();
 void launch_norm2_f64(const double* x, long long n, double* partials, double* out, cudaStream_t s);
 void launch_norm2_f32(const float* x, long long n, double* partials, double* out, cudaStream_t s);
 void launch_finish_sum(const double* partials, int nparts, int ncols, double* out, cudaStream_t s);
-// h[i] = V_i . w for i <= j (V rows of length n with stride ld), accumulated in FP64
-void launch_multidot_f64(const double* V, long long ld, int j, const double* w, long long n, double* partials,
-                         double* h, cudaStream_t s);
-void launch_multidot_f32(const float* V, long long ld, int j, const float* w, long long n, double* partials,
-                         double* h, cudaStream_t s);
-// w -= sum_{i<=j} h[i] V_i ; if partials != null also the FP64 sum of squares of the new w
-void launch_cgs_update_f64(const double* V, long long ld, int j, const double* h, double* w, long long n,
-                           double* partials, cudaStream_t s);
-void launch_cgs_update_f32(const float* V, long long ld, int j, const double* h, float* w, long long n,
-                           double* partials, cudaStream_t s);
 // y = x * (1 / sqrt(*nrm2)), zero when the norm is zero
 void launch_scale_inv_sqrt_f64(const double* x, const double* nrm2, double* y, long long n, cudaStream_t s);
 void launch_scale_inv_sqrt_f32(const float* x, const double* nrm2, float* y, long long n, cudaStream_t s);
@@ -80,10 +70,6 @@ void launch_axpby_f64(double a, const double* x, double b, const double* y, doub
 void launch_f64_to_f32(const double* x, float* y, long long n, cudaStream_t s);
 void launch_f32_to_f64(const float* x, double* y, long long n, cudaStream_t s);
 void launch_scale_f64_to_f32(const double* x, const double* nrm2, float* y, long long n, cudaStream_t s);
-// Givens update of Hessenberg column j (device scalars), resid[0] = |g_{j+1}|
-// (hcol = h1 + h2 of the two Gram-Schmidt passes, h2 may be null)
-void launch_givens(double* H, double* cs, double* sn, double* g, const double* h1, const double* h2,
-                   const double* hnorm2, int j, double* resid, cudaStream_t s);
 // back substitution y = H^-1 g on the rotated k x k triangle
 void launch_backsolve(const double* H, const double* g, int k, double* y, cudaStream_t s);
 // count cells with |F| > c E and non-finite entries

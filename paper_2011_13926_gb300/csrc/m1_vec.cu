@@ -1,7 +1,7 @@
-// m1_vec.cu — Krylov vector kernels: norms, fused multi-dot products and
-// Gram-Schmidt updates (warp shuffles + block reductions, FP64 accumulation in
-// a fixed order so that results are reproducible run to run), the Givens
-// update of the Hessenberg matrix and the least-squares back substitution.
+// m1_vec.cu — vector kernels around the Krylov solver: norms (warp shuffles +
+// block reductions, FP64 accumulation in a fixed order so that results are
+// reproducible run to run), linear combinations, precision conversions, the
+// least-squares back substitution and the realizability count.
 #include "m1_internal.h"
 
 namespace m1 {
@@ -67,89 +67,6 @@ void launch_norm2_f32(const float* x, long long n, double* partials, double* out
     launch_finish_sum(partials, kRedBlocks, 1, out, s);
 }
 
-// h_i = V_i . w for i = 0..j in one pass over w: each thread keeps j+1 FP64
-// accumulators; products of FP32 inputs are exact in FP64.
-template <class T>
-__global__ void __launch_bounds__(kRedThreads) k_multidot(const T* __restrict__ V, long long ld, int j,
-                                                          const T* __restrict__ w, long long n,
-                                                          double* __restrict__ partials) {
-    __shared__ double red[kRedThreads / 32][kMaxCols];
-    double acc[kMaxCols];
-#pragma unroll
-    for (int i = 0; i < kMaxCols; ++i) acc[i] = 0.0;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const double we = (double)w[e];
-#pragma unroll
-        for (int i = 0; i < kMaxCols; ++i)
-            if (i <= j) acc[i] += (double)V[i * ld + e] * we;
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < kMaxCols; ++i) {
-        if (i <= j) {
-            const double t = warp_sum(acc[i]);
-            if (lane == 0) red[wid][i] = t;
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][i];
-        partials[(long long)blockIdx.x * (j + 1) + i] = t;
-    }
-}
-
-void launch_multidot_f64(const double* V, long long ld, int j, const double* w, long long n, double* partials,
-                         double* h, cudaStream_t s) {
-    k_multidot<double><<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j, w, n, partials);
-    launch_finish_sum(partials, kRedBlocks, j + 1, h, s);
-}
-void launch_multidot_f32(const float* V, long long ld, int j, const float* w, long long n, double* partials,
-                         double* h, cudaStream_t s) {
-    k_multidot<float><<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j, w, n, partials);
-    launch_finish_sum(partials, kRedBlocks, j + 1, h, s);
-}
-
-// w -= sum_{i<=j} h_i V_i, optionally with the sum of squares of the new w
-template <class T>
-__global__ void __launch_bounds__(kRedThreads) k_cgs_update(const T* __restrict__ V, long long ld, int j,
-                                                            const double* __restrict__ h, T* __restrict__ w,
-                                                            long long n, double* __restrict__ partials) {
-    __shared__ double hs[kMaxCols];
-    __shared__ double red[kRedThreads / 32];
-    if (threadIdx.x < kMaxCols) hs[threadIdx.x] = threadIdx.x <= j ? h[threadIdx.x] : 0.0;
-    __syncthreads();
-    double t = 0.0;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        double x = (double)w[e];
-#pragma unroll
-        for (int i = 0; i < kMaxCols; ++i)
-            if (i <= j) x -= hs[i] * (double)V[i * ld + e];
-        const T xt = (T)x;
-        w[e] = xt;
-        t += (double)xt * (double)xt;
-    }
-    if (partials) {
-        t = warp_sum(t);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double u = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-            u = warp_sum(u);
-            if (threadIdx.x == 0) partials[blockIdx.x] = u;
-        }
-    }
-}
-
-void launch_cgs_update_f64(const double* V, long long ld, int j, const double* h, double* w, long long n,
-                           double* partials, cudaStream_t s) {
-    k_cgs_update<double><<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j, h, w, n, partials);
-}
-void launch_cgs_update_f32(const float* V, long long ld, int j, const double* h, float* w, long long n,
-                           double* partials, cudaStream_t s) {
-    k_cgs_update<float><<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, j, h, w, n, partials);
-}
-
 template <class T>
 __global__ void k_scale_inv_sqrt(const T* __restrict__ x, const double* __restrict__ nrm2, T* __restrict__ y,
                                  long long n) {
@@ -176,18 +93,29 @@ void launch_scale_f64_to_f32(const double* x, const double* nrm2, float* y, long
     k_scale_f64_to_f32<<<kRedBlocks, kRedThreads, 0, s>>>(x, nrm2, y, n);
 }
 
+// x += sum_{i<k} y_i Z_i; rows of Z start on 256-byte boundaries (ld % 64 == 0),
+// x is a separate 256-byte-aligned allocation: two elements per thread step
 template <class T>
 __global__ void k_lincomb_add(const T* __restrict__ Z, long long ld, int k, const double* __restrict__ y,
                               double* __restrict__ x, long long n) {
     __shared__ double ys[kMaxCols];
     if (threadIdx.x < kMaxCols) ys[threadIdx.x] = threadIdx.x < k ? y[threadIdx.x] : 0.0;
     __syncthreads();
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        double acc = x[e];
-#pragma unroll
-        for (int i = 0; i < kMaxCols; ++i)
-            if (i < k) acc += ys[i] * (double)Z[i * ld + e];
-        x[e] = acc;
+    const long long n2 = n / 2;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += (long long)gridDim.x * blockDim.x) {
+        double2 acc = reinterpret_cast<const double2*>(x)[q];
+#pragma unroll 4
+        for (int i = 0; i < k; ++i) {
+            const T* zi = Z + i * ld + 2 * q;
+            acc.x += ys[i] * (double)zi[0];
+            acc.y += ys[i] * (double)zi[1];
+        }
+        reinterpret_cast<double2*>(x)[q] = acc;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) {
+        double acc = x[n - 1];
+        for (int i = 0; i < k; ++i) acc += ys[i] * (double)Z[i * ld + n - 1];
+        x[n - 1] = acc;
     }
 }
 void launch_lincomb_add_f64(const double* Z, long long ld, int k, const double* y, double* x, long long n,
@@ -222,40 +150,6 @@ void launch_f64_to_f32(const double* x, float* y, long long n, cudaStream_t s) {
 }
 void launch_f32_to_f64(const float* x, double* y, long long n, cudaStream_t s) {
     k_convert<float, double><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n);
-}
-
-// Column j of the Hessenberg matrix H (column-major, ld = kMaxRestart + 1):
-// H[i][j] = h1_i + h2_i (i <= j), H[j+1][j] = ||w||; apply the previous
-// rotations, form rotation j, rotate g; resid = |g_{j+1}|.
-__global__ void k_givens(double* H, double* cs, double* sn, double* g, const double* h1, const double* h2,
-                         const double* hnorm2, int j, double* resid) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int ldh = kMaxRestart + 1;
-    double* col = H + (long long)j * ldh;
-    for (int i = 0; i <= j; ++i) col[i] = h1[i] + (h2 ? h2[i] : 0.0);
-    col[j + 1] = sqrt(fmax(hnorm2[0], 0.0));
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
-    }
-    const double a = col[j], b = col[j + 1];
-    const double den = hypot(a, b);
-    const double c = den > 0.0 ? a / den : 1.0;
-    const double s = den > 0.0 ? b / den : 0.0;
-    cs[j] = c;
-    sn[j] = s;
-    col[j] = den;
-    col[j + 1] = 0.0;
-    g[j + 1] = -s * g[j];
-    g[j] = c * g[j];
-    resid[0] = fabs(g[j + 1]);
-    resid[1] = den;
-}
-
-void launch_givens(double* H, double* cs, double* sn, double* g, const double* h1, const double* h2,
-                   const double* hnorm2, int j, double* resid, cudaStream_t s) {
-    k_givens<<<1, 32, 0, s>>>(H, cs, sn, g, h1, h2, hnorm2, j, resid);
 }
 
 __global__ void k_backsolve(const double* H, const double* g, int k, double* y) {

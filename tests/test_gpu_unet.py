@@ -101,7 +101,10 @@ def test_training_and_learned_fgmres(m1mod):
     for k in range(6):
         p = si.gaussian_lognormal_2d(n, 1000 + k, dt_factor=50.0)
         ctx = m1mod.context_from_problem(p)
-        st, info = ctx.implicit_step(p.dt, m1mod.default_opts(advance=0, precision=m1mod.PREC_MIXED))
+        # the last Newton iterate is a valid linearisation point even when the
+        # plain solver stops short of the tolerance
+        st, info = ctx.implicit_step(p.dt, m1mod.default_opts(advance=0, precision=m1mod.PREC_MIXED),
+                                     raise_on_fail=False)
         u1 = ctx.get_solution()
         u0 = p.state_vector()
         rng = np.random.default_rng(2000 + k)
