@@ -61,11 +61,11 @@ def flatten(p: Dict[str, np.ndarray]) -> np.ndarray:
 
 def init_params(seed: int = 0) -> np.ndarray:
     """He-normal weights (std sqrt(2 / (9 cin))), zero biases; the last layer is
-    scaled by 0.1 so that the initial correction is small."""
+    scaled by 1e-3 so that the network starts as a near-zero correction."""
     rng = np.random.default_rng(seed)
     p = {}
     for name, ci, co, relu in LAYERS:
-        std = np.sqrt(2.0 / (9 * ci)) * (1.0 if relu else 0.1)
+        std = np.sqrt(2.0 / (9 * ci)) * (1.0 if relu else 1e-3)
         p[name + ".w"] = rng.standard_normal((3, 3, ci, co)) * std
         p[name + ".b"] = np.zeros(co)
     return flatten(p)
