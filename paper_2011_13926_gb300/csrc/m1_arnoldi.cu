@@ -14,7 +14,8 @@
 //   dots/update(pass 2): the classical second Gram-Schmidt pass, only when the
 //     criterion asked for it (otherwise the blocks return at once).
 // FP32 vectors accumulate their dot products in double-float arithmetic
-// (error-free TwoProd with FMA and TwoSum), FP64 vectors in FP64; the
+// (each 16-byte group of four products by an FMA chain, then an error-free
+// TwoSum into a (hi, lo) pair), FP64 vectors in FP64; the
 // cross-block sums are FP64 in a fixed order, so results are reproducible.
 // The Hessenberg least-squares problem stays in FP64 on the device.
 #include "m1_internal.h"
@@ -42,6 +43,10 @@ template <> struct Acc<double> {
     double v;
     __device__ __forceinline__ void zero() { v = 0.0; }
     __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ void add_prod4(const double2& a, const double2& b) {
+        v = fma(a.x, b.x, v);
+        v = fma(a.y, b.y, v);
+    }
     __device__ __forceinline__ double get() const { return v; }
 };
 template <> struct Acc<float> {
@@ -51,6 +56,14 @@ template <> struct Acc<float> {
         const float p = a * b;
         const float e = fmaf(a, b, -p);
         two_sum_acc(t, p, e);
+    }
+    // four products by an FMA chain (FP32 rounding), then one compensated add
+    __device__ __forceinline__ void add_prod4(const float4& a, const float4& b) {
+        float p = a.x * b.x;
+        p = fmaf(a.y, b.y, p);
+        p = fmaf(a.z, b.z, p);
+        p = fmaf(a.w, b.w, p);
+        two_sum_acc(t, p, 0.f);
     }
     __device__ __forceinline__ double get() const { return (double)t.hi + (double)t.lo; }
 };
@@ -136,36 +149,26 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
         const VT wa = reinterpret_cast<const VT*>(w)[q];
         const VT wb = reinterpret_cast<const VT*>(w)[q + stride];
         if (with_norm) {
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                ww.add_prod(comp(wa, k), comp(wa, k));
-                ww.add_prod(comp(wb, k), comp(wb, k));
-            }
+            ww.add_prod4(wa, wa);
+            ww.add_prod4(wb, wb);
         }
 #pragma unroll
         for (int i = 0; i < kGroup; ++i)
             if (i < ni) {
                 const VT va = reinterpret_cast<const VT*>(Vg + i * ld)[q];
                 const VT vb = reinterpret_cast<const VT*>(Vg + i * ld)[q + stride];
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    acc[i].add_prod(comp(va, k), comp(wa, k));
-                    acc[i].add_prod(comp(vb, k), comp(wb, k));
-                }
+                acc[i].add_prod4(va, wa);
+                acc[i].add_prod4(vb, wb);
             }
     }
     for (; q < nv; q += stride) {
         const VT wv = reinterpret_cast<const VT*>(w)[q];
-        if (with_norm) {
-#pragma unroll
-            for (int k = 0; k < W; ++k) ww.add_prod(comp(wv, k), comp(wv, k));
-        }
+        if (with_norm) ww.add_prod4(wv, wv);
 #pragma unroll
         for (int i = 0; i < kGroup; ++i)
             if (i < ni) {
                 const VT vv = reinterpret_cast<const VT*>(Vg + i * ld)[q];
-#pragma unroll
-                for (int k = 0; k < W; ++k) acc[i].add_prod(comp(vv, k), comp(wv, k));
+                acc[i].add_prod4(vv, wv);
             }
     }
     if (blockIdx.x == 0) {  // scalar tail
