@@ -280,6 +280,39 @@ m1_status m1_nn_make_pair(m1_ctx* ctx, double dt, const double* U, const double*
 m1_status m1_set_preconditioner(m1_ctx* ctx, m1_nn* nn);
 
 /* ---------------------------------------------------------------------------
+ * Batched steps: many independent 2D radiation-only problems (periodic,
+ * outflow or reflecting boundaries; frozen or fixed wave speeds) solved by one
+ * persistent launch per size class, all classes replayed from one CUDA graph.
+ * Each CTA takes problems from a device work queue and runs a whole
+ * backward-Euler step (Newton, FP32 GMRES under FP64 refinement, point-block
+ * Jacobi, line search) with CTA-wide barriers only.
+ * ------------------------------------------------------------------------- */
+typedef struct m1_batch m1_batch;
+
+typedef struct {
+    int converged, newton_iters, gmres_iters;
+    double res0, res;
+} m1_batch_problem_info;
+
+/* nprob grids (descs[k]); size classes are the distinct cell counts. */
+m1_status m1_batch_create(int nprob, const m1_grid_desc* descs, void* cuda_stream, m1_batch** out);
+m1_status m1_batch_destroy(m1_batch* b);
+/* Problem k's opacities, time-n state (E: N, F: 2N) and frozen emission (NULL = 0). */
+m1_status m1_batch_set_problem(m1_batch* b, int k, const double* sigma_a, const double* sigma_f, const double* E,
+                               const double* F, const double* B, m1_mem mem);
+/* Time each class's persistent launch with CTAs of 128, 256 and 512 threads and
+ * keep the fastest (chosen[c] receives it; may be NULL). */
+m1_status m1_batch_tune(m1_batch* b, const double* dts, const m1_solver_opts* opts, int* chosen);
+/* One implicit step of every problem (dts[k]); info[k] per problem (may be
+ * NULL); *elapsed_ms = device time of the graph launch (may be NULL). The
+ * solutions are read with m1_batch_get_solution; the time-n states are kept. */
+m1_status m1_batch_implicit_step(m1_batch* b, const double* dts, const m1_solver_opts* opts,
+                                 m1_batch_problem_info* info, double* elapsed_ms);
+m1_status m1_batch_get_solution(const m1_batch* b, int k, double* U, m1_mem mem);
+int m1_batch_num_classes(const m1_batch* b);
+const char* m1_batch_last_error(const m1_batch* b);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free residual.
  *
  * The paper has no counterpart of this entry point. It serves callers that

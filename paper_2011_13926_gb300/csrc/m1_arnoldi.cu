@@ -74,27 +74,31 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// Hessenberg column j from h (j+1 entries) and beta = ||w - V h||; rotations.
-__device__ void givens_column(const ArnoldiDev& K, const double* h, double beta, int j) {
-    double* col = K.H + (long long)j * kHLd;
-    for (int i = 0; i <= j; ++i) col[i] = h[i];
+// Hessenberg column j from h (j+1 entries, shared memory) and beta = ||w - V h||:
+// apply the previous rotations (cs, sn staged in shared memory), form rotation
+// j, rotate g; one thread, no dependent global loads.
+__device__ void givens_column(const ArnoldiDev& K, double* col, const double* scs, const double* ssn, double beta,
+                              int j) {
     col[j + 1] = beta;
     for (int i = 0; i < j; ++i) {
-        const double t = K.cs[i] * col[i] + K.sn[i] * col[i + 1];
-        col[i + 1] = -K.sn[i] * col[i] + K.cs[i] * col[i + 1];
+        const double t = scs[i] * col[i] + ssn[i] * col[i + 1];
+        col[i + 1] = -ssn[i] * col[i] + scs[i] * col[i + 1];
         col[i] = t;
     }
     const double a = col[j], b = col[j + 1];
     const double den = hypot(a, b);
     const double c = den > 0.0 ? a / den : 1.0;
     const double s = den > 0.0 ? b / den : 0.0;
-    K.cs[j] = c;
-    K.sn[j] = s;
     col[j] = den;
     col[j + 1] = 0.0;
-    K.g[j + 1] = -s * K.g[j];
-    K.g[j] = c * K.g[j];
-    K.resid[0] = fabs(K.g[j + 1]);
+    double* H = K.H + (long long)j * kHLd;
+    for (int i = 0; i <= j + 1; ++i) H[i] = col[i];
+    K.cs[j] = c;
+    K.sn[j] = s;
+    const double gj = K.g[j];
+    K.g[j + 1] = -s * gj;
+    K.g[j] = c * gj;
+    K.resid[0] = fabs(s * gj);
     K.resid[1] = beta;
     K.nrm2[1] = beta * beta;
 }
@@ -216,26 +220,34 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
             if (lane == 0) tot[i] = t;
         }
     }
+    // stage the previous rotations and the column (h1 [+ h2]) in shared memory
+    __shared__ double col[kCols + 1], scs[kCols], ssn[kCols];
+    double* h = pass == 1 ? K.h1 : K.h2;
+    if (threadIdx.x <= j) {
+        const double hv = tot[threadIdx.x];
+        h[threadIdx.x] = hv;
+        col[threadIdx.x] = pass == 2 ? K.h1[threadIdx.x] + hv : hv;
+    }
+    if (threadIdx.x < j) {
+        scs[threadIdx.x] = K.cs[threadIdx.x];
+        ssn[threadIdx.x] = K.sn[threadIdx.x];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         *K.counter = 0u;
-        double* h = pass == 1 ? K.h1 : K.h2;
         double hh = 0.0;
-        for (int i = 0; i <= j; ++i) {
-            h[i] = tot[i];
-            hh += tot[i] * tot[i];
-        }
+        for (int i = 0; i <= j; ++i) hh += tot[i] * tot[i];
         const double wn2 = tot[kCols];
         const double rest = wn2 - hh;
         if (pass == 1 && !(rest > 0.5 * wn2)) {
             *K.reorth = 1;  // second pass decides the column
             K.resid[2] = 1.0;
         } else {
-            if (pass == 1) K.resid[2] = 0.0;
-            if (pass == 1) *K.reorth = 0;
-            double hsum[kCols];
-            for (int i = 0; i <= j; ++i) hsum[i] = K.h1[i] + (pass == 2 ? K.h2[i] : 0.0);
-            givens_column(K, hsum, sqrt(fmax(rest, 0.0)), j);
+            if (pass == 1) {
+                K.resid[2] = 0.0;
+                *K.reorth = 0;
+            }
+            givens_column(K, col, scs, ssn, sqrt(fmax(rest, 0.0)), j);
         }
     }
 }

@@ -15,60 +15,15 @@ static constexpr int kThreads = 256;
 int stencil_blocks(long long N) { return (int)((N + kThreads - 1) / kThreads); }
 
 // ------------------------------------------------------------------ time-n faces
-// lambda+-(U^n) and alpha (Eq. asymptoticCorrection with f_{i+1/2} = (f_i + f_{i+1})/2
-// and sigma_{i+1/2} = (sigma_i + sigma_{i+1})/2) on the faces of axis a.
 template <int DIM>
 __global__ void k_faces_time_n(Dev<double> g, int a, double* lam_p, double* lam_m, double* alpha) {
     const long long nfaces = g.N / g.n[a] * (g.n[a] + 1);
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nfaces) return;
-    int fn[3] = {g.n[0], g.n[1], g.n[2]};
-    fn[a] += 1;
-    int coord[3];
-    cell_coord(f, fn[0], fn[1], coord);
-    const int fa = coord[a];
-    LoadPlain<double> ld{g.Un, g.N};
-    // the cell on the right of the face unless the face is the high boundary
-    int cc[3] = {coord[0], coord[1], coord[2]};
-    const bool high = (fa == g.n[a]);
-    cc[a] = high ? g.n[a] - 1 : fa;
-    const long long idx = ((long long)cc[2] * g.n[1] + cc[1]) * g.n[0] + cc[0];
-    St<double, DIM> self = load_state<double, DIM, false>(ld, idx, idx);
-    double sig_nb;
-    bool bnd;
-    St<double, DIM> nb;
-    if (high) {
-        nb = neighbour<double, DIM, false>(g, ld, self, idx, cc, a, 1, sig_nb, bnd);
-    } else if (fa == 0) {
-        nb = neighbour<double, DIM, false>(g, ld, self, idx, cc, a, 0, sig_nb, bnd);
-    } else {
-        const long long j = idx - g.stride[a];
-        nb = load_state<double, DIM, false>(ld, j, idx);
-        sig_nb = g.sig_f[j];
-    }
-    const St<double, DIM>& uL = high ? self : nb;
-    const St<double, DIM>& uR = high ? nb : self;
-    const Cl<double, DIM> kL = closure(uL, g.c), kR = closure(uR, g.c);
-    double lp, lm;
-    if (g.fixed_eigs) {
-        lp = g.c;
-        lm = -g.c;
-    } else {
-        double xL, nL, xR, nR;
-        eigen(kL, a, g.c, xL, nL);
-        eigen(kR, a, g.c, xR, nR);
-        wave_speeds(xL, nL, xR, nR, g.lambda_floor, lp, lm);
-    }
+    double lp, lm, al;
+    face_time_n<DIM>(g, a, f, lp, lm, al);
     lam_p[f] = lp;
     lam_m[f] = lm;
-    double al = 1.0;
-    if (g.ap) {
-        const double fbar = 0.5 * (sqrt(kL.f2) + sqrt(kR.f2));
-        const double sig = 0.5 * (g.sig_f[idx] + sig_nb);
-        const double den = lp - lm;
-        const double term = den >= Tiny<double>::den() ? lp * lm / (g.c * den) : 0.0;
-        al = 1.0 / (1.0 - 3.0 * sig * g.dx[a] * (1.0 - fbar * fbar) * term);
-    }
     alpha[f] = al;
 }
 
@@ -380,61 +335,8 @@ __global__ void k_block_inverse(long long N, const B* __restrict__ blocks, doubl
 #pragma unroll
     for (int r = 0; r < NU; ++r)
 #pragma unroll
-        for (int c = 0; c < NU; ++c) {
-            a[r][c] = (double)blocks[(long long)(r * NU + c) * N + i];
-            x[r][c] = (r == c) ? 1.0 : 0.0;
-        }
-    bool bad = false;
-#pragma unroll
-    for (int col = 0; col < NU; ++col) {
-        int piv = col;
-        double best = fabs(a[col][col]);
-#pragma unroll
-        for (int r = col + 1; r < NU; ++r)
-            if (fabs(a[r][col]) > best) {
-                best = fabs(a[r][col]);
-                piv = r;
-            }
-        if (!(best > 0.0)) bad = true;
-        // swap rows col and piv (predicated, registers only)
-#pragma unroll
-        for (int r = col + 1; r < NU; ++r) {
-            if (r == piv) {
-#pragma unroll
-                for (int c = 0; c < NU; ++c) {
-                    double t = a[col][c];
-                    a[col][c] = a[r][c];
-                    a[r][c] = t;
-                    t = x[col][c];
-                    x[col][c] = x[r][c];
-                    x[r][c] = t;
-                }
-            }
-        }
-        const double inv = bad ? 0.0 : 1.0 / a[col][col];
-#pragma unroll
-        for (int c = 0; c < NU; ++c) {
-            a[col][c] *= inv;
-            x[col][c] *= inv;
-        }
-#pragma unroll
-        for (int r = 0; r < NU; ++r) {
-            if (r == col) continue;
-            const double m = a[r][col];
-#pragma unroll
-            for (int c = 0; c < NU; ++c) {
-                a[r][c] -= m * a[col][c];
-                x[r][c] -= m * x[col][c];
-            }
-        }
-    }
-    if (bad) {
-        atomicAdd(singular, 1);
-#pragma unroll
-        for (int r = 0; r < NU; ++r)
-#pragma unroll
-            for (int c = 0; c < NU; ++c) x[r][c] = (r == c) ? 1.0 : 0.0;
-    }
+        for (int c = 0; c < NU; ++c) a[r][c] = (double)blocks[(long long)(r * NU + c) * N + i];
+    if (!invert_block<NU>(a, x)) atomicAdd(singular, 1);
 #pragma unroll
     for (int r = 0; r < NU; ++r)
 #pragma unroll

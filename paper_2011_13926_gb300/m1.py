@@ -31,7 +31,8 @@ EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "
             "m1_profile", "m1_last_error", "m1_residual_noalloc", "m1_nn_num_params", "m1_nn_create",
             "m1_nn_destroy", "m1_nn_set_params", "m1_nn_get_params", "m1_nn_forward", "m1_nn_loss_grad",
             "m1_nn_train", "m1_nn_last_error", "m1_nn_make_pair", "m1_set_preconditioner", "m1_set_velocity",
-            "m1_advect"]
+            "m1_advect", "m1_batch_create", "m1_batch_destroy", "m1_batch_set_problem", "m1_batch_tune",
+            "m1_batch_implicit_step", "m1_batch_get_solution", "m1_batch_num_classes", "m1_batch_last_error"]
 
 
 class GridDesc(C.Structure):
@@ -94,6 +95,11 @@ class Stats(C.Structure):
 
 
 NOALLOC_MAX_CELLS = 65536
+
+
+class BatchProblemInfo(C.Structure):
+    _fields_ = [("converged", C.c_int), ("newton_iters", C.c_int), ("gmres_iters", C.c_int),
+                ("res0", C.c_double), ("res", C.c_double)]
 
 
 class TrainOpts(C.Structure):
@@ -159,6 +165,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_nn_make_pair": (I, [P, D, P, P, P, P, I]),
         "m1_set_preconditioner": (I, [P, P]),
         "m1_set_velocity": (I, [P, P, P, P, I]),
+        "m1_batch_create": (I, [I, P, P, C.POINTER(P)]),
+        "m1_batch_destroy": (I, [P]),
+        "m1_batch_set_problem": (I, [P, I, P, P, P, P, P, I]),
+        "m1_batch_tune": (I, [P, P, C.POINTER(SolverOpts), P]),
+        "m1_batch_implicit_step": (I, [P, P, C.POINTER(SolverOpts), P, C.POINTER(D)]),
+        "m1_batch_get_solution": (I, [P, I, P, I]),
+        "m1_batch_num_classes": (I, [P]),
+        "m1_batch_last_error": (C.c_char_p, [P]),
         "m1_advect": (I, [P, D]),
     }
     for name, (res, args) in sig.items():
@@ -526,3 +540,67 @@ class Net:
         info = TrainInfo()
         self._call("m1_nn_train", px, pt, int(npairs), C.byref(o), C.byref(info), _check_mem(mx, mt))
         return info.as_dict()
+
+
+class Batch:
+    """m1_batch: many independent 2D radiation-only problems per launch."""
+
+    def __init__(self, problems, stream: int = 0):
+        self.lib = load()
+        descs = (GridDesc * len(problems))()
+        for k, p in enumerate(problems):
+            descs[k] = grid_desc(p.dim, p.n[:p.dim], p.lo[:p.dim], p.hi[:p.dim], p.bc, p.c, p.a_r, p.gas,
+                                 p.well_balanced, p.ap_correction, p.fixed_eigs, p.lambda_floor, p.wb_boundary,
+                                 p.implicit_eigs)
+        h = C.c_void_p()
+        st = self.lib.m1_batch_create(len(problems), C.cast(descs, C.c_void_p), C.c_void_p(stream or None),
+                                      C.byref(h))
+        if st != M1_OK:
+            raise M1Error(st, "m1_batch_create failed")
+        self.h = h
+        self.problems = problems
+        for k, p in enumerate(problems):
+            arrs = [np.ascontiguousarray(x, dtype=np.float64).ravel() for x in (p.sigma_a, p.sigma_f, p.E, p.F)]
+            Bm = np.ascontiguousarray(p.B, dtype=np.float64).ravel() if p.B is not None else None
+            self._call("m1_batch_set_problem", k, *[a.ctypes.data for a in arrs],
+                       Bm.ctypes.data if Bm is not None else None, MEM_HOST)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.m1_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, *args):
+        st = getattr(self.lib, name)(self.h, *args)
+        if st != M1_OK:
+            raise M1Error(st, self.lib.m1_batch_last_error(self.h).decode())
+
+    def num_classes(self) -> int:
+        return int(self.lib.m1_batch_num_classes(self.h))
+
+    def tune(self, dts, opts=None):
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        chosen = np.zeros(self.num_classes(), dtype=np.int32)
+        o = opts if opts is not None else default_opts()
+        self._call("m1_batch_tune", d.ctypes.data, C.byref(o), chosen.ctypes.data)
+        return chosen
+
+    def implicit_step(self, dts, opts=None):
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        info = (BatchProblemInfo * len(self.problems))()
+        ms = C.c_double()
+        o = opts if opts is not None else default_opts()
+        self._call("m1_batch_implicit_step", d.ctypes.data, C.byref(o), C.cast(info, C.c_void_p), C.byref(ms))
+        return [{k: getattr(i, k) for k, _ in i._fields_} for i in info], ms.value
+
+    def get_solution(self, k: int):
+        p = self.problems[k]
+        out = np.empty(p.n_u * p.ncell)
+        self._call("m1_batch_get_solution", int(k), out.ctypes.data, MEM_HOST)
+        return out

@@ -33,7 +33,11 @@ def test_pool_up_adjoint():
 
 def test_gradient_matches_central_differences():
     rng = np.random.default_rng(2)
-    theta = unet.init_params(3)
+    # an O(1) last layer (the default initialisation starts it near zero), so
+    # that every layer's gradient is well above the round-off of the loss
+    p = unet.unflatten(unet.init_params(3))
+    p["d1b.w"] = p["d1b.w"] * 1e3
+    theta = unet.flatten(p)
     x = rng.standard_normal((2, 8, 8, 4))
     t = rng.standard_normal((2, 8, 8, 3))
     L, g = unet.grad(theta, x, t)
