@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
             if (lane == 0) tot[i] = t;
         }
     }
+    __syncthreads();  // tot[] complete
     // stage the previous rotations and the column (h1 [+ h2]) in shared memory
     __shared__ double col[kCols + 1], scs[kCols], ssn[kCols];
     double* h = pass == 1 ? K.h1 : K.h2;

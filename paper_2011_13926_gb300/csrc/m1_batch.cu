@@ -404,7 +404,8 @@ size_t smem_bytes() { return sizeof(double) * (128 + (kM + 1) * kM + 2 * kM + (k
 
 // ============================================================================ host side
 struct m1_batch {
-    cudaStream_t s = nullptr;
+    cudaStream_t s = nullptr;       // the library's own stream (capturable), synchronised per call
+    cudaStream_t user = nullptr;    // the caller's stream (ordered before each call)
     int nprob = 0;
     std::vector<m1_grid_desc> descs;
     std::vector<Prob> hp;               // host copies of the problem descriptors
@@ -496,7 +497,12 @@ m1_status m1_batch_create(int nprob, const m1_grid_desc* descs, void* stream, m1
     }
     m1_batch* B = new (std::nothrow) m1_batch();
     if (!B) return M1_ERR_NOMEM;
-    B->s = (cudaStream_t)stream;
+    B->user = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&B->s, cudaStreamNonBlocking) != cudaSuccess) {
+        delete B;
+        return M1_ERR_CUDA;
+    }
+    cudaStreamSynchronize(B->user);
     B->nprob = nprob;
     B->descs.assign(descs, descs + nprob);
     B->hp.resize(nprob);
@@ -648,6 +654,7 @@ m1_status m1_batch_destroy(m1_batch* B) {
     for (auto s : B->side) cudaStreamDestroy(s);
     for (auto e : B->ev) cudaEventDestroy(e);
     for (void* p : B->allocs) cudaFree(p);
+    if (B->s) cudaStreamDestroy(B->s);
     delete B;
     return M1_OK;
 }
@@ -679,9 +686,9 @@ static m1_status run(m1_batch* B, const Opts& o, bool use_graph) {
             cudaGraphExecDestroy(B->exec);
             B->exec = nullptr;
         }
-        cudaGraph_t graph;
-        if (cudaStreamBeginCapture(B->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-            return bfail(B, M1_ERR_CUDA, "capture failed");
+        cudaGraph_t graph = nullptr;
+        cudaError_t e0 = cudaStreamBeginCapture(B->s, cudaStreamCaptureModeThreadLocal);
+        if (e0 != cudaSuccess) return bfail(B, M1_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e0));
         cudaEventRecord(B->ev[B->ncls], B->s);
         for (int c = 0; c < B->ncls; ++c) {
             cudaStreamWaitEvent(B->side[c], B->ev[B->ncls], 0);
@@ -689,7 +696,12 @@ static m1_status run(m1_batch* B, const Opts& o, bool use_graph) {
             cudaEventRecord(B->ev[c], B->side[c]);
             cudaStreamWaitEvent(B->s, B->ev[c], 0);
         }
-        if (cudaStreamEndCapture(B->s, &graph) != cudaSuccess) return bfail(B, M1_ERR_CUDA, "capture failed");
+        const cudaError_t e1 = cudaStreamEndCapture(B->s, &graph);  // always ends the capture
+        if (e1 != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return bfail(B, M1_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e1));
+        }
         const cudaError_t e = cudaGraphInstantiate(&B->exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return bfail(B, M1_ERR_CUDA, "graph instantiation failed");
@@ -723,6 +735,7 @@ m1_status m1_batch_implicit_step(m1_batch* B, const double* dts, const m1_solver
         B->hp[k].g64.dt = dts[k];
         B->hp[k].g32.dt = (float)dts[k];
     }
+    if (cudaStreamSynchronize(B->user) != cudaSuccess) return bfail(B, M1_ERR_CUDA, "caller stream failed");
     if (cudaMemcpyAsync(B->dprobs, B->hp.data(), sizeof(Prob) * B->nprob, cudaMemcpyHostToDevice, B->s) != cudaSuccess)
         return bfail(B, M1_ERR_CUDA, "copy failed");
     cudaEvent_t e0, e1;

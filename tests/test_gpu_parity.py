@@ -240,3 +240,16 @@ def test_advection(m1mod, name):
     ctx.advect(p.dt)
     _, _, T = ctx.get_state()
     assert np.abs(T - ref.ravel()).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_krylov_is_deterministic(m1mod, prec):
+    # fixed-order reductions: the same solve twice gives bit-identical results
+    p = si.beam_lognormal_2d(96, 70, dt_factor=10.0)
+    ctx = ctx_for(m1mod, p)
+    b = np.random.default_rng(21).standard_normal(3 * p.ncell)
+    opts = m1mod.default_opts(precision=prec, gmres_rtol=1e-8, gmres_max=400)
+    x1, i1 = ctx.gmres_solve(p.dt, b, opts=opts, raise_on_fail=False)
+    x2, i2 = ctx.gmres_solve(p.dt, b, opts=opts, raise_on_fail=False)
+    assert i1.iters == i2.iters
+    assert np.array_equal(x1, x2)
