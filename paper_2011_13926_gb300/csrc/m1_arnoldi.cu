@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
     for (int i = wid; i <= kCols; i += (int)(blockDim.x >> 5)) {
         if (i <= j || i == kCols) {
             double t = 0.0;
+#pragma unroll 12
             for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(K.partials + (long long)b * (kCols + 1) + i);
             t = warp_sum_d(t);
             if (lane == 0) tot[i] = t;
