@@ -83,12 +83,14 @@ struct m1_ctx {
     double* ar_partials = nullptr;
     unsigned* ar_counter = nullptr;
     int* ar_reorth = nullptr;
+    int gs_grid32[kMaxRestart] = {}, gs_grid64[kMaxRestart] = {};  // Gram-Schmidt grid per Arnoldi step
     Scal sc{};
     double* scal_base = nullptr;
     int* singular = nullptr;
     unsigned long long* viol = nullptr;
     double* hpin = nullptr;  // pinned host scalars
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev_res[2] = {nullptr, nullptr};  // residual estimate of Arnoldi steps j (even, odd) on the host
     // per-kernel-class timers (m1_profile)
     bool prof = false;
     std::vector<cudaEvent_t> evs;
@@ -427,11 +429,12 @@ struct Ops32 {
     }
 };
 
-ArnoldiDev arnoldi_dev(m1_ctx* ctx) {
+ArnoldiDev arnoldi_dev(m1_ctx* ctx, bool fp32) {
     ArnoldiDev K;
     K.n = ctx->n;
     K.ld = ctx->ld;
-    K.blocks = 2 * 152;  // two resident blocks per SM, one wave
+    const int* grid = fp32 ? ctx->gs_grid32 : ctx->gs_grid64;
+    for (int j = 0; j < kMaxRestart; ++j) K.grid[j] = grid[j];
     K.H = ctx->sc.H;
     K.cs = ctx->sc.cs;
     K.sn = ctx->sc.sn;
@@ -491,26 +494,42 @@ m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, doub
     int k = 0;
     double e = beta;
     const long long ld = ctx->ld;
-    for (int j = 0; j < maxk; ++j) {
-        T* Vj = V + (long long)j * ld;
-        T* zj = Z ? Z + (long long)j * ld : z;  // flexible GMRES keeps every preconditioned vector
-        ops.M(Vj, zj);
-        ops.A(zj, w);
-        {
-            TK t(ctx, M1_K_ORTHO);
-            arnoldi_step(arnoldi_dev(ctx), V, w, j, s);
+    // Step j is enqueued before the host reads the residual estimate of step
+    // j - 1, so the device never idles on the convergence test. A step enqueued
+    // past the stopping one is discarded: it writes only V_{j+1}, z_j,
+    // Hessenberg column j, the rotation j and g[j], g[j+1], none of which the
+    // back substitution over the first j columns reads.
+    for (int j = 0; j <= maxk; ++j) {
+        if (j < maxk) {
+            T* Vj = V + (long long)j * ld;
+            T* zj = Z ? Z + (long long)j * ld : z;  // flexible GMRES keeps every preconditioned vector
+            ops.M(Vj, zj);
+            ops.A(zj, w);
+            {
+                TK t(ctx, M1_K_ORTHO);
+                arnoldi_step(arnoldi_dev(ctx, sizeof(T) == 4), V, w, j, s);
+            }
+            count(ctx, 3);
+            CK(cudaMemcpyAsync(ctx->hpin + 8 + 4 * (j & 1), sc.resid, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                               s));
+            CK(cudaEventRecord(ctx->ev_res[j & 1], s));
         }
-        count(ctx, 4);
-        CK(cudaMemcpyAsync(ctx->hpin, sc.resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CKS(sync(ctx));
-        k = j + 1;
-        e = ctx->hpin[0];
+        if (j == 0) continue;
+        const int jj = j - 1;  // the step inspected now
+        CK(cudaGetLastError());
+        CK(cudaEventSynchronize(ctx->ev_res[jj & 1]));
+        const double* r = ctx->hpin + 8 + 4 * (jj & 1);
+        k = jj + 1;
+        e = r[0];
         ctx->st.gmres_iters++;
-        // per Gram-Schmidt pass: dots read V_0..V_j and w, the update reads them
-        // again and writes one vector
-        ctx->st.ortho_bytes += (double)sizeof(T) * n * (2.0 * (j + 1) + 3.0) * (1.0 + ctx->hpin[2]);
-        if (!(e == e)) return fail(ctx, M1_ERR_NONFINITE, "non-finite GMRES residual estimate");
-        if (e <= target || ctx->hpin[1] == 0.0) break;
+        // the dots pass reads V_0..V_j and w (and once more for the second
+        // Gram-Schmidt pass); the update reads them and writes V_{j+1}
+        ctx->st.ortho_bytes += (double)sizeof(T) * n * ((jj + 2.0) * (1.0 + r[2]) + (jj + 3.0));
+        if (!(e == e)) {
+            cudaStreamSynchronize(s);
+            return fail(ctx, M1_ERR_NONFINITE, "non-finite GMRES residual estimate");
+        }
+        if (e <= target || r[1] == 0.0) break;
     }
     launch_backsolve(sc.H, sc.g, k, sc.y, s);
     CK(cudaMemsetAsync(ctx->tmp, 0, sizeof(double) * n, s));
@@ -775,7 +794,7 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
     AL(ctx->scal_base, nscal);
     AL(ctx->singular, 1);
     AL(ctx->viol, 1);
-    AL(ctx->ar_partials, (size_t)reduce_blocks() * (kPartCols + 1));
+    AL(ctx->ar_partials, (size_t)kMaxGsBlocks * (kPartCols + 1));
     AL(ctx->ar_counter, 1);
     AL(ctx->ar_reorth, 1);
 #undef AL
@@ -798,7 +817,9 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
     p += kMaxRestart;
     ctx->sc.resid = p;
     if (cudaMallocHost((void**)&ctx->hpin, 16 * sizeof(double)) != cudaSuccess) return cleanup(M1_ERR_NOMEM);
-    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
+    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_res[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_res[1], cudaEventDisableTiming) != cudaSuccess)
         return cleanup(M1_ERR_CUDA);
     if (cudaMemsetAsync(ctx->scal_base, 0, nscal * sizeof(double), ctx->s) != cudaSuccess) return cleanup(M1_ERR_CUDA);
     if (cudaMemsetAsync(ctx->ar_counter, 0, sizeof(unsigned), ctx->s) != cudaSuccess ||
@@ -807,6 +828,9 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
     if (!desc->gas_coupling && cudaMemsetAsync(ctx->B, 0, N * sizeof(double), ctx->s) != cudaSuccess)
         return cleanup(M1_ERR_CUDA);
     if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cleanup(M1_ERR_CUDA);
+    arnoldi_grid_table(ctx->n, true, ctx->gs_grid32);
+    arnoldi_grid_table(ctx->n, false, ctx->gs_grid64);
+    if (cudaGetLastError() != cudaSuccess) return cleanup(M1_ERR_CUDA);
     {
         // minimal traffic per launch: J v reads U, v, sigma_a, sigma_f, alpha (one
         // face per cell and axis), the time-n wave speeds when they are frozen
@@ -849,6 +873,8 @@ m1_status m1_destroy(m1_ctx* ctx) {
     if (ctx->hpin) cudaFreeHost(ctx->hpin);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (cudaEvent_t ev : ctx->ev_res)
+        if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
     delete ctx;
     return M1_OK;

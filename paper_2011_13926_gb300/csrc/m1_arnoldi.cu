@@ -1,30 +1,47 @@
 // m1_arnoldi.cu — fused Arnoldi step of restarted GMRES (classical
 // Gram-Schmidt with selective reorthogonalisation).
 //
-// One Arnoldi step j on the new vector w = A M^-1 V_j is four kernels:
-//   dots(pass 1): h = V_{0..j}^T w and ||w||^2 (basis vectors in groups of 8
-//     over a second grid dimension, w shared through L2); the last
-//     block to finish sums the per-block partials in a fixed order, tests
-//     ||w - V h||^2 = ||w||^2 - ||h||^2 against ||w||^2 / 2 (the Daniel-Gragg-
-//     Kaufman-Stewart criterion), and when no second pass is needed applies
-//     the Givens rotations to Hessenberg column j and updates the residual
-//     estimate |g_{j+1}|;
-//   update(pass 1): w - V h, written straight into V_{j+1} (normalised) when no
-//     second pass is needed, else back into w;
-//   dots/update(pass 2): the classical second Gram-Schmidt pass, only when the
-//     criterion asked for it (otherwise the blocks return at once).
+// One Arnoldi step j on the new vector w = A M^-1 V_j is three launches of one
+// kernel, each a single pass over V_0..V_j and w:
+//   dots: h1 = V^T w and ||w||^2. The last block to finish sums the
+//     per-block partials in a fixed order, tests ||w - V h1||^2 =
+//     ||w||^2 - ||h1||^2 against ||w||^2 / 2 (the Daniel-Gragg-Kaufman-Stewart
+//     criterion) and, when no second pass is needed, applies the Givens
+//     rotations to Hessenberg column j and updates the residual estimate
+//     |g_{j+1}|;
+//   dots of the residual (only when the criterion asked for it; otherwise the
+//     blocks return at once): w' = w - V h1 is formed on the fly, element by
+//     element, and h2 = V^T w', ||w'||^2 are accumulated in the same pass, so
+//     the classical second Gram-Schmidt pass costs one read of the basis, not
+//     two; the last block rotates column h1 + h2;
+//   update: V_{j+1} = (w - V h1 [- V h2]) / beta, with the same rounding of w'
+//     as the second dots pass.
+// Every pass is one grid-stride sweep in which a thread loads the 16-byte slot
+// q of all rows at once into registers (the rows are a compile-time count, so
+// the loads are issued back to back and the accumulation chains interleave).
+// The grid is as many blocks as fit on the SMs. For FP32 vectors the sums stay
+// in double-float FP32 arithmetic through the warp, block and cross-block
+// reductions and reach FP64 once per column: GB300 runs FP64 at a small
+// fraction of its FP32 rate, and FP64 reductions in every lane cost a fifth
+// of a dots pass.
 // FP32 vectors accumulate their dot products in double-float arithmetic
 // (each 16-byte group of four products by an FMA chain, then an error-free
-// TwoSum into a (hi, lo) pair), FP64 vectors in FP64; the
-// cross-block sums are FP64 in a fixed order, so results are reproducible.
+// TwoSum into a (hi, lo) pair), FP64 vectors in FP64; the cross-block sums
+// are FP64 in a fixed order, so results are reproducible run to run.
 // The Hessenberg least-squares problem stays in FP64 on the device.
 #include "m1_internal.h"
 
+#include <algorithm>
+
 namespace m1 {
 
-static constexpr int kArThreads = 256;
-static constexpr int kCols = kMaxRestart + 1;
+static constexpr int kOrThreads = 128;            // threads per block (one 16-byte slot each per row)
+static constexpr int kCols = kMaxRestart + 1;     // partial row: h_0..h_{kCols-1}, then ||w||^2
 static constexpr int kHLd = kMaxRestart + 1;
+static_assert(kCols + 1 == 32, "the last-block reduction reads partial rows of 32 eight-byte columns");
+static_assert(kOrThreads == 128, "the last-block reduction maps 128 threads onto 8 x 16 double pairs");
+
+enum GsMode : int { kDots = 0, kDotsResidual = 1, kUpdate = 2 };
 
 struct TwoF {
     float hi, lo;
@@ -38,6 +55,14 @@ __device__ __forceinline__ void two_sum_acc(TwoF& acc, float p, float perr) {
     acc.lo += err + perr;
 }
 
+// (a.hi, a.lo) + (b.hi, b.lo): TwoSum of the high parts, low parts added
+__device__ __forceinline__ TwoF df_add(TwoF a, TwoF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (b.hi - bb);
+    return TwoF{s, a.lo + b.lo + err};
+}
+
 template <class T> struct Acc;
 template <> struct Acc<double> {
     double v;
@@ -48,6 +73,13 @@ template <> struct Acc<double> {
         v = fma(a.y, b.y, v);
     }
     __device__ __forceinline__ double get() const { return v; }
+    // sum over the warp (valid in every lane)
+    __device__ __forceinline__ double warp_total() const {
+        double t = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        return t;
+    }
 };
 template <> struct Acc<float> {
     TwoF t;
@@ -66,13 +98,47 @@ template <> struct Acc<float> {
         two_sum_acc(t, p, 0.f);
     }
     __device__ __forceinline__ double get() const { return (double)t.hi + (double)t.lo; }
+    // sum over the warp by double-float additions in FP32 (valid in every lane)
+    __device__ __forceinline__ TwoF warp_total() const {
+        TwoF a = t;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, a.hi, o);
+            const float bl = __shfl_xor_sync(0xffffffffu, a.lo, o);
+            a = df_add(a, TwoF{bh, bl});
+        }
+        return a;
+    }
 };
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+// Per-column partial sums: double-float pairs for FP32 vectors (so that no
+// lane does FP64 work before the last block converts each column once: FP64
+// is a narrow pipe on this GPU), FP64 for FP64 vectors. Both are 8 bytes, a
+// partial row of 32 columns is 256 bytes, and two columns load as 16 bytes.
+template <class T> struct Part;
+template <> struct Part<float> {
+    using type = TwoF;
+    using pair = float4;
+    static __device__ __forceinline__ TwoF zero() { return TwoF{0.f, 0.f}; }
+    static __device__ __forceinline__ TwoF add(TwoF a, TwoF b) { return df_add(a, b); }
+    static __device__ __forceinline__ double to_double(TwoF a) { return (double)a.hi + (double)a.lo; }
+    static __device__ __forceinline__ void split(const float4& v, TwoF& c0, TwoF& c1) {
+        c0 = TwoF{v.x, v.y};
+        c1 = TwoF{v.z, v.w};
+    }
+};
+template <> struct Part<double> {
+    using type = double;
+    using pair = double2;
+    static __device__ __forceinline__ double zero() { return 0.0; }
+    static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double to_double(double a) { return a; }
+    static __device__ __forceinline__ void split(const double2& v, double& c0, double& c1) {
+        c0 = v.x;
+        c1 = v.y;
+    }
+};
+
 
 // Hessenberg column j from h (j+1 entries, shared memory) and beta = ||w - V h||:
 // apply the previous rotations (cs, sn staged in shared memory), form rotation
@@ -101,6 +167,7 @@ __device__ void givens_column(const ArnoldiDev& K, double* col, const double* sc
     K.resid[0] = fabs(s * gj);
     K.resid[1] = beta;
     K.nrm2[1] = beta * beta;
+    K.nrm2[2] = beta > 0.0 ? 1.0 / beta : 0.0;  // the update pass scales by it
 }
 
 // 16-byte vectors of the basis element type (rows of V start on 256-byte
@@ -114,138 +181,188 @@ template <> struct Vec<double> {
     using type = double2;
     static constexpr int W = 2;
 };
-__device__ __forceinline__ float comp(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
-__device__ __forceinline__ double comp(const double2& v, int k) { return k == 0 ? v.x : v.y; }
-__device__ __forceinline__ void setc(float4& v, int k, float x) {
-    if (k == 0) v.x = x; else if (k == 1) v.y = x; else if (k == 2) v.z = x; else v.w = x;
+
+// w -= a v, component-wise FMA
+__device__ __forceinline__ void fnma(float4& x, float a, const float4& v) {
+    x.x = fmaf(-a, v.x, x.x);
+    x.y = fmaf(-a, v.y, x.y);
+    x.z = fmaf(-a, v.z, x.z);
+    x.w = fmaf(-a, v.w, x.w);
 }
-__device__ __forceinline__ void setc(double2& v, int k, double x) {
-    if (k == 0) v.x = x; else v.y = x;
+__device__ __forceinline__ void fnma(double2& x, double a, const double2& v) {
+    x.x = fma(-a, v.x, x.x);
+    x.y = fma(-a, v.y, x.y);
+}
+__device__ __forceinline__ void scale(float4& x, float a) {
+    x.x *= a;
+    x.y *= a;
+    x.z *= a;
+    x.w *= a;
+}
+__device__ __forceinline__ void scale(double2& x, double a) {
+    x.x *= a;
+    x.y *= a;
 }
 
-// Dots: grid (bx, G). Block (x, y) accumulates the dot products of basis
-// vectors i in [8y, 8y + 8) with w (and ||w||^2 when y == 0) over its
-// element stride; the last block of the whole grid sums the partials.
-constexpr int kGroup = 8;
-
-template <class T>
-__global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const T* __restrict__ V,
-                                                             const T* __restrict__ w, int j, int pass) {
-    if (pass == 2 && *K.reorth == 0) return;
+// Gram-Schmidt pass of Arnoldi step j (mode: kDots, kDotsResidual, kUpdate).
+// NC >= j + 1 (a multiple of 4, at most 32) is the compile-time number of rows
+// a thread loads per 16-byte slot: all of them are issued before any is used,
+// so each thread keeps NC loads in flight. Rows above j re-read row j (an L1/L2
+// hit), their h is zero and their accumulators are never read, so the loops
+// carry no branch and the NC accumulation chains interleave.
+template <class T, int NC>
+__global__ void __launch_bounds__(kOrThreads) k_gram_schmidt(ArnoldiDev K, T* __restrict__ V,
+                                                             const T* __restrict__ w, int j, int mode) {
     using VT = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
-    __shared__ double red[kArThreads / 32][kGroup + 1];
-    __shared__ bool last;
-    const int i0 = blockIdx.y * kGroup;
-    const int ni = min(kGroup, j + 1 - i0);  // >= 1
-    const bool with_norm = blockIdx.y == 0;
-    Acc<T> acc[kGroup];
+    const int reorth = mode == kDots ? 0 : *K.reorth;
+    if (mode == kDotsResidual && reorth == 0) return;  // uniform over the grid
+    using P = Part<T>;
+    using PT = typename P::type;
+    __shared__ T h1s[kCols + 1], h2s[kCols + 1];
+    __shared__ PT red[kOrThreads / 32][kCols + 1];
+    __shared__ int last;
+    const int tid = threadIdx.x;
+    if (mode != kDots) {
+        if (tid <= kCols) {
+            h1s[tid] = tid <= j ? (T)K.h1[tid] : T(0);
+            h2s[tid] = (tid <= j && reorth) ? (T)K.h2[tid] : T(0);
+        }
+        __syncthreads();
+    }
+    const bool dots = mode != kUpdate;
+    const T inv = dots ? T(1) : (T)K.nrm2[2];
+    Acc<T> acc[NC];
     Acc<T> ww;
 #pragma unroll
-    for (int i = 0; i < kGroup; ++i) acc[i].zero();
+    for (int i = 0; i < NC; ++i) acc[i].zero();
     ww.zero();
     const long long n = K.n, ld = K.ld;
     const long long nv = n / W;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const T* Vg = V + (long long)i0 * ld;
-    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; q + stride < nv; q += 2 * stride) {  // two vectors in flight per row
-        const VT wa = reinterpret_cast<const VT*>(w)[q];
-        const VT wb = reinterpret_cast<const VT*>(w)[q + stride];
-        if (with_norm) {
-            ww.add_prod4(wa, wa);
-            ww.add_prod4(wb, wb);
-        }
+    const VT* rows[NC];
 #pragma unroll
-        for (int i = 0; i < kGroup; ++i)
-            if (i < ni) {
-                const VT va = reinterpret_cast<const VT*>(Vg + i * ld)[q];
-                const VT vb = reinterpret_cast<const VT*>(Vg + i * ld)[q + stride];
-                acc[i].add_prod4(va, wa);
-                acc[i].add_prod4(vb, wb);
+    for (int i = 0; i < NC; ++i) rows[i] = reinterpret_cast<const VT*>(V + (long long)min(i, j) * ld);
+    VT* out = reinterpret_cast<VT*>(V + (long long)(j + 1) * ld);
+    for (long long q = (long long)blockIdx.x * kOrThreads + tid; q < nv; q += (long long)gridDim.x * kOrThreads) {
+        VT v[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) v[i] = __ldg(rows[i] + q);
+        VT x = __ldg(reinterpret_cast<const VT*>(w) + q);
+        if (mode != kDots) {
+#pragma unroll
+            for (int i = 0; i < NC; ++i) fnma(x, h1s[i], v[i]);
+        }
+        if (dots) {
+            ww.add_prod4(x, x);
+#pragma unroll
+            for (int i = 0; i < NC; ++i) acc[i].add_prod4(v[i], x);
+        } else {
+            if (reorth) {
+#pragma unroll
+                for (int i = 0; i < NC; ++i) fnma(x, h2s[i], v[i]);
             }
+            scale(x, inv);
+            out[q] = x;
+        }
     }
-    for (; q < nv; q += stride) {
-        const VT wv = reinterpret_cast<const VT*>(w)[q];
-        if (with_norm) ww.add_prod4(wv, wv);
+    if (blockIdx.x == 0) {  // the n % W scalar tail
+        for (long long e = nv * W + tid; e < n; e += kOrThreads) {
+            T x = w[e];
+            if (mode != kDots)
+                for (int i = 0; i <= j; ++i) x = fma(-h1s[i], V[i * ld + e], x);
+            if (dots) {
+                ww.add_prod(x, x);
 #pragma unroll
-        for (int i = 0; i < kGroup; ++i)
-            if (i < ni) {
-                const VT vv = reinterpret_cast<const VT*>(Vg + i * ld)[q];
-                acc[i].add_prod4(vv, wv);
+                for (int i = 0; i < NC; ++i)
+                    if (i <= j) acc[i].add_prod(V[i * ld + e], x);
+            } else {
+                if (reorth)
+                    for (int i = 0; i <= j; ++i) x = fma(-h2s[i], V[i * ld + e], x);
+                V[(long long)(j + 1) * ld + e] = x * inv;
             }
-    }
-    if (blockIdx.x == 0) {  // scalar tail
-        for (long long e = nv * W + threadIdx.x; e < n; e += blockDim.x) {
-            const T we = w[e];
-            if (with_norm) ww.add_prod(we, we);
-#pragma unroll
-            for (int i = 0; i < kGroup; ++i)
-                if (i < ni) acc[i].add_prod(Vg[i * ld + e], we);
         }
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (!dots) return;
+    // block partials: h_0..h_j and ||x||^2
+    const int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
-    for (int i = 0; i < kGroup; ++i) {
-        if (i < ni) {
-            const double t = warp_sum_d(acc[i].get());
-            if (lane == 0) red[wid][i] = t;
+    for (int i = 0; i < NC; ++i) {
+        if (i <= j) {
+            const PT v = acc[i].warp_total();
+            if (lane == 0) red[wid][i] = v;
         }
     }
-    if (with_norm) {
-        const double t = warp_sum_d(ww.get());
-        if (lane == 0) red[wid][kGroup] = t;
+    {
+        const PT v = ww.warp_total();
+        if (lane == 0) red[wid][kCols] = v;
     }
     __syncthreads();
-    double* part = K.partials + (long long)blockIdx.x * (kCols + 1);
-    for (int i = threadIdx.x; i <= kGroup; i += blockDim.x) {
-        if (i < ni || (i == kGroup && with_norm)) {
-            double t = 0.0;
-            for (int qq = 0; qq < (int)(blockDim.x >> 5); ++qq) t += red[qq][i];
-            part[i < kGroup ? i0 + i : kCols] = t;
-        }
+    PT* part = reinterpret_cast<PT*>(K.partials) + (long long)blockIdx.x * (kCols + 1);
+    if (tid <= j || tid == kCols) {
+        PT v = red[0][tid];
+#pragma unroll
+        for (int qq = 1; qq < kOrThreads / 32; ++qq) v = P::add(v, red[qq][tid]);
+        part[tid] = v;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(K.counter, 1u) == gridDim.x * gridDim.y - 1);
+    if (tid == 0) last = (atomicAdd(K.counter, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!last) return;
-    // the last block: fixed-order sums of the partials over the x blocks
+    // the last block: fixed-order sums over the partial rows. Thread t adds the
+    // column pair (2 (t % 16), 2 (t % 16) + 1) of rows t / 16, t / 16 + 8, ...
+    // with 16-byte loads (columns above j hold stale values and are not used);
+    // each column reaches FP64 once
+    __shared__ PT tot8[8][kCols + 1];
     __shared__ double tot[kCols + 1];
-    for (int i = wid; i <= kCols; i += (int)(blockDim.x >> 5)) {
-        if (i <= j || i == kCols) {
-            double t = 0.0;
-#pragma unroll 12
-            for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(K.partials + (long long)b * (kCols + 1) + i);
-            t = warp_sum_d(t);
-            if (lane == 0) tot[i] = t;
+    {
+        const int c2 = tid & 15, r0 = tid >> 4;
+        const int nb = (int)gridDim.x;
+        PT s0 = P::zero(), s1 = P::zero();
+        const PT* base = reinterpret_cast<const PT*>(K.partials);
+#pragma unroll 8
+        for (int b = r0; b < nb; b += 8) {
+            const typename P::pair v = __ldcg(reinterpret_cast<const typename P::pair*>(base + (long long)b * (kCols + 1)) + c2);
+            PT c0, c1;
+            P::split(v, c0, c1);
+            s0 = P::add(s0, c0);
+            s1 = P::add(s1, c1);
         }
-    }
-    __syncthreads();  // tot[] complete
-    // stage the previous rotations and the column (h1 [+ h2]) in shared memory
-    __shared__ double col[kCols + 1], scs[kCols], ssn[kCols];
-    double* h = pass == 1 ? K.h1 : K.h2;
-    if (threadIdx.x <= j) {
-        const double hv = tot[threadIdx.x];
-        h[threadIdx.x] = hv;
-        col[threadIdx.x] = pass == 2 ? K.h1[threadIdx.x] + hv : hv;
-    }
-    if (threadIdx.x < j) {
-        scs[threadIdx.x] = K.cs[threadIdx.x];
-        ssn[threadIdx.x] = K.sn[threadIdx.x];
+        tot8[r0][2 * c2] = s0;
+        tot8[r0][2 * c2 + 1] = s1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid <= kCols) {
+        PT v = tot8[0][tid];
+#pragma unroll
+        for (int r = 1; r < 8; ++r) v = P::add(v, tot8[r][tid]);
+        tot[tid] = P::to_double(v);
+    }
+    __syncthreads();
+    // stage the previous rotations and the column (h1 [+ h2]) in shared memory
+    __shared__ double col[kCols + 1], scs[kCols], ssn[kCols];
+    double* h = mode == kDots ? K.h1 : K.h2;
+    if (tid <= j) {
+        const double hv = tot[tid];
+        h[tid] = hv;
+        col[tid] = mode == kDotsResidual ? K.h1[tid] + hv : hv;
+    }
+    if (tid < j) {
+        scs[tid] = K.cs[tid];
+        ssn[tid] = K.sn[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
         *K.counter = 0u;
         double hh = 0.0;
         for (int i = 0; i <= j; ++i) hh += tot[i] * tot[i];
         const double wn2 = tot[kCols];
         const double rest = wn2 - hh;
-        if (pass == 1 && !(rest > 0.5 * wn2)) {
-            *K.reorth = 1;  // second pass decides the column
+        if (mode == kDots && !(rest > 0.5 * wn2)) {
+            *K.reorth = 1;  // the second pass decides the column
             K.resid[2] = 1.0;
         } else {
-            if (pass == 1) {
+            if (mode == kDots) {
                 K.resid[2] = 0.0;
                 *K.reorth = 0;
             }
@@ -254,78 +371,56 @@ __global__ void __launch_bounds__(kArThreads) k_arnoldi_dots(ArnoldiDev K, const
     }
 }
 
-// Update: out = (w - sum_{i<=j} h_i V_i) * inv; the loop over i has a runtime
-// bound (unrolled by 4) so that the loads of the basis are not all hoisted.
-template <class T>
-__global__ void __launch_bounds__(kArThreads) k_arnoldi_update(ArnoldiDev K, T* __restrict__ V, T* __restrict__ w,
-                                                               int j, int pass) {
-    const int reorth = *K.reorth;
-    if (pass == 2 && reorth == 0) return;
-    using VT = typename Vec<T>::type;
-    constexpr int W = Vec<T>::W;
-    __shared__ T hs[kCols];
-    const double* h = pass == 1 ? K.h1 : K.h2;
-    if (threadIdx.x < kCols) hs[threadIdx.x] = threadIdx.x <= j ? (T)h[threadIdx.x] : T(0);
-    __syncthreads();
-    const bool final_pass = (pass == 2) || (reorth == 0);
-    const double b2 = K.nrm2[1];
-    const T inv = final_pass ? (b2 > 0.0 ? (T)(1.0 / sqrt(b2)) : T(0)) : T(1);
-    T* out = final_pass ? V + (long long)(j + 1) * K.ld : w;
-    const long long n = K.n, ld = K.ld;
-    const long long nv = n / W;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; q + stride < nv; q += 2 * stride) {  // two vectors in flight per row
-        VT xa = reinterpret_cast<const VT*>(w)[q];
-        VT xb = reinterpret_cast<const VT*>(w)[q + stride];
-#pragma unroll 4
-        for (int i = 0; i <= j; ++i) {
-            const VT va = reinterpret_cast<const VT*>(V + i * ld)[q];
-            const VT vb = reinterpret_cast<const VT*>(V + i * ld)[q + stride];
-            const T hi = hs[i];
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                setc(xa, k, fma(-hi, comp(va, k), comp(xa, k)));
-                setc(xb, k, fma(-hi, comp(vb, k), comp(xb, k)));
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            setc(xa, k, comp(xa, k) * inv);
-            setc(xb, k, comp(xb, k) * inv);
-        }
-        reinterpret_cast<VT*>(out)[q] = xa;
-        reinterpret_cast<VT*>(out)[q + stride] = xb;
+template <class T, int NC>
+static int gs_grid_one(int j, long long n, int sms) {
+    (void)j;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_schmidt<T, NC>, kOrThreads, 0) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    const long long nv = n / Vec<T>::W;
+    const long long tiles = std::max(1LL, (nv + kOrThreads - 1) / kOrThreads);
+    return (int)std::min<long long>({(long long)occ * sms, tiles, (long long)kMaxGsBlocks});
+}
+
+// the accumulator size of step j: j + 1 rounded up to a multiple of 4
+template <class T, int NC = 4>
+static int gs_grid_for(int j, long long n, int sms) {
+    if constexpr (NC < 32) {
+        if (j + 1 > NC) return gs_grid_for<T, NC + 4>(j, n, sms);
     }
-    for (; q < nv; q += stride) {
-        VT x = reinterpret_cast<const VT*>(w)[q];
-#pragma unroll 4
-        for (int i = 0; i <= j; ++i) {
-            const VT vv = reinterpret_cast<const VT*>(V + i * ld)[q];
-            const T hi = hs[i];
-#pragma unroll
-            for (int k = 0; k < W; ++k) setc(x, k, fma(-hi, comp(vv, k), comp(x, k)));
-        }
-#pragma unroll
-        for (int k = 0; k < W; ++k) setc(x, k, comp(x, k) * inv);
-        reinterpret_cast<VT*>(out)[q] = x;
-    }
-    if (blockIdx.x == 0) {
-        for (long long e = nv * W + threadIdx.x; e < n; e += blockDim.x) {
-            T x = w[e];
-            for (int i = 0; i <= j; ++i) x = fma(-hs[i], V[i * ld + e], x);
-            out[e] = x * inv;
-        }
-    }
+    return gs_grid_one<T, NC>(j, n, sms);
 }
 
 template <class T>
-static void arnoldi_step(const ArnoldiDev& K, T* V, T* w, int j, cudaStream_t s) {
-    const dim3 gd(K.blocks, (j + kGroup) / kGroup);  // ceil((j + 1) / 8) groups of basis vectors
-    for (int pass = 1; pass <= 2; ++pass) {
-        k_arnoldi_dots<T><<<gd, kArThreads, 0, s>>>(K, V, w, j, pass);
-        k_arnoldi_update<T><<<2 * K.blocks, kArThreads, 0, s>>>(K, V, w, j, pass);
+static void gs_grid_table(long long n, int* grid) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int j = 0; j < kMaxRestart; ++j) grid[j] = gs_grid_for<T>(j, n, sms);
+}
+
+void arnoldi_grid_table(long long n, bool fp32, int* grid) {
+    if (fp32)
+        gs_grid_table<float>(n, grid);
+    else
+        gs_grid_table<double>(n, grid);
+}
+
+template <class T, int NC>
+static void gs_launch(const ArnoldiDev& K, T* V, const T* w, int j, cudaStream_t s) {
+    const dim3 gd(K.grid[j]);
+    k_gram_schmidt<T, NC><<<gd, kOrThreads, 0, s>>>(K, V, w, j, kDots);
+    k_gram_schmidt<T, NC><<<gd, kOrThreads, 0, s>>>(K, V, w, j, kDotsResidual);
+    k_gram_schmidt<T, NC><<<gd, kOrThreads, 0, s>>>(K, V, w, j, kUpdate);
+}
+
+template <class T, int NC = 4>
+static void arnoldi_step(const ArnoldiDev& K, T* V, const T* w, int j, cudaStream_t s) {
+    if constexpr (NC < 32) {
+        if (j + 1 > NC) return arnoldi_step<T, NC + 4>(K, V, w, j, s);
     }
+    gs_launch<T, NC>(K, V, w, j, s);
 }
 
 void launch_arnoldi_step_f64(const ArnoldiDev& K, double* V, double* w, int j, cudaStream_t s) {

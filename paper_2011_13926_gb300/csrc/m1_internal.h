@@ -42,11 +42,14 @@ void launch_advect(const Dev<double>& g, const double* const u[3], double* Tout,
 // reorthogonalisation, Givens on the FP64 Hessenberg column in the last block)
 struct ArnoldiDev {
     long long n, ld;     // vector length, basis stride
-    int blocks;          // grid size of the dot/update kernels (partials has blocks * (kMaxRestart + 2))
+    int grid[kMaxRestart];  // blocks of the Gram-Schmidt passes of step j (partials has grid[j] rows of kMaxRestart + 2)
     double *H, *cs, *sn, *g, *resid, *h1, *h2, *nrm2, *partials;
     unsigned* counter;   // arrival counter of the last-block reduction (kept at 0 between launches)
     int* reorth;         // 1 when the second Gram-Schmidt pass runs
 };
+constexpr int kMaxGsBlocks = 4096;  // bound of ArnoldiDev::grid, rows of ArnoldiDev::partials
+// blocks of each Arnoldi step's passes for vectors of length n (occupancy of this device)
+void arnoldi_grid_table(long long n, bool fp32, int* grid);
 void launch_arnoldi_step_f64(const ArnoldiDev& K, double* V, double* w, int j, cudaStream_t s);
 void launch_arnoldi_step_f32(const ArnoldiDev& K, float* V, float* w, int j, cudaStream_t s);
 

@@ -58,22 +58,52 @@ __global__ void k_norm2(const T* __restrict__ x, long long n, double* __restrict
     }
 }
 
+// FP32 vector: squares accumulated per thread in double-float FP32 (TwoSum),
+// one FP64 conversion per thread, so the narrow FP64 pipe sees no per-element work
+__global__ void k_norm2_f32(const float* __restrict__ x, long long n, double* __restrict__ partials) {
+    __shared__ double red[kRedThreads / 32];
+    float hi = 0.f, lo = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        const float p = v * v;
+        const float pe = fmaf(v, v, -p);
+        const float s = hi + p;
+        const float bb = s - hi;
+        lo += ((hi - (s - bb)) + (p - bb)) + pe;
+        hi = s;
+    }
+    double t = (double)hi + (double)lo;
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double u = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        u = warp_sum(u);
+        if (threadIdx.x == 0) partials[blockIdx.x] = u;
+    }
+}
+
 void launch_norm2_f64(const double* x, long long n, double* partials, double* out, cudaStream_t s) {
     k_norm2<double><<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partials);
     launch_finish_sum(partials, kRedBlocks, 1, out, s);
 }
 void launch_norm2_f32(const float* x, long long n, double* partials, double* out, cudaStream_t s) {
-    k_norm2<float><<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partials);
+    k_norm2_f32<<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partials);
     launch_finish_sum(partials, kRedBlocks, 1, out, s);
 }
 
 template <class T>
 __global__ void k_scale_inv_sqrt(const T* __restrict__ x, const double* __restrict__ nrm2, T* __restrict__ y,
                                  long long n) {
-    const double nn = nrm2[0];
-    const double s = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    __shared__ T sc;
+    if (threadIdx.x == 0) {
+        const double nn = nrm2[0];
+        sc = (T)(nn > 0.0 ? 1.0 / sqrt(nn) : 0.0);
+    }
+    __syncthreads();
+    const T s = sc;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        y[i] = (T)((double)x[i] * s);
+        y[i] = x[i] * s;
 }
 void launch_scale_inv_sqrt_f64(const double* x, const double* nrm2, double* y, long long n, cudaStream_t s) {
     k_scale_inv_sqrt<double><<<kRedBlocks, kRedThreads, 0, s>>>(x, nrm2, y, n);
@@ -118,13 +148,51 @@ __global__ void k_lincomb_add(const T* __restrict__ Z, long long ld, int k, cons
         x[n - 1] = acc;
     }
 }
+// FP32 basis: the k-term combination in FP32 (FMA chain with the weights
+// rounded to FP32; it feeds an inner correction solved to a relative 1e-4),
+// then one FP64 add per element
+__global__ void k_lincomb_add_f32(const float* __restrict__ Z, long long ld, int k, const double* __restrict__ y,
+                                  double* __restrict__ x, long long n) {
+    __shared__ float ys[kMaxCols];
+    if (threadIdx.x < kMaxCols) ys[threadIdx.x] = threadIdx.x < k ? (float)y[threadIdx.x] : 0.f;
+    __syncthreads();
+    const long long n4 = n / 4;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+        for (int i = 0; i < k; ++i) {
+            const float4 z = __ldg(reinterpret_cast<const float4*>(Z + i * ld) + q);
+            const float yi = ys[i];
+            a.x = fmaf(yi, z.x, a.x);
+            a.y = fmaf(yi, z.y, a.y);
+            a.z = fmaf(yi, z.z, a.z);
+            a.w = fmaf(yi, z.w, a.w);
+        }
+        double2* xp = reinterpret_cast<double2*>(x) + 2 * q;
+        double2 x0 = xp[0], x1 = xp[1];
+        x0.x += (double)a.x;
+        x0.y += (double)a.y;
+        x1.x += (double)a.z;
+        x1.y += (double)a.w;
+        xp[0] = x0;
+        xp[1] = x1;
+    }
+    if (blockIdx.x == 0) {
+        for (long long e = n4 * 4 + threadIdx.x; e < n; e += blockDim.x) {
+            float a = 0.f;
+            for (int i = 0; i < k; ++i) a = fmaf(ys[i], Z[i * ld + e], a);
+            x[e] += (double)a;
+        }
+    }
+}
+
 void launch_lincomb_add_f64(const double* Z, long long ld, int k, const double* y, double* x, long long n,
                             cudaStream_t s) {
     k_lincomb_add<double><<<kRedBlocks, kRedThreads, 0, s>>>(Z, ld, k, y, x, n);
 }
 void launch_lincomb_add_f32_to_f64(const float* Z, long long ld, int k, const double* y, double* x, long long n,
                                    cudaStream_t s) {
-    k_lincomb_add<float><<<kRedBlocks, kRedThreads, 0, s>>>(Z, ld, k, y, x, n);
+    k_lincomb_add_f32<<<kRedBlocks, kRedThreads, 0, s>>>(Z, ld, k, y, x, n);
 }
 
 __global__ void k_axpby(double a, const double* __restrict__ x, double b, const double* __restrict__ y,
