@@ -84,6 +84,7 @@ struct m1_ctx {
     unsigned* ar_counter = nullptr;
     int* ar_reorth = nullptr;
     int gs_grid32[kMaxRestart] = {}, gs_grid64[kMaxRestart] = {};  // Gram-Schmidt grid per Arnoldi step
+    long long residual_partials = 0;                                 // entries of partials
     Scal sc{};
     double* scal_base = nullptr;
     int* singular = nullptr;
@@ -353,10 +354,9 @@ m1_status norm_f64(m1_ctx* ctx, const double* x, double* out) {
 
 // R = R(U) and its norm
 m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g, const double* U, double* R, double* nrm) {
-    const int nb = stencil_blocks(ctx->N);
     {
         TK t(ctx, M1_K_RESIDUAL);
-        launch_residual_f64(g, U, R, ctx->partials, nb, ctx->s);
+        const int nb = launch_residual_f64(g, U, R, ctx->partials, ctx->residual_partials, ctx->s);
         launch_finish_sum(ctx->partials, nb, 1, ctx->sc.nrm2, ctx->s);
     }
     count(ctx, 2);
@@ -789,7 +789,8 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
         AL(ctx->f32.lam_p[a], ctx->nfaces[a]);
         AL(ctx->f32.lam_m[a], ctx->nfaces[a]);
     }
-    AL(ctx->partials, (size_t)reduce_blocks() * kPartCols + stencil_blocks(N));
+    ctx->residual_partials = std::max((long long)reduce_blocks() * kPartCols, residual_partial_count(ctx->dim, ctx->d.n));
+    AL(ctx->partials, (size_t)ctx->residual_partials);
     const size_t nscal = 4 + 4 * kPartCols + (size_t)kHLd * kMaxRestart + 2 * kMaxRestart + 4;
     AL(ctx->scal_base, nscal);
     AL(ctx->singular, 1);

@@ -14,9 +14,13 @@ constexpr int kMaxRestart = 30;  // GMRES(m) basis bound, m <= 30
 // time-n face data: lambda+-, alpha on every face of every axis (FP64)
 void launch_faces_time_n(const Dev<double>& g, double* const lam_p[3], double* const lam_m[3],
                          double* const alpha[3], cudaStream_t s);
-// R(U); optional FP64 partial sums of R^2 per block into partials (nblocks entries)
-void launch_residual_f64(const Dev<double>& g, const double* U, double* R, double* partials, int nblocks,
-                         cudaStream_t s);
+// residual of every cell and, when partials is not null, the partial sums of
+// squares (one per block); returns the number of partials written (at most
+// capacity: the 2D tiled kernel is used when its tile count fits)
+int launch_residual_f64(const Dev<double>& g, const double* U, double* R, double* partials, long long capacity,
+                        cudaStream_t s);
+// partial-sum entries the residual may need for this grid
+long long residual_partial_count(int dim, const int n[3]);
 void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s);
 void launch_jv_f32(const Dev<float>& g, const float* U, const float* v, float* Jv, cudaStream_t s);
 void launch_diag_f64(const Dev<double>& g, const double* U, double* blocks, cudaStream_t s);

@@ -138,8 +138,7 @@ extern "C" m1_status m1_residual_noalloc(const m1_grid_desc* d, double dt, const
     double* nrm = partials + kPartials;
 
     launch_faces_time_n(g, lam_p, lam_m, alpha, s);
-    const int nb = stencil_blocks(N);
-    launch_residual_f64(g, U, R, partials, nb, s);
+    const int nb = launch_residual_f64(g, U, R, partials, kPartials, s);
     launch_finish_sum(partials, nb, 1, nrm, s);
     if (norm2 && cudaMemcpyAsync(norm2, nrm, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return M1_ERR_CUDA;

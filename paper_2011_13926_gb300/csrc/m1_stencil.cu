@@ -8,6 +8,9 @@
 
 #include "m1_internal.h"
 
+#include <algorithm>
+#include <type_traits>
+
 namespace m1 {
 
 static constexpr int kThreads = 256;
@@ -40,7 +43,26 @@ void launch_faces_time_n(const Dev<double>& g, double* const lam_p[3], double* c
     }
 }
 
-// ------------------------------------------------------------------ block reduction helper
+// ------------------------------------------------------------------ block reduction helpers
+// sum over a block of nthreads threads (any shape; tid the linear thread
+// index, nthreads a multiple of 32), fixed order; valid in tid 0
+__device__ __forceinline__ double block_sum_linear(double v, int tid, int nthreads) {
+    __shared__ double red_l[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = tid & 31, w = tid >> 5;
+    if (lane == 0) red_l[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < (nthreads >> 5) ? red_l[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+
+// sum over a one-dimensional block; valid in thread 0
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double red[32];
 #pragma unroll
@@ -98,25 +120,38 @@ __global__ void __launch_bounds__(kThreads) k_jv(Dev<R> g, const R* __restrict__
     for (int k = 0; k < NU; ++k) Jv[k * g.N + idx] = out[k].d;
 }
 
-// ------------------------------------------------------------------ J v, 2D tiled
-// 2D J v with the closure of every cell computed once per CTA: a 32 x 8 tile
-// plus a one-cell halo (axis neighbours only; ghosts by the boundary rules) is
-// staged in shared memory as dual numbers (E, F, P), then each thread forms
-// its four HLL faces and sources. For frozen (time-n) or fixed wave speeds.
+// ------------------------------------------------------------------ 2D tiled residual and J v
+// 2D residual (S = R) or J v (S = Dual<R>, the derivative parts) with the
+// closure of every cell computed once per CTA: a 32 x 8 tile plus a one-cell
+// halo (axis neighbours only; ghosts by the boundary rules) is staged in
+// shared memory as (E, F, P), then each thread forms its four HLL faces and
+// the sources in the order of cell_residual. Terms that do not depend on U
+// (U^n, the emission B, the source S) enter the residual only: they carry no
+// derivative. For frozen (time-n) or fixed wave speeds. The residual variant
+// also writes the block's partial sum of squares.
 constexpr int kTX = 32, kTY = 8;
 
-template <class R>
-struct CellD {
-    Dual<R> E, Fx, Fy, Pxx, Pxy, Pyy;
+template <class S>
+struct CellT {
+    S E, Fx, Fy, Pxx, Pxy, Pyy;
 };
 
-template <class R, bool GAS>
-__global__ void __launch_bounds__(kTX* kTY) k_jv2d_tiled(Dev<R> g, const R* __restrict__ U, const R* __restrict__ v,
-                                                        R* __restrict__ Jv) {
-    __shared__ CellD<R> cs[kTY + 2][kTX + 2];
+template <class S, bool GAS, bool RES>
+__global__ void __launch_bounds__(kTX* kTY)
+    k_stencil2d_tiled(Dev<typename RealOf<S>::type> g, const typename RealOf<S>::type* __restrict__ U,
+                      const typename RealOf<S>::type* __restrict__ v, typename RealOf<S>::type* __restrict__ out,
+                      double* __restrict__ partials) {
+    using R = typename RealOf<S>::type;
+    using L = std::conditional_t<RES, LoadPlain<R>, LoadDir<R>>;
+    __shared__ CellT<S> cs[kTY + 2][kTX + 2];
     const int nx = g.n[0], ny = g.n[1];
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-    LoadDir<R> ld{U, v, g.N};
+    L ld;
+    if constexpr (RES) {
+        ld = L{U, g.N};
+    } else {
+        ld = L{U, v, g.N};
+    }
     const int tid = threadIdx.y * kTX + threadIdx.x;
     for (int t = tid; t < (kTX + 2) * (kTY + 2); t += kTX * kTY) {
         const int hx = t % (kTX + 2), hy = t / (kTX + 2);
@@ -125,23 +160,23 @@ __global__ void __launch_bounds__(kTX* kTY) k_jv2d_tiled(Dev<R> g, const R* __re
         if (!(in_x || in_y)) continue;              // corner: no face needs it
         if (gx > nx || gy > ny) continue;           // beyond the last ghost of a ragged tile
         if ((hx == 0 || hx == kTX + 1) && (hy == 0 || hy == kTY + 1)) continue;  // tile corners
-        St<Dual<R>, 2> u;
+        St<S, 2> u;
         if (in_x && in_y) {
             const long long idx = (long long)gy * nx + gx;
-            u = load_state<Dual<R>, 2, false>(ld, idx, idx);
+            u = load_state<S, 2, false>(ld, idx, idx);
         } else {
             // ghost of the adjacent boundary cell along the axis that left the domain
             const int a = in_x ? 1 : 0;
             const int side = a == 0 ? (gx < 0 ? 0 : 1) : (gy < 0 ? 0 : 1);
             int cc[3] = {a == 0 ? (gx < 0 ? 0 : nx - 1) : gx, a == 1 ? (gy < 0 ? 0 : ny - 1) : gy, 0};
             const long long idx = (long long)cc[1] * nx + cc[0];
-            const St<Dual<R>, 2> self = load_state<Dual<R>, 2, false>(ld, idx, idx);
+            const St<S, 2> self = load_state<S, 2, false>(ld, idx, idx);
             R sig_nb;
             bool bnd;
-            u = neighbour<Dual<R>, 2, false>(g, ld, self, idx, cc, a, side, sig_nb, bnd);
+            u = neighbour<S, 2, false>(g, ld, self, idx, cc, a, side, sig_nb, bnd);
         }
-        const Cl<Dual<R>, 2> k = closure(u, g.c);
-        CellD<R> c;
+        const Cl<S, 2> k = closure(u, g.c);
+        CellT<S> c;
         c.E = u.E;
         c.Fx = u.F[0];
         c.Fy = u.F[1];
@@ -152,86 +187,114 @@ __global__ void __launch_bounds__(kTX* kTY) k_jv2d_tiled(Dev<R> g, const R* __re
     }
     __syncthreads();
     const int ix = x0 + threadIdx.x, iy = y0 + threadIdx.y;
-    if (ix >= nx || iy >= ny) return;
-    const long long idx = (long long)iy * nx + ix;
-    const int coord[3] = {ix, iy, 0};
-    const CellD<R>& me = cs[threadIdx.y + 1][threadIdx.x + 1];
-    const R sig_self = g.sig_f[idx];
-    const R dt = g.dt, c = g.c, c2 = g.c * g.c;
-    Dual<R> RE = me.E, RFx = me.Fx, RFy = me.Fy;  // the identity part of J (U - U^n)
-    Dual<R> phi[2] = {cst<Dual<R>>(R(0)), cst<Dual<R>>(R(0))};
+    double ss = 0.0;
+    if (ix < nx && iy < ny) {
+        const long long idx = (long long)iy * nx + ix;
+        const int coord[3] = {ix, iy, 0};
+        const CellT<S>& me = cs[threadIdx.y + 1][threadIdx.x + 1];
+        const R sig_self = g.sig_f[idx];
+        const R dt = g.dt, c = g.c, c2 = g.c * g.c;
+        S RE = me.E, RFx = me.Fx, RFy = me.Fy;
+        if constexpr (RES) {
+            RE = RE - g.Un[idx];
+            RFx = RFx - g.Un[g.N + idx];
+            RFy = RFy - g.Un[2 * g.N + idx];
+        }
+        S phi[2] = {cst<S>(R(0)), cst<S>(R(0))};
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < 2; ++a) {
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const int hx = threadIdx.x + 1 + (a == 0 ? (side ? 1 : -1) : 0);
-            const int hy = threadIdx.y + 1 + (a == 1 ? (side ? 1 : -1) : 0);
-            const CellD<R>& nb = cs[hy][hx];
-            const CellD<R>& L = side ? me : nb;
-            const CellD<R>& Rr = side ? nb : me;
-            const int ca = coord[a] + (side ? 1 : -1);
-            const bool inside = ca >= 0 && ca < g.n[a];
-            const bool periodic = g.bc[a][side] == BC_PERIODIC;
-            const bool boundary = !inside && !periodic;
-            R sig_nb = sig_self;
-            if (inside)
-                sig_nb = g.sig_f[idx + (side ? g.stride[a] : -g.stride[a])];
-            else if (periodic)
-                sig_nb = g.sig_f[idx + (side ? -(long long)(g.n[a] - 1) : (long long)(g.n[a] - 1)) * g.stride[a]];
-            const long long fidx = face_index(g.n, coord, a, coord[a] + side);
-            R lp, lm;
-            if (g.fixed_eigs) {
-                lp = c;
-                lm = -c;
-            } else {
-                lp = g.lam_p[a][fidx];
-                lm = g.lam_m[a][fidx];
-            }
-            const R den = lp - lm;
-            const R inv = den >= Tiny<R>::den() ? R(1) / den : R(0);
-            const R pm = lp * lm * inv;
-            const Dual<R> FaL = a == 0 ? L.Fx : L.Fy, FaR = a == 0 ? Rr.Fx : Rr.Fy;
-            const Dual<R> Fs = (lp * FaL - lm * FaR) * inv + pm * (Rr.E - L.E);
-            // P*_b = c^2 (lp P_ab,L - lm P_ab,R) inv + pm (F_b,R - F_b,L)
-            const Dual<R> PaxL = a == 0 ? L.Pxx : L.Pxy, PaxR = a == 0 ? Rr.Pxx : Rr.Pxy;
-            const Dual<R> PayL = a == 0 ? L.Pxy : L.Pyy, PayR = a == 0 ? Rr.Pxy : Rr.Pyy;
-            const Dual<R> Psx = c2 * (lp * PaxL - lm * PaxR) * inv + pm * (Rr.Fx - L.Fx);
-            const Dual<R> Psy = c2 * (lp * PayL - lm * PayR) * inv + pm * (Rr.Fy - L.Fy);
-            const R w = (side ? dt : -dt) * g.inv_dx[a];
-            RE = RE + (w * g.alpha[a][fidx]) * Fs;
-            RFx = RFx + w * Psx;
-            RFy = RFy + w * Psy;
-            if (g.wb) {
-                if (boundary && g.wb_boundary) {
-                    const Dual<R> PR = a == 0 ? Rr.Pxx : Rr.Pyy, PL = a == 0 ? L.Pxx : L.Pyy;
-                    phi[a] = phi[a] - c * g.inv_dx[a] * (PR - PL);
+            for (int side = 0; side < 2; ++side) {
+                const int hx = threadIdx.x + 1 + (a == 0 ? (side ? 1 : -1) : 0);
+                const int hy = threadIdx.y + 1 + (a == 1 ? (side ? 1 : -1) : 0);
+                const CellT<S>& nb = cs[hy][hx];
+                const CellT<S>& Lc = side ? me : nb;
+                const CellT<S>& Rc = side ? nb : me;
+                const int ca = coord[a] + (side ? 1 : -1);
+                const bool inside = ca >= 0 && ca < g.n[a];
+                const bool periodic = g.bc[a][side] == BC_PERIODIC;
+                const bool boundary = !inside && !periodic;
+                R sig_nb = sig_self;
+                if (inside)
+                    sig_nb = g.sig_f[idx + (side ? g.stride[a] : -g.stride[a])];
+                else if (periodic)
+                    sig_nb = g.sig_f[idx + (side ? -(long long)(g.n[a] - 1) : (long long)(g.n[a] - 1)) * g.stride[a]];
+                const long long fidx = face_index(g.n, coord, a, coord[a] + side);
+                R lp, lm;
+                if (g.fixed_eigs) {
+                    lp = c;
+                    lm = -c;
                 } else {
-                    phi[a] = phi[a] + (R(0.25) * (sig_self + sig_nb)) * (FaL + FaR);
+                    lp = g.lam_p[a][fidx];
+                    lm = g.lam_m[a][fidx];
+                }
+                const R den = lp - lm;
+                const R inv = den >= Tiny<R>::den() ? R(1) / den : R(0);
+                const R pm = lp * lm * inv;
+                const S FaL = a == 0 ? Lc.Fx : Lc.Fy, FaR = a == 0 ? Rc.Fx : Rc.Fy;
+                const S Fs = (lp * FaL - lm * FaR) * inv + pm * (Rc.E - Lc.E);
+                // P*_b = c^2 (lp P_ab,L - lm P_ab,R) inv + pm (F_b,R - F_b,L)
+                const S PaxL = a == 0 ? Lc.Pxx : Lc.Pxy, PaxR = a == 0 ? Rc.Pxx : Rc.Pxy;
+                const S PayL = a == 0 ? Lc.Pxy : Lc.Pyy, PayR = a == 0 ? Rc.Pxy : Rc.Pyy;
+                const S Psx = c2 * (lp * PaxL - lm * PaxR) * inv + pm * (Rc.Fx - Lc.Fx);
+                const S Psy = c2 * (lp * PayL - lm * PayR) * inv + pm * (Rc.Fy - Lc.Fy);
+                const R w = (side ? dt : -dt) * g.inv_dx[a];
+                RE = RE + (w * g.alpha[a][fidx]) * Fs;
+                RFx = RFx + w * Psx;
+                RFy = RFy + w * Psy;
+                if (g.wb) {
+                    if (boundary && g.wb_boundary) {
+                        const S PR = a == 0 ? Rc.Pxx : Rc.Pyy, PL = a == 0 ? Lc.Pxx : Lc.Pyy;
+                        phi[a] = phi[a] - c * g.inv_dx[a] * (PR - PL);
+                    } else {
+                        phi[a] = phi[a] + (R(0.25) * (sig_self + sig_nb)) * (FaL + FaR);
+                    }
                 }
             }
         }
-    }
-    const R cdt = c * dt;
-    if (g.wb) {
-        RFx = RFx + cdt * (R(0.5) * phi[0]);
-        RFy = RFy + cdt * (R(0.5) * phi[1]);
-    } else {
-        RFx = RFx + cdt * (sig_self * me.Fx);
-        RFy = RFy + cdt * (sig_self * me.Fy);
-    }
-    const R ka = cdt * g.sig_a[idx];
-    if constexpr (GAS) {
-        const Dual<R> T = ld.get(3, idx, idx);
-        const Dual<R> T2 = T * T;
-        const Dual<R> exch = ka * (g.a_r * (T2 * T2) - me.E);
+        const R cdt = c * dt;
+        if (g.wb) {
+            RFx = RFx + cdt * (R(0.5) * phi[0]);
+            RFy = RFy + cdt * (R(0.5) * phi[1]);
+        } else {
+            RFx = RFx + cdt * (sig_self * me.Fx);
+            RFy = RFy + cdt * (sig_self * me.Fy);
+        }
+        S emis;
+        S T;
+        if constexpr (GAS) {
+            T = ld.get(3, idx, idx);
+            const S T2 = T * T;
+            emis = g.a_r * (T2 * T2);
+        } else {
+            emis = cst<S>(RES && g.B ? g.B[idx] : R(0));
+        }
+        const S exch = (cdt * g.sig_a[idx]) * (emis - me.E);
         RE = RE - exch;
-        Jv[3 * g.N + idx] = (g.rho_cv[idx] * T + exch).d;
-    } else {
-        RE = RE + ka * me.E;  // -c sigma_a dt (B - E): only E varies
+        if constexpr (RES) {
+            if (g.S) RE = RE - dt * g.S[idx];
+            out[idx] = RE;
+            out[g.N + idx] = RFx;
+            out[2 * g.N + idx] = RFy;
+            ss = (double)RE * RE + (double)RFx * RFx + (double)RFy * RFy;
+            if constexpr (GAS) {
+                const S RT = g.rho_cv[idx] * (T - g.Un[3 * g.N + idx]) + exch;
+                out[3 * g.N + idx] = RT;
+                ss += (double)RT * RT;
+            }
+        } else {
+            out[idx] = RE.d;
+            out[g.N + idx] = RFx.d;
+            out[2 * g.N + idx] = RFy.d;
+            if constexpr (GAS) out[3 * g.N + idx] = (g.rho_cv[idx] * T + exch).d;
+        }
     }
-    Jv[idx] = RE.d;
-    Jv[g.N + idx] = RFx.d;
-    Jv[2 * g.N + idx] = RFy.d;
+    if constexpr (RES) {
+        if (partials) {
+            const double t = block_sum_linear(ss, tid, kTX * kTY);
+            if (tid == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ point blocks
@@ -274,13 +337,33 @@ __global__ void __launch_bounds__(kThreads) k_diag(Dev<R> g, const R* __restrict
         }                             \
     } while (0)
 
-void launch_residual_f64(const Dev<double>& g, const double* U, double* R, double* partials, int nblocks,
-                         cudaStream_t s) {
+static bool tiled2d(const Dev<double>& g) { return g.dim == 2 && !(g.implicit_eigs && !g.fixed_eigs); }
+
+long long residual_partial_count(int dim, const int n[3]) {
+    const long long N = (long long)n[0] * n[1] * n[2];
+    long long nb = stencil_blocks(N);
+    if (dim == 2) nb = std::max(nb, (long long)((n[0] + kTX - 1) / kTX) * ((n[1] + kTY - 1) / kTY));
+    return nb;
+}
+
+int launch_residual_f64(const Dev<double>& g, const double* U, double* R, double* partials, long long capacity,
+                        cudaStream_t s) {
+    if (tiled2d(g)) {
+        const dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
+        const long long nb = (long long)grid.x * grid.y;
+        if (!partials || nb <= capacity) {
+            if (g.gas)
+                k_stencil2d_tiled<double, true, true><<<grid, block, 0, s>>>(g, U, nullptr, R, partials);
+            else
+                k_stencil2d_tiled<double, false, true><<<grid, block, 0, s>>>(g, U, nullptr, R, partials);
+            return (int)nb;
+        }
+    }
     const int nb = stencil_blocks(g.N);
-    (void)nblocks;
 #define CALL(D, G) k_residual<D, G><<<nb, kThreads, 0, s>>>(g, U, R, partials)
     M1_DISPATCH(g.dim, g.gas, CALL);
 #undef CALL
+    return nb;
 }
 
 template <class R>
@@ -288,9 +371,9 @@ static bool jv_tiled(const Dev<R>& g, const R* U, const R* v, R* Jv, cudaStream_
     if (g.dim != 2 || (g.implicit_eigs && !g.fixed_eigs)) return false;
     dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
     if (g.gas)
-        k_jv2d_tiled<R, true><<<grid, block, 0, s>>>(g, U, v, Jv);
+        k_stencil2d_tiled<Dual<R>, true, false><<<grid, block, 0, s>>>(g, U, v, Jv, nullptr);
     else
-        k_jv2d_tiled<R, false><<<grid, block, 0, s>>>(g, U, v, Jv);
+        k_stencil2d_tiled<Dual<R>, false, false><<<grid, block, 0, s>>>(g, U, v, Jv, nullptr);
     return true;
 }
 

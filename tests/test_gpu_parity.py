@@ -172,6 +172,8 @@ def test_implicit_step_fp64(m1mod, name):
     opts = m1mod.default_opts(newton_rtol=1e-10, gmres_rtol=1e-8, advance=0)
     st, info = ctx.implicit_step(p.dt, opts)
     assert info.converged
+    # the device norm of R(U^n) (block partial sums, fixed-order finish) is the oracle's
+    assert info.res0 == pytest.approx(ref.res0, rel=1e-12)
     u = ctx.get_solution()
     # the GPU result solves the oracle's system: relative residual <= 1e-8
     assert np.linalg.norm(s.residual(u)) <= 1e-8 * ref.res0
