@@ -77,6 +77,8 @@ struct m1_ctx {
     m1_nn* nn = nullptr;        // learned preconditioner (not owned)
     float* logsig = nullptr;    // its opacity channel
     float* Z32 = nullptr;       // flexible-GMRES basis of preconditioned vectors
+    double* pj64 = nullptr;     // dP/dU at the Newton iterate (2D frozen wave speeds), FP64
+    float* pj32 = nullptr;      // the same in FP32
     float *pair_x = nullptr, *pair_t = nullptr;  // staging of one training pair (4N and 3N floats)
     double* vel[3] = {nullptr, nullptr, nullptr};  // prescribed face velocities (gas advection)
     double* partials = nullptr;
@@ -367,6 +369,21 @@ m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g, const double* U, doub
     return M1_OK;
 }
 
+// dP/dU at U for the linear J v (2D, frozen or fixed wave speeds); false
+// when J v stays on dual numbers
+m1_status pressure_jacobian(m1_ctx* ctx, const Dev<double>& g, const double* U, bool fp32, bool* made) {
+    *made = false;
+    if (!jv_linear_available(g)) return M1_OK;
+    const size_t planes = (size_t)pressure_jacobian_size(g);
+    CKS(dalloc(ctx, &ctx->pj64, planes * ctx->N));
+    if (fp32) CKS(dalloc(ctx, &ctx->pj32, planes * ctx->N));
+    TK t(ctx, M1_K_PC_BUILD);
+    launch_pressure_jacobian(g, U, ctx->pj64, fp32 ? ctx->pj32 : nullptr, ctx->s);
+    count(ctx, 1);
+    *made = true;
+    return M1_OK;
+}
+
 m1_status build_precond(m1_ctx* ctx, const Dev<double>& g, const double* U) {
     TK t(ctx, M1_K_PC_BUILD);
     launch_diag_f64(g, U, ctx->blocks, ctx->s);
@@ -386,9 +403,13 @@ struct Ops64 {
     Dev<double> g;
     const double* U;
     bool precond;
+    const double* pj = nullptr;  // dP/dU at U: J v as a linear stencil, else by dual numbers
     void A(const double* in, double* out) {
         TK t(ctx, M1_K_JV64);
-        launch_jv_f64(g, U, in, out, ctx->s);
+        if (pj)
+            launch_jv_linear_f64(g, U, pj, in, out, ctx->s);
+        else
+            launch_jv_f64(g, U, in, out, ctx->s);
         count(ctx, 1);
         ctx->st.jv_calls++;
     }
@@ -408,9 +429,13 @@ struct Ops32 {
     const float* U;
     bool precond;
     bool learned = false;
+    const float* pj = nullptr;  // dP/dU at U in FP32: J v as a linear stencil, else by dual numbers
     void A(const float* in, float* out) {
         TK t(ctx, M1_K_JV32);
-        launch_jv_f32(g, U, in, out, ctx->s);
+        if (pj)
+            launch_jv_linear_f32(g, U, pj, in, out, ctx->s);
+        else
+            launch_jv_f32(g, U, in, out, ctx->s);
         count(ctx, 1);
         ctx->st.jv_calls++;
     }
@@ -839,8 +864,12 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
         // U^n and the emission (or T^n) and the source.
         const double nu = ctx->nu, dim = ctx->dim;
         const double fields = 2.0 + dim + (desc->implicit_eigs ? 0.0 : 2.0 * dim) + (desc->gas_coupling ? 1.0 : 0.0);
-        ctx->st.bytes_per_jv = (double)N * 8.0 * (3.0 * nu + fields);
-        ctx->st.bytes_per_jv32 = (double)N * 4.0 * (3.0 * nu + fields);
+        // the linear 2D J v reads v and dP/dU (9 planes, + d(a_r T^4)/dT with
+        // gas) instead of U and v
+        const bool lin = desc->dim == 2 && (desc->fixed_eigs || !desc->implicit_eigs);
+        const double jv_fields = lin ? 2.0 * nu + fields + 9.0 + (desc->gas_coupling ? 1.0 : 0.0) : 3.0 * nu + fields;
+        ctx->st.bytes_per_jv = (double)N * 8.0 * jv_fields;
+        ctx->st.bytes_per_jv32 = (double)N * 4.0 * jv_fields;
         ctx->st.bytes_per_residual = (double)N * 8.0 * (3.0 * nu + fields + (desc->gas_coupling ? 0.0 : 1.0));
     }
     *out = ctx;
@@ -855,7 +884,7 @@ m1_status m1_destroy(m1_ctx* ctx) {
                     ctx->delta, ctx->rhs, ctx->w, ctx->z, ctx->tmp, ctx->V, ctx->xacc, ctx->blocks, ctx->binv,
                     ctx->binv32, ctx->V32, ctx->w32, ctx->z32, ctx->U32, ctx->tmp32, ctx->Fstar, ctx->linework,
                     ctx->partials, ctx->scal_base, ctx->singular, ctx->viol, ctx->ar_partials,
-                    ctx->ar_counter, ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t};
+                    ctx->ar_counter, ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int a = 0; a < 3; ++a) {
@@ -1052,15 +1081,25 @@ m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double
     CKS(ensure_work(ctx));
     CKS(copy_in(ctx, ctx->U, U, sizeof(double) * ctx->n, mem));
     CKS(copy_in(ctx, ctx->z, v, sizeof(double) * ctx->n, mem));
+    // the operator the solvers apply: a linear stencil of dP/dU at U where
+    // available (2D, frozen or fixed wave speeds), else dual numbers
+    bool lin = false;
+    CKS(pressure_jacobian(ctx, dev64(ctx, dt), ctx->U, precision == M1_PREC_MIXED, &lin));
     if (precision == M1_PREC_MIXED) {
         CKS(ensure_work32(ctx));
         launch_f64_to_f32(ctx->U, ctx->U32, ctx->n, ctx->s);
         launch_f64_to_f32(ctx->z, ctx->z32, ctx->n, ctx->s);
-        launch_jv_f32(dev32(ctx, dt), ctx->U32, ctx->z32, ctx->w32, ctx->s);
+        if (lin)
+            launch_jv_linear_f32(dev32(ctx, dt), ctx->U32, ctx->pj32, ctx->z32, ctx->w32, ctx->s);
+        else
+            launch_jv_f32(dev32(ctx, dt), ctx->U32, ctx->z32, ctx->w32, ctx->s);
         launch_f32_to_f64(ctx->w32, ctx->w, ctx->n, ctx->s);
         count(ctx, 4);
     } else {
-        launch_jv_f64(dev64(ctx, dt), ctx->U, ctx->z, ctx->w, ctx->s);
+        if (lin)
+            launch_jv_linear_f64(dev64(ctx, dt), ctx->U, ctx->pj64, ctx->z, ctx->w, ctx->s);
+        else
+            launch_jv_f64(dev64(ctx, dt), ctx->U, ctx->z, ctx->w, ctx->s);
         count(ctx, 1);
     }
     ctx->st.jv_calls++;
@@ -1091,6 +1130,9 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
     if (learned) CKS(dalloc(ctx, &ctx->Z32, (size_t)ctx->ld * (kMaxRestart + 1)));
     Dev<double> g = dev64(ctx, dt);
     Ops64 ops{ctx, g, Ud, pre};
+    bool lin = false;
+    CKS(pressure_jacobian(ctx, g, Ud, o->precision == M1_PREC_MIXED, &lin));
+    if (lin) ops.pj = ctx->pj64;
     *refinements = 0;
     if (o->precision == M1_PREC_MIXED) {
         CKS(ensure_work32(ctx));
@@ -1108,6 +1150,7 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
         }
         Ops32 ops32{ctx, g32, ctx->U32, pre};
         ops32.learned = learned;
+        if (lin) ops32.pj = ctx->pj32;
         return gmres_mixed(ctx, ops, ops32, b, x, o->gmres_rtol, o->restart, o->gmres_max, o->refine_max, iters,
                            refinements, bnorm, res, conv);
     }

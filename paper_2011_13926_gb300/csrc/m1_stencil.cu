@@ -121,37 +121,70 @@ __global__ void __launch_bounds__(kThreads) k_jv(Dev<R> g, const R* __restrict__
 }
 
 // ------------------------------------------------------------------ 2D tiled residual and J v
-// 2D residual (S = R) or J v (S = Dual<R>, the derivative parts) with the
-// closure of every cell computed once per CTA: a 32 x 8 tile plus a one-cell
-// halo (axis neighbours only; ghosts by the boundary rules) is staged in
-// shared memory as (E, F, P), then each thread forms its four HLL faces and
-// the sources in the order of cell_residual. Terms that do not depend on U
-// (U^n, the emission B, the source S) enter the residual only: they carry no
-// derivative. For frozen (time-n) or fixed wave speeds. The residual variant
-// also writes the block's partial sum of squares.
+// 2D residual (MODE kTileResidual, S = R), J v by dual numbers (kTileJvDual,
+// S = Dual<R>, the derivative parts) or J v from the pressure Jacobian
+// frozen at the Newton iterate (kTileJvLinear, S = R) with the closure of
+// every cell computed once per CTA: a 32 x 8 tile plus a one-cell halo (axis
+// neighbours only; ghosts by the boundary rules) is staged in shared memory
+// as (E, F, P), then each thread forms its four HLL faces and the sources in
+// the order of cell_residual. Terms that do not depend on U (U^n, the
+// emission B, the source S) enter the residual only: they carry no
+// derivative. For frozen (time-n) or fixed wave speeds, where J v is linear
+// in v but for dP = (dP/dU) v; kTileJvLinear reads dP/dU (from
+// k_pressure_jacobian2d) for the cells of the domain and takes the ghosts by
+// dual numbers through the boundary rules. The residual variant also writes
+// the block's partial sum of squares.
 constexpr int kTX = 32, kTY = 8;
+constexpr int kTileResidual = 0, kTileJvDual = 1, kTileJvLinear = 2;
 
 template <class S>
 struct CellT {
     S E, Fx, Fy, Pxx, Pxy, Pyy;
 };
 
-template <class S, bool GAS, bool RES>
+// dP/dU of one cell in 2D: row r of (Pxx, Pxy, Pyy), column c of (E, Fx, Fy)
+// at pj[(3 r + c) N + idx]; with gas, d(a_r T^4)/dT at pj[9 N + idx]
+template <bool GAS>
+__global__ void __launch_bounds__(kThreads) k_pressure_jacobian2d(Dev<double> g, const double* __restrict__ U,
+                                                                   double* __restrict__ pj64, float* __restrict__ pj32) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    const long long N = g.N;
+    const double E = U[idx], Fx = U[N + idx], Fy = U[2 * N + idx];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        St<Dual<double>, 2> u;
+        u.E = Dual<double>{E, c == 0 ? 1.0 : 0.0};
+        u.F[0] = Dual<double>{Fx, c == 1 ? 1.0 : 0.0};
+        u.F[1] = Dual<double>{Fy, c == 2 ? 1.0 : 0.0};
+        const Cl<Dual<double>, 2> k = closure(u, g.c);
+        const double d[3] = {pressure(k, 0, 0).d, pressure(k, 0, 1).d, pressure(k, 1, 1).d};
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            pj64[(3 * r + c) * N + idx] = d[r];
+            if (pj32) pj32[(3 * r + c) * N + idx] = (float)d[r];
+        }
+    }
+    if constexpr (GAS) {
+        const double T = U[3 * N + idx];
+        const double dB = 4.0 * g.a_r * T * T * T;
+        pj64[9 * N + idx] = dB;
+        if (pj32) pj32[9 * N + idx] = (float)dB;
+    }
+}
+
+template <class S, bool GAS, int MODE>
 __global__ void __launch_bounds__(kTX* kTY)
     k_stencil2d_tiled(Dev<typename RealOf<S>::type> g, const typename RealOf<S>::type* __restrict__ U,
-                      const typename RealOf<S>::type* __restrict__ v, typename RealOf<S>::type* __restrict__ out,
-                      double* __restrict__ partials) {
+                      const typename RealOf<S>::type* __restrict__ v, const typename RealOf<S>::type* __restrict__ pj,
+                      typename RealOf<S>::type* __restrict__ out, double* __restrict__ partials) {
     using R = typename RealOf<S>::type;
-    using L = std::conditional_t<RES, LoadPlain<R>, LoadDir<R>>;
+    constexpr bool RES = MODE == kTileResidual;
+    static_assert((MODE == kTileJvDual) == std::is_same<S, Dual<R>>::value, "dual numbers only for kTileJvDual");
     __shared__ CellT<S> cs[kTY + 2][kTX + 2];
     const int nx = g.n[0], ny = g.n[1];
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-    L ld;
-    if constexpr (RES) {
-        ld = L{U, g.N};
-    } else {
-        ld = L{U, v, g.N};
-    }
+    const long long N = g.N;
     const int tid = threadIdx.y * kTX + threadIdx.x;
     for (int t = tid; t < (kTX + 2) * (kTY + 2); t += kTX * kTY) {
         const int hx = t % (kTX + 2), hy = t / (kTX + 2);
@@ -160,29 +193,66 @@ __global__ void __launch_bounds__(kTX* kTY)
         if (!(in_x || in_y)) continue;              // corner: no face needs it
         if (gx > nx || gy > ny) continue;           // beyond the last ghost of a ragged tile
         if ((hx == 0 || hx == kTX + 1) && (hy == 0 || hy == kTY + 1)) continue;  // tile corners
-        St<S, 2> u;
-        if (in_x && in_y) {
-            const long long idx = (long long)gy * nx + gx;
-            u = load_state<S, 2, false>(ld, idx, idx);
-        } else {
-            // ghost of the adjacent boundary cell along the axis that left the domain
-            const int a = in_x ? 1 : 0;
-            const int side = a == 0 ? (gx < 0 ? 0 : 1) : (gy < 0 ? 0 : 1);
-            int cc[3] = {a == 0 ? (gx < 0 ? 0 : nx - 1) : gx, a == 1 ? (gy < 0 ? 0 : ny - 1) : gy, 0};
-            const long long idx = (long long)cc[1] * nx + cc[0];
-            const St<S, 2> self = load_state<S, 2, false>(ld, idx, idx);
-            R sig_nb;
-            bool bnd;
-            u = neighbour<S, 2, false>(g, ld, self, idx, cc, a, side, sig_nb, bnd);
-        }
-        const Cl<S, 2> k = closure(u, g.c);
         CellT<S> c;
-        c.E = u.E;
-        c.Fx = u.F[0];
-        c.Fy = u.F[1];
-        c.Pxx = pressure(k, 0, 0);
-        c.Pxy = pressure(k, 0, 1);
-        c.Pyy = pressure(k, 1, 1);
+        bool staged = false;
+        if constexpr (MODE == kTileJvLinear) {
+            if (in_x && in_y) {
+            staged = true;
+            const long long idx = (long long)gy * nx + gx;
+            const R vE = v[idx], vFx = v[N + idx], vFy = v[2 * N + idx];
+            c.E = vE;
+            c.Fx = vFx;
+            c.Fy = vFy;
+            R d[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                d[r] = pj[(3 * r) * N + idx] * vE + pj[(3 * r + 1) * N + idx] * vFx + pj[(3 * r + 2) * N + idx] * vFy;
+            c.Pxx = d[0];
+            c.Pxy = d[1];
+            c.Pyy = d[2];
+            }
+        }
+        if (!staged) {
+            using SD = std::conditional_t<MODE == kTileResidual, R, Dual<R>>;  // ghosts of the linear mode by duals
+            using L = std::conditional_t<MODE == kTileResidual, LoadPlain<R>, LoadDir<R>>;
+            L ld;
+            if constexpr (MODE == kTileResidual) {
+                ld = L{U, N};
+            } else {
+                ld = L{U, v, N};
+            }
+            St<SD, 2> u;
+            if (in_x && in_y) {
+                const long long idx = (long long)gy * nx + gx;
+                u = load_state<SD, 2, false>(ld, idx, idx);
+            } else {
+                // ghost of the adjacent boundary cell along the axis that left the domain
+                const int a = in_x ? 1 : 0;
+                const int side = a == 0 ? (gx < 0 ? 0 : 1) : (gy < 0 ? 0 : 1);
+                int cc[3] = {a == 0 ? (gx < 0 ? 0 : nx - 1) : gx, a == 1 ? (gy < 0 ? 0 : ny - 1) : gy, 0};
+                const long long idx = (long long)cc[1] * nx + cc[0];
+                const St<SD, 2> self = load_state<SD, 2, false>(ld, idx, idx);
+                R sig_nb;
+                bool bnd;
+                u = neighbour<SD, 2, false>(g, ld, self, idx, cc, a, side, sig_nb, bnd);
+            }
+            const Cl<SD, 2> k = closure(u, g.c);
+            if constexpr (MODE == kTileJvLinear) {
+                c.E = u.E.d;
+                c.Fx = u.F[0].d;
+                c.Fy = u.F[1].d;
+                c.Pxx = pressure(k, 0, 0).d;
+                c.Pxy = pressure(k, 0, 1).d;
+                c.Pyy = pressure(k, 1, 1).d;
+            } else {
+                c.E = u.E;
+                c.Fx = u.F[0];
+                c.Fy = u.F[1];
+                c.Pxx = pressure(k, 0, 0);
+                c.Pxy = pressure(k, 0, 1);
+                c.Pyy = pressure(k, 1, 1);
+            }
+        }
         cs[hy][hx] = c;
     }
     __syncthreads();
@@ -263,30 +333,45 @@ __global__ void __launch_bounds__(kTX* kTY)
         S emis;
         S T;
         if constexpr (GAS) {
-            T = ld.get(3, idx, idx);
-            const S T2 = T * T;
-            emis = g.a_r * (T2 * T2);
+            if constexpr (MODE == kTileJvDual) {
+                T = S{U[3 * N + idx], v[3 * N + idx]};
+            } else if constexpr (MODE == kTileJvLinear) {
+                T = v[3 * N + idx];
+            } else {
+                T = U[3 * N + idx];
+            }
+            if constexpr (MODE == kTileJvLinear) {
+                emis = pj[9 * N + idx] * T;
+            } else {
+                const S T2 = T * T;
+                emis = g.a_r * (T2 * T2);
+            }
         } else {
             emis = cst<S>(RES && g.B ? g.B[idx] : R(0));
         }
         const S exch = (cdt * g.sig_a[idx]) * (emis - me.E);
         RE = RE - exch;
-        if constexpr (RES) {
+        if constexpr (MODE == kTileJvDual) {
+            out[idx] = RE.d;
+            out[N + idx] = RFx.d;
+            out[2 * N + idx] = RFy.d;
+            if constexpr (GAS) out[3 * N + idx] = (g.rho_cv[idx] * T + exch).d;
+        } else if constexpr (MODE == kTileJvLinear) {
+            out[idx] = RE;
+            out[N + idx] = RFx;
+            out[2 * N + idx] = RFy;
+            if constexpr (GAS) out[3 * N + idx] = g.rho_cv[idx] * T + exch;
+        } else {
             if (g.S) RE = RE - dt * g.S[idx];
             out[idx] = RE;
-            out[g.N + idx] = RFx;
-            out[2 * g.N + idx] = RFy;
+            out[N + idx] = RFx;
+            out[2 * N + idx] = RFy;
             ss = (double)RE * RE + (double)RFx * RFx + (double)RFy * RFy;
             if constexpr (GAS) {
-                const S RT = g.rho_cv[idx] * (T - g.Un[3 * g.N + idx]) + exch;
-                out[3 * g.N + idx] = RT;
+                const S RT = g.rho_cv[idx] * (T - g.Un[3 * N + idx]) + exch;
+                out[3 * N + idx] = RT;
                 ss += (double)RT * RT;
             }
-        } else {
-            out[idx] = RE.d;
-            out[g.N + idx] = RFx.d;
-            out[2 * g.N + idx] = RFy.d;
-            if constexpr (GAS) out[3 * g.N + idx] = (g.rho_cv[idx] * T + exch).d;
         }
     }
     if constexpr (RES) {
@@ -353,9 +438,11 @@ int launch_residual_f64(const Dev<double>& g, const double* U, double* R, double
         const long long nb = (long long)grid.x * grid.y;
         if (!partials || nb <= capacity) {
             if (g.gas)
-                k_stencil2d_tiled<double, true, true><<<grid, block, 0, s>>>(g, U, nullptr, R, partials);
+                k_stencil2d_tiled<double, true, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, R,
+                                                                                     partials);
             else
-                k_stencil2d_tiled<double, false, true><<<grid, block, 0, s>>>(g, U, nullptr, R, partials);
+                k_stencil2d_tiled<double, false, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, R,
+                                                                                      partials);
             return (int)nb;
         }
     }
@@ -371,10 +458,39 @@ static bool jv_tiled(const Dev<R>& g, const R* U, const R* v, R* Jv, cudaStream_
     if (g.dim != 2 || (g.implicit_eigs && !g.fixed_eigs)) return false;
     dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
     if (g.gas)
-        k_stencil2d_tiled<Dual<R>, true, false><<<grid, block, 0, s>>>(g, U, v, Jv, nullptr);
+        k_stencil2d_tiled<Dual<R>, true, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, Jv, nullptr);
     else
-        k_stencil2d_tiled<Dual<R>, false, false><<<grid, block, 0, s>>>(g, U, v, Jv, nullptr);
+        k_stencil2d_tiled<Dual<R>, false, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, Jv, nullptr);
     return true;
+}
+
+bool jv_linear_available(const Dev<double>& g) { return tiled2d(g); }
+
+int pressure_jacobian_size(const Dev<double>& g) { return 9 + (g.gas ? 1 : 0); }
+
+void launch_pressure_jacobian(const Dev<double>& g, const double* U, double* pj64, float* pj32, cudaStream_t s) {
+    const int nb = stencil_blocks(g.N);
+    if (g.gas)
+        k_pressure_jacobian2d<true><<<nb, kThreads, 0, s>>>(g, U, pj64, pj32);
+    else
+        k_pressure_jacobian2d<false><<<nb, kThreads, 0, s>>>(g, U, pj64, pj32);
+}
+
+template <class R>
+static void jv_linear(const Dev<R>& g, const R* U, const R* pj, const R* v, R* Jv, cudaStream_t s) {
+    const dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
+    if (g.gas)
+        k_stencil2d_tiled<R, true, kTileJvLinear><<<grid, block, 0, s>>>(g, U, v, pj, Jv, nullptr);
+    else
+        k_stencil2d_tiled<R, false, kTileJvLinear><<<grid, block, 0, s>>>(g, U, v, pj, Jv, nullptr);
+}
+void launch_jv_linear_f64(const Dev<double>& g, const double* U, const double* pj, const double* v, double* Jv,
+                          cudaStream_t s) {
+    jv_linear<double>(g, U, pj, v, Jv, s);
+}
+void launch_jv_linear_f32(const Dev<float>& g, const float* U, const float* pj, const float* v, float* Jv,
+                          cudaStream_t s) {
+    jv_linear<float>(g, U, pj, v, Jv, s);
 }
 
 void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s) {
