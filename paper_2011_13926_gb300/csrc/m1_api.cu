@@ -85,7 +85,8 @@ struct m1_ctx {
     double* ar_partials = nullptr;
     unsigned* ar_counter = nullptr;
     int* ar_reorth = nullptr;
-    int gs_grid32[kMaxRestart] = {}, gs_grid64[kMaxRestart] = {};  // Gram-Schmidt grid per Arnoldi step
+    int gs_grid32[kMaxRestart] = {}, gs_grid64[kMaxRestart] = {};  // Gram-Schmidt grids per Arnoldi step
+    int gs_dots32[kMaxRestart] = {}, gs_dots64[kMaxRestart] = {};
     long long residual_partials = 0;                                 // entries of partials
     Scal sc{};
     double* scal_base = nullptr;
@@ -404,6 +405,8 @@ struct Ops64 {
     const double* U;
     bool precond;
     const double* pj = nullptr;  // dP/dU at U: J v as a linear stencil, else by dual numbers
+    bool fused() const { return false; }
+    void AM(const double*, double*) {}
     void A(const double* in, double* out) {
         TK t(ctx, M1_K_JV64);
         if (pj)
@@ -430,6 +433,14 @@ struct Ops32 {
     bool precond;
     bool learned = false;
     const float* pj = nullptr;  // dP/dU at U in FP32: J v as a linear stencil, else by dual numbers
+    // J M^-1 v in one stencil (point-block Jacobi applied while staging)
+    bool fused() const { return pj && precond && !learned; }
+    void AM(const float* in, float* out) {
+        TK t(ctx, M1_K_JV32);
+        launch_jv_linear_pre_f32(g, U, pj, ctx->binv32, in, out, ctx->s);
+        count(ctx, 1);
+        ctx->st.jv_calls++;
+    }
     void A(const float* in, float* out) {
         TK t(ctx, M1_K_JV32);
         if (pj)
@@ -459,7 +470,11 @@ ArnoldiDev arnoldi_dev(m1_ctx* ctx, bool fp32) {
     K.n = ctx->n;
     K.ld = ctx->ld;
     const int* grid = fp32 ? ctx->gs_grid32 : ctx->gs_grid64;
-    for (int j = 0; j < kMaxRestart; ++j) K.grid[j] = grid[j];
+    const int* grid_dots = fp32 ? ctx->gs_dots32 : ctx->gs_dots64;
+    for (int j = 0; j < kMaxRestart; ++j) {
+        K.grid[j] = grid[j];
+        K.grid_dots[j] = grid_dots[j];
+    }
     K.H = ctx->sc.H;
     K.cs = ctx->sc.cs;
     K.sn = ctx->sc.sn;
@@ -527,9 +542,13 @@ m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, doub
     for (int j = 0; j <= maxk; ++j) {
         if (j < maxk) {
             T* Vj = V + (long long)j * ld;
-            T* zj = Z ? Z + (long long)j * ld : z;  // flexible GMRES keeps every preconditioned vector
-            ops.M(Vj, zj);
-            ops.A(zj, w);
+            if (!Z && ops.fused()) {
+                ops.AM(Vj, w);  // J M^-1 V_j, M^-1 V_j never stored
+            } else {
+                T* zj = Z ? Z + (long long)j * ld : z;  // flexible GMRES keeps every preconditioned vector
+                ops.M(Vj, zj);
+                ops.A(zj, w);
+            }
             {
                 TK t(ctx, M1_K_ORTHO);
                 arnoldi_step(arnoldi_dev(ctx, sizeof(T) == 4), V, w, j, s);
@@ -854,8 +873,8 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
     if (!desc->gas_coupling && cudaMemsetAsync(ctx->B, 0, N * sizeof(double), ctx->s) != cudaSuccess)
         return cleanup(M1_ERR_CUDA);
     if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cleanup(M1_ERR_CUDA);
-    arnoldi_grid_table(ctx->n, true, ctx->gs_grid32);
-    arnoldi_grid_table(ctx->n, false, ctx->gs_grid64);
+    arnoldi_grid_table(ctx->n, true, ctx->gs_grid32, ctx->gs_dots32);
+    arnoldi_grid_table(ctx->n, false, ctx->gs_grid64, ctx->gs_dots64);
     if (cudaGetLastError() != cudaSuccess) return cleanup(M1_ERR_CUDA);
     {
         // minimal traffic per launch: J v reads U, v, sigma_a, sigma_f, alpha (one

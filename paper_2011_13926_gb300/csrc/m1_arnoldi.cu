@@ -243,11 +243,10 @@ __global__ void __launch_bounds__(kOrThreads) k_gram_schmidt(ArnoldiDev K, T* __
 #pragma unroll
     for (int i = 0; i < NC; ++i) rows[i] = reinterpret_cast<const VT*>(V + (long long)min(i, j) * ld);
     VT* out = reinterpret_cast<VT*>(V + (long long)(j + 1) * ld);
-    for (long long q = (long long)blockIdx.x * kOrThreads + tid; q < nv; q += (long long)gridDim.x * kOrThreads) {
-        VT v[NC];
-#pragma unroll
-        for (int i = 0; i < NC; ++i) v[i] = __ldg(rows[i] + q);
-        VT x = __ldg(reinterpret_cast<const VT*>(w) + q);
+    // U slots per thread per trip (U x NC loads in flight), then single slots
+    constexpr int U = NC <= 4 ? 8 : NC <= 8 ? 4 : NC <= 16 ? 2 : 1;
+    const long long S = (long long)gridDim.x * kOrThreads;
+    auto slot = [&](const VT* v, VT x, long long q) {
         if (mode != kDots) {
 #pragma unroll
             for (int i = 0; i < NC; ++i) fnma(x, h1s[i], v[i]);
@@ -264,6 +263,24 @@ __global__ void __launch_bounds__(kOrThreads) k_gram_schmidt(ArnoldiDev K, T* __
             scale(x, inv);
             out[q] = x;
         }
+    };
+    long long q = (long long)blockIdx.x * kOrThreads + tid;
+    for (; q + (U - 1) * S < nv; q += U * S) {
+        VT v[U][NC], x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int i = 0; i < NC; ++i) v[u][i] = __ldg(rows[i] + q + u * S);
+            x[u] = __ldg(reinterpret_cast<const VT*>(w) + q + u * S);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) slot(v[u], x[u], q + u * S);
+    }
+    for (; q < nv; q += S) {
+        VT v[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) v[i] = __ldg(rows[i] + q);
+        slot(v, __ldg(reinterpret_cast<const VT*>(w) + q), q);
     }
     if (blockIdx.x == 0) {  // the n % W scalar tail
         for (long long e = nv * W + tid; e < n; e += kOrThreads) {
@@ -372,7 +389,7 @@ __global__ void __launch_bounds__(kOrThreads) k_gram_schmidt(ArnoldiDev K, T* __
 }
 
 template <class T, int NC>
-static int gs_grid_one(int j, long long n, int sms) {
+static int gs_grid_one(int j, long long n, int sms, bool dots) {
     (void)j;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_schmidt<T, NC>, kOrThreads, 0) != cudaSuccess ||
@@ -380,39 +397,45 @@ static int gs_grid_one(int j, long long n, int sms) {
         occ = 1;
     const long long nv = n / Vec<T>::W;
     const long long tiles = std::max(1LL, (nv + kOrThreads - 1) / kOrThreads);
+    // the dots passes end in one block summing a partial row per block: two
+    // blocks per SM keep that tail short (the U-slot trips keep loads in flight)
+    if (dots) occ = std::min(occ, 2);
     return (int)std::min<long long>({(long long)occ * sms, tiles, (long long)kMaxGsBlocks});
 }
 
 // the accumulator size of step j: j + 1 rounded up to a multiple of 4
 template <class T, int NC = 4>
-static int gs_grid_for(int j, long long n, int sms) {
+static int gs_grid_for(int j, long long n, int sms, bool dots) {
     if constexpr (NC < 32) {
-        if (j + 1 > NC) return gs_grid_for<T, NC + 4>(j, n, sms);
+        if (j + 1 > NC) return gs_grid_for<T, NC + 4>(j, n, sms, dots);
     }
-    return gs_grid_one<T, NC>(j, n, sms);
+    return gs_grid_one<T, NC>(j, n, sms, dots);
 }
 
 template <class T>
-static void gs_grid_table(long long n, int* grid) {
+static void gs_grid_table(long long n, int* grid, int* grid_dots) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int j = 0; j < kMaxRestart; ++j) grid[j] = gs_grid_for<T>(j, n, sms);
+    for (int j = 0; j < kMaxRestart; ++j) {
+        grid[j] = gs_grid_for<T>(j, n, sms, false);
+        grid_dots[j] = gs_grid_for<T>(j, n, sms, true);
+    }
 }
 
-void arnoldi_grid_table(long long n, bool fp32, int* grid) {
+void arnoldi_grid_table(long long n, bool fp32, int* grid, int* grid_dots) {
     if (fp32)
-        gs_grid_table<float>(n, grid);
+        gs_grid_table<float>(n, grid, grid_dots);
     else
-        gs_grid_table<double>(n, grid);
+        gs_grid_table<double>(n, grid, grid_dots);
 }
 
 template <class T, int NC>
 static void gs_launch(const ArnoldiDev& K, T* V, const T* w, int j, cudaStream_t s) {
-    const dim3 gd(K.grid[j]);
-    k_gram_schmidt<T, NC><<<gd, kOrThreads, 0, s>>>(K, V, w, j, kDots);
-    k_gram_schmidt<T, NC><<<gd, kOrThreads, 0, s>>>(K, V, w, j, kDotsResidual);
-    k_gram_schmidt<T, NC><<<gd, kOrThreads, 0, s>>>(K, V, w, j, kUpdate);
+    const dim3 gdots(K.grid_dots[j]), gupd(K.grid[j]);
+    k_gram_schmidt<T, NC><<<gdots, kOrThreads, 0, s>>>(K, V, w, j, kDots);
+    k_gram_schmidt<T, NC><<<gdots, kOrThreads, 0, s>>>(K, V, w, j, kDotsResidual);
+    k_gram_schmidt<T, NC><<<gupd, kOrThreads, 0, s>>>(K, V, w, j, kUpdate);
 }
 
 template <class T, int NC = 4>

@@ -30,6 +30,10 @@ void launch_jv_linear_f64(const Dev<double>& g, const double* U, const double* p
                           cudaStream_t s);
 void launch_jv_linear_f32(const Dev<float>& g, const float* U, const float* pj, const float* v, float* Jv,
                           cudaStream_t s);
+// J M^-1 v with the point-block inverse binv (NU x NU row-major planes, FP32)
+// applied to v inside the stencil (M^-1 v is never stored)
+void launch_jv_linear_pre_f32(const Dev<float>& g, const float* U, const float* pj, const float* binv,
+                              const float* v, float* Jv, cudaStream_t s);
 // partial-sum entries the residual may need for this grid
 long long residual_partial_count(int dim, const int n[3]);
 void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s);
@@ -57,14 +61,15 @@ void launch_advect(const Dev<double>& g, const double* const u[3], double* Tout,
 // reorthogonalisation, Givens on the FP64 Hessenberg column in the last block)
 struct ArnoldiDev {
     long long n, ld;     // vector length, basis stride
-    int grid[kMaxRestart];  // blocks of the Gram-Schmidt passes of step j (partials has grid[j] rows of kMaxRestart + 2)
+    int grid[kMaxRestart];       // blocks of the update pass of Arnoldi step j
+    int grid_dots[kMaxRestart];  // blocks of its dots passes (partials holds one row of kMaxRestart + 2 per block)
     double *H, *cs, *sn, *g, *resid, *h1, *h2, *nrm2, *partials;
     unsigned* counter;   // arrival counter of the last-block reduction (kept at 0 between launches)
     int* reorth;         // 1 when the second Gram-Schmidt pass runs
 };
 constexpr int kMaxGsBlocks = 4096;  // bound of ArnoldiDev::grid, rows of ArnoldiDev::partials
 // blocks of each Arnoldi step's passes for vectors of length n (occupancy of this device)
-void arnoldi_grid_table(long long n, bool fp32, int* grid);
+void arnoldi_grid_table(long long n, bool fp32, int* grid, int* grid_dots);
 void launch_arnoldi_step_f64(const ArnoldiDev& K, double* V, double* w, int j, cudaStream_t s);
 void launch_arnoldi_step_f32(const ArnoldiDev& K, float* V, float* w, int j, cudaStream_t s);
 

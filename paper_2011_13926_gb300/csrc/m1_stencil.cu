@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_jv(Dev<R> g, const R* __restrict__
 // dual numbers through the boundary rules. The residual variant also writes
 // the block's partial sum of squares.
 constexpr int kTX = 32, kTY = 8;
-constexpr int kTileResidual = 0, kTileJvDual = 1, kTileJvLinear = 2;
+constexpr int kTileResidual = 0, kTileJvDual = 1, kTileJvLinear = 2, kTileJvLinearPre = 3;
 
 template <class S>
 struct CellT {
@@ -173,19 +173,73 @@ __global__ void __launch_bounds__(kThreads) k_pressure_jacobian2d(Dev<double> g,
     }
 }
 
+// Loader of U + eps M^-1 v for the fused preconditioned J v: the direction
+// at a cell is its point-block inverse (NU x NU, row-major planes) times v
+template <class R, int NU>
+struct LoadPre {
+    const R* U;
+    const R* v;
+    const R* binv;
+    long long N;
+    __device__ __forceinline__ Dual<R> get(int comp, long long idx, long long) const {
+        R z = R(0);
+#pragma unroll
+        for (int c = 0; c < NU; ++c) z += binv[(long long)(comp * NU + c) * N + idx] * v[(long long)c * N + idx];
+        return {U[comp * N + idx], z};
+    }
+};
+
 template <class S, bool GAS, int MODE>
 __global__ void __launch_bounds__(kTX* kTY)
     k_stencil2d_tiled(Dev<typename RealOf<S>::type> g, const typename RealOf<S>::type* __restrict__ U,
                       const typename RealOf<S>::type* __restrict__ v, const typename RealOf<S>::type* __restrict__ pj,
-                      typename RealOf<S>::type* __restrict__ out, double* __restrict__ partials) {
+                      const typename RealOf<S>::type* __restrict__ binv, typename RealOf<S>::type* __restrict__ out,
+                      double* __restrict__ partials) {
     using R = typename RealOf<S>::type;
     constexpr bool RES = MODE == kTileResidual;
+    constexpr bool LIN = MODE == kTileJvLinear || MODE == kTileJvLinearPre;
+    constexpr bool PRE = MODE == kTileJvLinearPre;
+    constexpr int NU = GAS ? 4 : 3;
     static_assert((MODE == kTileJvDual) == std::is_same<S, Dual<R>>::value, "dual numbers only for kTileJvDual");
     __shared__ CellT<S> cs[kTY + 2][kTX + 2];
     const int nx = g.n[0], ny = g.n[1];
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const long long N = g.N;
     const int tid = threadIdx.y * kTX + threadIdx.x;
+    // this thread's cell and its face data, loaded before the halo so that
+    // their latency overlaps the staging
+    const int ix = x0 + threadIdx.x, iy = y0 + threadIdx.y;
+    const bool valid = ix < nx && iy < ny;
+    const long long idx = valid ? (long long)iy * nx + ix : 0;
+    const int coord[3] = {ix, iy, 0};
+    R sig_self = R(0), sig_nb[2][2], lpf[2][2], lmf[2][2], alf[2][2];
+    if (valid) {
+        sig_self = g.sig_f[idx];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int ca = coord[a] + (side ? 1 : -1);
+                const bool inside = ca >= 0 && ca < g.n[a];
+                const bool periodic = g.bc[a][side] == BC_PERIODIC;
+                R sn = sig_self;
+                if (inside)
+                    sn = g.sig_f[idx + (side ? g.stride[a] : -g.stride[a])];
+                else if (periodic)
+                    sn = g.sig_f[idx + (side ? -(long long)(g.n[a] - 1) : (long long)(g.n[a] - 1)) * g.stride[a]];
+                sig_nb[a][side] = sn;
+                const long long fidx = face_index(g.n, coord, a, coord[a] + side);
+                if (g.fixed_eigs) {
+                    lpf[a][side] = g.c;
+                    lmf[a][side] = -g.c;
+                } else {
+                    lpf[a][side] = g.lam_p[a][fidx];
+                    lmf[a][side] = g.lam_m[a][fidx];
+                }
+                alf[a][side] = g.alpha[a][fidx];
+            }
+        }
+    }
     for (int t = tid; t < (kTX + 2) * (kTY + 2); t += kTX * kTY) {
         const int hx = t % (kTX + 2), hy = t / (kTX + 2);
         int gx = x0 + hx - 1, gy = y0 + hy - 1;
@@ -195,49 +249,68 @@ __global__ void __launch_bounds__(kTX* kTY)
         if ((hx == 0 || hx == kTX + 1) && (hy == 0 || hy == kTY + 1)) continue;  // tile corners
         CellT<S> c;
         bool staged = false;
-        if constexpr (MODE == kTileJvLinear) {
+        if constexpr (LIN) {
             if (in_x && in_y) {
-            staged = true;
-            const long long idx = (long long)gy * nx + gx;
-            const R vE = v[idx], vFx = v[N + idx], vFy = v[2 * N + idx];
-            c.E = vE;
-            c.Fx = vFx;
-            c.Fy = vFy;
-            R d[3];
+                staged = true;
+                const long long k = (long long)gy * nx + gx;
+                R z[3];
+                if constexpr (PRE) {  // z = M^-1 v at this cell (rows E, Fx, Fy of the block inverse)
+                    R vv[NU];
 #pragma unroll
-            for (int r = 0; r < 3; ++r)
-                d[r] = pj[(3 * r) * N + idx] * vE + pj[(3 * r + 1) * N + idx] * vFx + pj[(3 * r + 2) * N + idx] * vFy;
-            c.Pxx = d[0];
-            c.Pxy = d[1];
-            c.Pyy = d[2];
+                    for (int q = 0; q < NU; ++q) vv[q] = v[q * N + k];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        R acc = R(0);
+#pragma unroll
+                        for (int q = 0; q < NU; ++q) acc += binv[(long long)(r * NU + q) * N + k] * vv[q];
+                        z[r] = acc;
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) z[r] = v[r * N + k];
+                }
+                c.E = z[0];
+                c.Fx = z[1];
+                c.Fy = z[2];
+                R d[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    d[r] = pj[(3 * r) * N + k] * z[0] + pj[(3 * r + 1) * N + k] * z[1] + pj[(3 * r + 2) * N + k] * z[2];
+                c.Pxx = d[0];
+                c.Pxy = d[1];
+                c.Pyy = d[2];
             }
         }
         if (!staged) {
-            using SD = std::conditional_t<MODE == kTileResidual, R, Dual<R>>;  // ghosts of the linear mode by duals
-            using L = std::conditional_t<MODE == kTileResidual, LoadPlain<R>, LoadDir<R>>;
+            // residual: plain values; dual J v: dual numbers; linear J v: the
+            // ghosts by dual numbers through the boundary rules
+            using SD = std::conditional_t<RES, R, Dual<R>>;
+            using L = std::conditional_t<RES, LoadPlain<R>, std::conditional_t<PRE, LoadPre<R, NU>, LoadDir<R>>>;
             L ld;
-            if constexpr (MODE == kTileResidual) {
+            if constexpr (RES) {
                 ld = L{U, N};
+            } else if constexpr (PRE) {
+                ld = L{U, v, binv, N};
             } else {
                 ld = L{U, v, N};
             }
             St<SD, 2> u;
             if (in_x && in_y) {
-                const long long idx = (long long)gy * nx + gx;
-                u = load_state<SD, 2, false>(ld, idx, idx);
+                const long long k = (long long)gy * nx + gx;
+                u = load_state<SD, 2, false>(ld, k, k);
             } else {
                 // ghost of the adjacent boundary cell along the axis that left the domain
                 const int a = in_x ? 1 : 0;
                 const int side = a == 0 ? (gx < 0 ? 0 : 1) : (gy < 0 ? 0 : 1);
                 int cc[3] = {a == 0 ? (gx < 0 ? 0 : nx - 1) : gx, a == 1 ? (gy < 0 ? 0 : ny - 1) : gy, 0};
-                const long long idx = (long long)cc[1] * nx + cc[0];
-                const St<SD, 2> self = load_state<SD, 2, false>(ld, idx, idx);
-                R sig_nb;
+                const long long k = (long long)cc[1] * nx + cc[0];
+                const St<SD, 2> self = load_state<SD, 2, false>(ld, k, k);
+                R sn;
                 bool bnd;
-                u = neighbour<SD, 2, false>(g, ld, self, idx, cc, a, side, sig_nb, bnd);
+                u = neighbour<SD, 2, false>(g, ld, self, k, cc, a, side, sn, bnd);
             }
             const Cl<SD, 2> k = closure(u, g.c);
-            if constexpr (MODE == kTileJvLinear) {
+            if constexpr (LIN) {
                 c.E = u.E.d;
                 c.Fx = u.F[0].d;
                 c.Fy = u.F[1].d;
@@ -256,19 +329,15 @@ __global__ void __launch_bounds__(kTX* kTY)
         cs[hy][hx] = c;
     }
     __syncthreads();
-    const int ix = x0 + threadIdx.x, iy = y0 + threadIdx.y;
     double ss = 0.0;
-    if (ix < nx && iy < ny) {
-        const long long idx = (long long)iy * nx + ix;
-        const int coord[3] = {ix, iy, 0};
+    if (valid) {
         const CellT<S>& me = cs[threadIdx.y + 1][threadIdx.x + 1];
-        const R sig_self = g.sig_f[idx];
         const R dt = g.dt, c = g.c, c2 = g.c * g.c;
         S RE = me.E, RFx = me.Fx, RFy = me.Fy;
         if constexpr (RES) {
             RE = RE - g.Un[idx];
-            RFx = RFx - g.Un[g.N + idx];
-            RFy = RFy - g.Un[2 * g.N + idx];
+            RFx = RFx - g.Un[N + idx];
+            RFy = RFy - g.Un[2 * N + idx];
         }
         S phi[2] = {cst<S>(R(0)), cst<S>(R(0))};
 #pragma unroll
@@ -284,20 +353,7 @@ __global__ void __launch_bounds__(kTX* kTY)
                 const bool inside = ca >= 0 && ca < g.n[a];
                 const bool periodic = g.bc[a][side] == BC_PERIODIC;
                 const bool boundary = !inside && !periodic;
-                R sig_nb = sig_self;
-                if (inside)
-                    sig_nb = g.sig_f[idx + (side ? g.stride[a] : -g.stride[a])];
-                else if (periodic)
-                    sig_nb = g.sig_f[idx + (side ? -(long long)(g.n[a] - 1) : (long long)(g.n[a] - 1)) * g.stride[a]];
-                const long long fidx = face_index(g.n, coord, a, coord[a] + side);
-                R lp, lm;
-                if (g.fixed_eigs) {
-                    lp = c;
-                    lm = -c;
-                } else {
-                    lp = g.lam_p[a][fidx];
-                    lm = g.lam_m[a][fidx];
-                }
+                const R lp = lpf[a][side], lm = lmf[a][side];
                 const R den = lp - lm;
                 const R inv = den >= Tiny<R>::den() ? R(1) / den : R(0);
                 const R pm = lp * lm * inv;
@@ -309,7 +365,7 @@ __global__ void __launch_bounds__(kTX* kTY)
                 const S Psx = c2 * (lp * PaxL - lm * PaxR) * inv + pm * (Rc.Fx - Lc.Fx);
                 const S Psy = c2 * (lp * PayL - lm * PayR) * inv + pm * (Rc.Fy - Lc.Fy);
                 const R w = (side ? dt : -dt) * g.inv_dx[a];
-                RE = RE + (w * g.alpha[a][fidx]) * Fs;
+                RE = RE + (w * alf[a][side]) * Fs;
                 RFx = RFx + w * Psx;
                 RFy = RFy + w * Psy;
                 if (g.wb) {
@@ -317,7 +373,7 @@ __global__ void __launch_bounds__(kTX* kTY)
                         const S PR = a == 0 ? Rc.Pxx : Rc.Pyy, PL = a == 0 ? Lc.Pxx : Lc.Pyy;
                         phi[a] = phi[a] - c * g.inv_dx[a] * (PR - PL);
                     } else {
-                        phi[a] = phi[a] + (R(0.25) * (sig_self + sig_nb)) * (FaL + FaR);
+                        phi[a] = phi[a] + (R(0.25) * (sig_self + sig_nb[a][side])) * (FaL + FaR);
                     }
                 }
             }
@@ -337,10 +393,15 @@ __global__ void __launch_bounds__(kTX* kTY)
                 T = S{U[3 * N + idx], v[3 * N + idx]};
             } else if constexpr (MODE == kTileJvLinear) {
                 T = v[3 * N + idx];
+            } else if constexpr (PRE) {
+                R acc = R(0);
+#pragma unroll
+                for (int q = 0; q < NU; ++q) acc += binv[(long long)(3 * NU + q) * N + idx] * v[q * N + idx];
+                T = acc;
             } else {
                 T = U[3 * N + idx];
             }
-            if constexpr (MODE == kTileJvLinear) {
+            if constexpr (LIN) {
                 emis = pj[9 * N + idx] * T;
             } else {
                 const S T2 = T * T;
@@ -356,7 +417,7 @@ __global__ void __launch_bounds__(kTX* kTY)
             out[N + idx] = RFx.d;
             out[2 * N + idx] = RFy.d;
             if constexpr (GAS) out[3 * N + idx] = (g.rho_cv[idx] * T + exch).d;
-        } else if constexpr (MODE == kTileJvLinear) {
+        } else if constexpr (LIN) {
             out[idx] = RE;
             out[N + idx] = RFx;
             out[2 * N + idx] = RFy;
@@ -438,11 +499,11 @@ int launch_residual_f64(const Dev<double>& g, const double* U, double* R, double
         const long long nb = (long long)grid.x * grid.y;
         if (!partials || nb <= capacity) {
             if (g.gas)
-                k_stencil2d_tiled<double, true, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, R,
-                                                                                     partials);
+                k_stencil2d_tiled<double, true, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, nullptr,
+                                                                                     R, partials);
             else
-                k_stencil2d_tiled<double, false, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, R,
-                                                                                      partials);
+                k_stencil2d_tiled<double, false, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, nullptr,
+                                                                                      R, partials);
             return (int)nb;
         }
     }
@@ -458,9 +519,9 @@ static bool jv_tiled(const Dev<R>& g, const R* U, const R* v, R* Jv, cudaStream_
     if (g.dim != 2 || (g.implicit_eigs && !g.fixed_eigs)) return false;
     dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
     if (g.gas)
-        k_stencil2d_tiled<Dual<R>, true, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, Jv, nullptr);
+        k_stencil2d_tiled<Dual<R>, true, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, nullptr, Jv, nullptr);
     else
-        k_stencil2d_tiled<Dual<R>, false, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, Jv, nullptr);
+        k_stencil2d_tiled<Dual<R>, false, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, nullptr, Jv, nullptr);
     return true;
 }
 
@@ -477,20 +538,31 @@ void launch_pressure_jacobian(const Dev<double>& g, const double* U, double* pj6
 }
 
 template <class R>
-static void jv_linear(const Dev<R>& g, const R* U, const R* pj, const R* v, R* Jv, cudaStream_t s) {
+static void jv_linear(const Dev<R>& g, const R* U, const R* pj, const R* binv, const R* v, R* Jv, cudaStream_t s) {
     const dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
-    if (g.gas)
-        k_stencil2d_tiled<R, true, kTileJvLinear><<<grid, block, 0, s>>>(g, U, v, pj, Jv, nullptr);
-    else
-        k_stencil2d_tiled<R, false, kTileJvLinear><<<grid, block, 0, s>>>(g, U, v, pj, Jv, nullptr);
+    if (binv) {
+        if (g.gas)
+            k_stencil2d_tiled<R, true, kTileJvLinearPre><<<grid, block, 0, s>>>(g, U, v, pj, binv, Jv, nullptr);
+        else
+            k_stencil2d_tiled<R, false, kTileJvLinearPre><<<grid, block, 0, s>>>(g, U, v, pj, binv, Jv, nullptr);
+    } else {
+        if (g.gas)
+            k_stencil2d_tiled<R, true, kTileJvLinear><<<grid, block, 0, s>>>(g, U, v, pj, nullptr, Jv, nullptr);
+        else
+            k_stencil2d_tiled<R, false, kTileJvLinear><<<grid, block, 0, s>>>(g, U, v, pj, nullptr, Jv, nullptr);
+    }
 }
 void launch_jv_linear_f64(const Dev<double>& g, const double* U, const double* pj, const double* v, double* Jv,
                           cudaStream_t s) {
-    jv_linear<double>(g, U, pj, v, Jv, s);
+    jv_linear<double>(g, U, pj, nullptr, v, Jv, s);
 }
 void launch_jv_linear_f32(const Dev<float>& g, const float* U, const float* pj, const float* v, float* Jv,
                           cudaStream_t s) {
-    jv_linear<float>(g, U, pj, v, Jv, s);
+    jv_linear<float>(g, U, pj, nullptr, v, Jv, s);
+}
+void launch_jv_linear_pre_f32(const Dev<float>& g, const float* U, const float* pj, const float* binv,
+                              const float* v, float* Jv, cudaStream_t s) {
+    jv_linear<float>(g, U, pj, binv, v, Jv, s);
 }
 
 void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s) {
