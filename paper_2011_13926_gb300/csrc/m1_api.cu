@@ -83,7 +83,6 @@ struct m1_ctx {
     double* vel[3] = {nullptr, nullptr, nullptr};  // prescribed face velocities (gas advection)
     double* partials = nullptr;
     double* ar_partials = nullptr;
-    unsigned* ar_counter = nullptr;
     int* ar_reorth = nullptr;
     int gs_grid32[kMaxRestart] = {}, gs_grid64[kMaxRestart] = {};  // Gram-Schmidt grids per Arnoldi step
     int gs_dots32[kMaxRestart] = {}, gs_dots64[kMaxRestart] = {};
@@ -484,7 +483,7 @@ ArnoldiDev arnoldi_dev(m1_ctx* ctx, bool fp32) {
     K.h2 = ctx->sc.h2;
     K.nrm2 = ctx->sc.nrm2;
     K.partials = ctx->ar_partials;
-    K.counter = ctx->ar_counter;
+    K.partials2 = ctx->ar_partials + (size_t)kMaxGsBlocks * (kPartCols + 1);
     K.reorth = ctx->ar_reorth;
     return K;
 }
@@ -839,8 +838,7 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
     AL(ctx->scal_base, nscal);
     AL(ctx->singular, 1);
     AL(ctx->viol, 1);
-    AL(ctx->ar_partials, (size_t)kMaxGsBlocks * (kPartCols + 1));
-    AL(ctx->ar_counter, 1);
+    AL(ctx->ar_partials, (size_t)2 * kMaxGsBlocks * (kPartCols + 1));
     AL(ctx->ar_reorth, 1);
 #undef AL
     double* p = ctx->scal_base;
@@ -867,8 +865,7 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
         cudaEventCreateWithFlags(&ctx->ev_res[1], cudaEventDisableTiming) != cudaSuccess)
         return cleanup(M1_ERR_CUDA);
     if (cudaMemsetAsync(ctx->scal_base, 0, nscal * sizeof(double), ctx->s) != cudaSuccess) return cleanup(M1_ERR_CUDA);
-    if (cudaMemsetAsync(ctx->ar_counter, 0, sizeof(unsigned), ctx->s) != cudaSuccess ||
-        cudaMemsetAsync(ctx->ar_reorth, 0, sizeof(int), ctx->s) != cudaSuccess)
+    if (cudaMemsetAsync(ctx->ar_reorth, 0, sizeof(int), ctx->s) != cudaSuccess)
         return cleanup(M1_ERR_CUDA);
     if (!desc->gas_coupling && cudaMemsetAsync(ctx->B, 0, N * sizeof(double), ctx->s) != cudaSuccess)
         return cleanup(M1_ERR_CUDA);
@@ -903,7 +900,7 @@ m1_status m1_destroy(m1_ctx* ctx) {
                     ctx->delta, ctx->rhs, ctx->w, ctx->z, ctx->tmp, ctx->V, ctx->xacc, ctx->blocks, ctx->binv,
                     ctx->binv32, ctx->V32, ctx->w32, ctx->z32, ctx->U32, ctx->tmp32, ctx->Fstar, ctx->linework,
                     ctx->partials, ctx->scal_base, ctx->singular, ctx->viol, ctx->ar_partials,
-                    ctx->ar_counter, ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32};
+                    ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int a = 0; a < 3; ++a) {

@@ -3,32 +3,28 @@
 //
 // One Arnoldi step j on the new vector w = A M^-1 V_j is three launches of one
 // kernel, each a single pass over V_0..V_j and w:
-//   dots: h1 = V^T w and ||w||^2. The last block to finish sums the
-//     per-block partials in a fixed order, tests ||w - V h1||^2 =
-//     ||w||^2 - ||h1||^2 against ||w||^2 / 2 (the Daniel-Gragg-Kaufman-Stewart
-//     criterion) and, when no second pass is needed, applies the Givens
-//     rotations to Hessenberg column j and updates the residual estimate
-//     |g_{j+1}|;
-//   dots of the residual (only when the criterion asked for it; otherwise the
-//     blocks return at once): w' = w - V h1 is formed on the fly, element by
-//     element, and h2 = V^T w', ||w'||^2 are accumulated in the same pass, so
-//     the classical second Gram-Schmidt pass costs one read of the basis, not
-//     two; the last block rotates column h1 + h2;
-//   update: V_{j+1} = (w - V h1 [- V h2]) / beta, with the same rounding of w'
-//     as the second dots pass.
+//   dots: per-block partial sums of h1 = V^T w and ||w||^2;
+//   dots of the residual: every block first sums the partial rows of the
+//     first pass (fixed order, so all blocks agree bit for bit) and applies
+//     the Daniel-Gragg-Kaufman-Stewart test ||w - V h1||^2 = ||w||^2 -
+//     ||h1||^2 > ||w||^2 / 2; when it holds the blocks return at once,
+//     otherwise w' = w - V h1 is formed on the fly, element by element, and
+//     the partial sums of h2 = V^T w' and ||w'||^2 are written, so the
+//     classical second Gram-Schmidt pass costs one read of the basis, not two;
+//   update: every block sums the partial rows (both passes when the second
+//     ran), forms beta and writes V_{j+1} = (w - V h1 [- V h2]) / beta with the
+//     same rounding of w' as the second pass; block 0 applies the Givens
+//     rotations to Hessenberg column h1 (+ h2), beta and updates the residual
+//     estimate |g_{j+1}|.
 // Every pass is one grid-stride sweep in which a thread loads the 16-byte slot
 // q of all rows at once into registers (the rows are a compile-time count, so
 // the loads are issued back to back and the accumulation chains interleave).
-// The grid is as many blocks as fit on the SMs. For FP32 vectors the sums stay
-// in double-float FP32 arithmetic through the warp, block and cross-block
-// reductions and reach FP64 once per column: GB300 runs FP64 at a small
-// fraction of its FP32 rate, and FP64 reductions in every lane cost a fifth
-// of a dots pass.
-// FP32 vectors accumulate their dot products in double-float arithmetic
-// (each 16-byte group of four products by an FMA chain, then an error-free
-// TwoSum into a (hi, lo) pair), FP64 vectors in FP64; the cross-block sums
-// are FP64 in a fixed order, so results are reproducible run to run.
-// The Hessenberg least-squares problem stays in FP64 on the device.
+// For FP32 vectors the sums stay in double-float FP32 arithmetic through the
+// warp, block and cross-block reductions and reach FP64 once per column:
+// GB300 runs FP64 at a small fraction of its FP32 rate, and FP64 reductions
+// in every lane cost a fifth of a dots pass. FP64 vectors accumulate in FP64.
+// All sums are in a fixed order, so results are reproducible run to run. The
+// Hessenberg least-squares problem stays in FP64 on the device.
 #include "m1_internal.h"
 
 #include <algorithm>
@@ -38,8 +34,8 @@ namespace m1 {
 static constexpr int kOrThreads = 128;            // threads per block (one 16-byte slot each per row)
 static constexpr int kCols = kMaxRestart + 1;     // partial row: h_0..h_{kCols-1}, then ||w||^2
 static constexpr int kHLd = kMaxRestart + 1;
-static_assert(kCols + 1 == 32, "the last-block reduction reads partial rows of 32 eight-byte columns");
-static_assert(kOrThreads == 128, "the last-block reduction maps 128 threads onto 8 x 16 double pairs");
+static_assert(kCols + 1 == 32, "the partial-row reduction reads rows of 32 eight-byte columns");
+static_assert(kOrThreads == 128, "the partial-row reduction maps 128 threads onto 8 x 16 column pairs");
 
 enum GsMode : int { kDots = 0, kDotsResidual = 1, kUpdate = 2 };
 
@@ -112,7 +108,7 @@ template <> struct Acc<float> {
 };
 
 // Per-column partial sums: double-float pairs for FP32 vectors (so that no
-// lane does FP64 work before the last block converts each column once: FP64
+// lane does FP64 work before the final reduction converts each column once: FP64
 // is a narrow pipe on this GPU), FP64 for FP64 vectors. Both are 8 bytes, a
 // partial row of 32 columns is 256 bytes, and two columns load as 16 bytes.
 template <class T> struct Part;
@@ -204,7 +200,51 @@ __device__ __forceinline__ void scale(double2& x, double a) {
     x.y *= a;
 }
 
+// Fixed-order sum of the partial rows part[0 .. nb) (kCols + 1 eight-byte
+// columns each) into tot[] (FP64), by all kOrThreads threads of the block:
+// thread t adds the column pair (2 (t % 16), 2 (t % 16) + 1) of rows t / 16,
+// t / 16 + 8, ... with 16-byte loads; only the pairs holding columns 0..j and
+// the ||.||^2 column are read. Every block that calls it on the same rows gets
+// the same values bit for bit.
+template <class T>
+__device__ void reduce_rows(const double* part_raw, int nb, int j, typename Part<T>::type (*tot8)[kCols + 1],
+                            double* tot) {
+    using P = Part<T>;
+    using PT = typename P::type;
+    const int tid = threadIdx.x;
+    const int c2 = tid & 15, r0 = tid >> 4;
+    const bool need = 2 * c2 <= j || c2 == 15;
+    PT s0 = P::zero(), s1 = P::zero();
+    if (need) {
+        const PT* base = reinterpret_cast<const PT*>(part_raw);
+#pragma unroll 8
+        for (int b = r0; b < nb; b += 8) {
+            const typename P::pair v =
+                __ldcg(reinterpret_cast<const typename P::pair*>(base + (long long)b * (kCols + 1)) + c2);
+            PT x0, x1;
+            P::split(v, x0, x1);
+            s0 = P::add(s0, x0);
+            s1 = P::add(s1, x1);
+        }
+    }
+    tot8[r0][2 * c2] = s0;
+    tot8[r0][2 * c2 + 1] = s1;
+    __syncthreads();
+    if (tid <= kCols) {
+        PT v = tot8[0][tid];
+#pragma unroll
+        for (int r = 1; r < 8; ++r) v = P::add(v, tot8[r][tid]);
+        tot[tid] = P::to_double(v);
+    }
+    __syncthreads();
+}
+
 // Gram-Schmidt pass of Arnoldi step j (mode: kDots, kDotsResidual, kUpdate).
+// The dots passes only write one partial row per block; the next pass reduces
+// them itself, in every block (a short parallel prologue instead of one
+// block's serial tail): the residual-dots pass decides the
+// Daniel-Gragg-Kaufman-Stewart test from the first dots, the update from both,
+// and block 0 of the update rotates the Hessenberg column.
 // NC >= j + 1 (a multiple of 4, at most 32) is the compile-time number of rows
 // a thread loads per 16-byte slot: all of them are issued before any is used,
 // so each thread keeps NC loads in flight. Rows above j re-read row j (an L1/L2
@@ -215,23 +255,60 @@ __global__ void __launch_bounds__(kOrThreads) k_gram_schmidt(ArnoldiDev K, T* __
                                                              const T* __restrict__ w, int j, int mode) {
     using VT = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
-    const int reorth = mode == kDots ? 0 : *K.reorth;
-    if (mode == kDotsResidual && reorth == 0) return;  // uniform over the grid
     using P = Part<T>;
     using PT = typename P::type;
     __shared__ T h1s[kCols + 1], h2s[kCols + 1];
     __shared__ PT red[kOrThreads / 32][kCols + 1];
-    __shared__ int last;
+    __shared__ PT tot8[8][kCols + 1];
+    __shared__ double tot1[kCols + 1], tot2[kCols + 1];
+    __shared__ double col[kCols + 1], scs[kCols], ssn[kCols];
     const int tid = threadIdx.x;
+    const int nb = K.grid_dots[j];
+    bool reorth = false;
+    double beta2 = 0.0;
     if (mode != kDots) {
+        // h1 = V^T w and ||w||^2 from the first dots pass; the second pass when
+        // ||w - V h1||^2 = ||w||^2 - ||h1||^2 is not above ||w||^2 / 2
+        reduce_rows<T>(K.partials, nb, j, tot8, tot1);
+        double hh = 0.0;
+        for (int i = 0; i <= j; ++i) hh += tot1[i] * tot1[i];
+        const double wn2 = tot1[kCols];
+        beta2 = wn2 - hh;
+        reorth = !(beta2 > 0.5 * wn2);
+        if (mode == kDotsResidual && !reorth) return;  // uniform over the grid
+        if (mode == kUpdate && reorth) {
+            reduce_rows<T>(K.partials2, nb, j, tot8, tot2);
+            double hh2 = 0.0;
+            for (int i = 0; i <= j; ++i) hh2 += tot2[i] * tot2[i];
+            beta2 = tot2[kCols] - hh2;
+        }
         if (tid <= kCols) {
-            h1s[tid] = tid <= j ? (T)K.h1[tid] : T(0);
-            h2s[tid] = (tid <= j && reorth) ? (T)K.h2[tid] : T(0);
+            h1s[tid] = tid <= j ? (T)tot1[tid] : T(0);
+            h2s[tid] = (tid <= j && reorth) ? (T)tot2[tid] : T(0);
         }
         __syncthreads();
     }
     const bool dots = mode != kUpdate;
-    const T inv = dots ? T(1) : (T)K.nrm2[2];
+    const double beta = sqrt(fmax(beta2, 0.0));
+    const T inv = dots ? T(1) : (beta > 0.0 ? (T)(1.0 / beta) : T(0));
+    if (mode == kUpdate && blockIdx.x == 0) {
+        // the Hessenberg column h1 (+ h2), beta: rotations, g, the estimate
+        if (tid <= j) {
+            K.h1[tid] = tot1[tid];
+            if (reorth) K.h2[tid] = tot2[tid];
+            col[tid] = reorth ? tot1[tid] + tot2[tid] : tot1[tid];
+        }
+        if (tid < j) {
+            scs[tid] = K.cs[tid];
+            ssn[tid] = K.sn[tid];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            *K.reorth = reorth ? 1 : 0;
+            K.resid[2] = reorth ? 1.0 : 0.0;
+            givens_column(K, col, scs, ssn, beta, j);
+        }
+    }
     Acc<T> acc[NC];
     Acc<T> ww;
 #pragma unroll
@@ -300,7 +377,7 @@ __global__ void __launch_bounds__(kOrThreads) k_gram_schmidt(ArnoldiDev K, T* __
         }
     }
     if (!dots) return;
-    // block partials: h_0..h_j and ||x||^2
+    // this block's partial row: h_0..h_j and ||x||^2
     const int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
@@ -314,77 +391,12 @@ __global__ void __launch_bounds__(kOrThreads) k_gram_schmidt(ArnoldiDev K, T* __
         if (lane == 0) red[wid][kCols] = v;
     }
     __syncthreads();
-    PT* part = reinterpret_cast<PT*>(K.partials) + (long long)blockIdx.x * (kCols + 1);
+    PT* part = reinterpret_cast<PT*>(mode == kDots ? K.partials : K.partials2) + (long long)blockIdx.x * (kCols + 1);
     if (tid <= j || tid == kCols) {
         PT v = red[0][tid];
 #pragma unroll
         for (int qq = 1; qq < kOrThreads / 32; ++qq) v = P::add(v, red[qq][tid]);
         part[tid] = v;
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) last = (atomicAdd(K.counter, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!last) return;
-    // the last block: fixed-order sums over the partial rows. Thread t adds the
-    // column pair (2 (t % 16), 2 (t % 16) + 1) of rows t / 16, t / 16 + 8, ...
-    // with 16-byte loads (columns above j hold stale values and are not used);
-    // each column reaches FP64 once
-    __shared__ PT tot8[8][kCols + 1];
-    __shared__ double tot[kCols + 1];
-    {
-        const int c2 = tid & 15, r0 = tid >> 4;
-        const int nb = (int)gridDim.x;
-        PT s0 = P::zero(), s1 = P::zero();
-        const PT* base = reinterpret_cast<const PT*>(K.partials);
-#pragma unroll 8
-        for (int b = r0; b < nb; b += 8) {
-            const typename P::pair v = __ldcg(reinterpret_cast<const typename P::pair*>(base + (long long)b * (kCols + 1)) + c2);
-            PT c0, c1;
-            P::split(v, c0, c1);
-            s0 = P::add(s0, c0);
-            s1 = P::add(s1, c1);
-        }
-        tot8[r0][2 * c2] = s0;
-        tot8[r0][2 * c2 + 1] = s1;
-    }
-    __syncthreads();
-    if (tid <= kCols) {
-        PT v = tot8[0][tid];
-#pragma unroll
-        for (int r = 1; r < 8; ++r) v = P::add(v, tot8[r][tid]);
-        tot[tid] = P::to_double(v);
-    }
-    __syncthreads();
-    // stage the previous rotations and the column (h1 [+ h2]) in shared memory
-    __shared__ double col[kCols + 1], scs[kCols], ssn[kCols];
-    double* h = mode == kDots ? K.h1 : K.h2;
-    if (tid <= j) {
-        const double hv = tot[tid];
-        h[tid] = hv;
-        col[tid] = mode == kDotsResidual ? K.h1[tid] + hv : hv;
-    }
-    if (tid < j) {
-        scs[tid] = K.cs[tid];
-        ssn[tid] = K.sn[tid];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        *K.counter = 0u;
-        double hh = 0.0;
-        for (int i = 0; i <= j; ++i) hh += tot[i] * tot[i];
-        const double wn2 = tot[kCols];
-        const double rest = wn2 - hh;
-        if (mode == kDots && !(rest > 0.5 * wn2)) {
-            *K.reorth = 1;  // the second pass decides the column
-            K.resid[2] = 1.0;
-        } else {
-            if (mode == kDots) {
-                K.resid[2] = 0.0;
-                *K.reorth = 0;
-            }
-            givens_column(K, col, scs, ssn, sqrt(fmax(rest, 0.0)), j);
-        }
     }
 }
 
@@ -397,9 +409,9 @@ static int gs_grid_one(int j, long long n, int sms, bool dots) {
         occ = 1;
     const long long nv = n / Vec<T>::W;
     const long long tiles = std::max(1LL, (nv + kOrThreads - 1) / kOrThreads);
-    // the dots passes end in one block summing a partial row per block: two
-    // blocks per SM keep that tail short (the U-slot trips keep loads in flight)
-    if (dots) occ = std::min(occ, 2);
+    // every block of the next pass reads the dots passes' partial rows: at most
+    // three blocks per SM keep that prologue short
+    if (dots) occ = std::min(occ, 3);
     return (int)std::min<long long>({(long long)occ * sms, tiles, (long long)kMaxGsBlocks});
 }
 

@@ -63,8 +63,9 @@ struct ArnoldiDev {
     long long n, ld;     // vector length, basis stride
     int grid[kMaxRestart];       // blocks of the update pass of Arnoldi step j
     int grid_dots[kMaxRestart];  // blocks of its dots passes (partials holds one row of kMaxRestart + 2 per block)
-    double *H, *cs, *sn, *g, *resid, *h1, *h2, *nrm2, *partials;
-    unsigned* counter;   // arrival counter of the last-block reduction (kept at 0 between launches)
+    double *H, *cs, *sn, *g, *resid, *h1, *h2, *nrm2;
+    double* partials;    // one row per block of the first dots pass
+    double* partials2;   // and of the second (residual) dots pass
     int* reorth;         // 1 when the second Gram-Schmidt pass runs
 };
 constexpr int kMaxGsBlocks = 4096;  // bound of ArnoldiDev::grid, rows of ArnoldiDev::partials
