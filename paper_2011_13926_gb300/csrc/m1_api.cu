@@ -91,7 +91,8 @@ struct m1_ctx {
     double* scal_base = nullptr;
     int* singular = nullptr;
     unsigned long long* viol = nullptr;
-    double* hpin = nullptr;  // pinned host scalars
+    double* hpin = nullptr;      // pinned host scalars (mapped)
+    double* hpin_dev = nullptr;  // their device address, or null when mapping is unavailable
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ev_res[2] = {nullptr, nullptr};  // residual estimate of Arnoldi steps j (even, odd) on the host
     // per-kernel-class timers (m1_profile)
@@ -485,6 +486,7 @@ ArnoldiDev arnoldi_dev(m1_ctx* ctx, bool fp32) {
     K.partials = ctx->ar_partials;
     K.partials2 = ctx->ar_partials + (size_t)kMaxGsBlocks * (kPartCols + 1);
     K.reorth = ctx->ar_reorth;
+    K.resid_host = nullptr;
     return K;
 }
 inline void arnoldi_step(const ArnoldiDev& K, double* V, double* w, int j, cudaStream_t s) {
@@ -550,11 +552,16 @@ m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, doub
             }
             {
                 TK t(ctx, M1_K_ORTHO);
-                arnoldi_step(arnoldi_dev(ctx, sizeof(T) == 4), V, w, j, s);
+                // the update pass writes step j's estimate straight into the
+                // mapped host slot; without mapping it is copied after the pass
+                ArnoldiDev K = arnoldi_dev(ctx, sizeof(T) == 4);
+                K.resid_host = ctx->hpin_dev ? ctx->hpin_dev + 8 + 4 * (j & 1) : nullptr;
+                arnoldi_step(K, V, w, j, s);
             }
             count(ctx, 3);
-            CK(cudaMemcpyAsync(ctx->hpin + 8 + 4 * (j & 1), sc.resid, 3 * sizeof(double), cudaMemcpyDeviceToHost,
-                               s));
+            if (!ctx->hpin_dev)
+                CK(cudaMemcpyAsync(ctx->hpin + 8 + 4 * (j & 1), sc.resid, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                                   s));
             CK(cudaEventRecord(ctx->ev_res[j & 1], s));
         }
         if (j == 0) continue;
@@ -859,7 +866,12 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
     ctx->sc.sn = p;
     p += kMaxRestart;
     ctx->sc.resid = p;
-    if (cudaMallocHost((void**)&ctx->hpin, 16 * sizeof(double)) != cudaSuccess) return cleanup(M1_ERR_NOMEM);
+    if (cudaHostAlloc((void**)&ctx->hpin, 16 * sizeof(double), cudaHostAllocMapped) != cudaSuccess)
+        return cleanup(M1_ERR_NOMEM);
+    if (cudaHostGetDevicePointer((void**)&ctx->hpin_dev, ctx->hpin, 0) != cudaSuccess) {
+        ctx->hpin_dev = nullptr;  // fall back to copies
+        cudaGetLastError();
+    }
     if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_res[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_res[1], cudaEventDisableTiming) != cudaSuccess)
@@ -881,11 +893,12 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
         const double nu = ctx->nu, dim = ctx->dim;
         const double fields = 2.0 + dim + (desc->implicit_eigs ? 0.0 : 2.0 * dim) + (desc->gas_coupling ? 1.0 : 0.0);
         // the linear 2D J v reads v and dP/dU (9 planes, + d(a_r T^4)/dT with
-        // gas) instead of U and v
+        // gas) instead of U and v; the FP32 one also reads the n_u x n_u block
+        // inverse it applies while staging (J M^-1 v)
         const bool lin = desc->dim == 2 && (desc->fixed_eigs || !desc->implicit_eigs);
         const double jv_fields = lin ? 2.0 * nu + fields + 9.0 + (desc->gas_coupling ? 1.0 : 0.0) : 3.0 * nu + fields;
         ctx->st.bytes_per_jv = (double)N * 8.0 * jv_fields;
-        ctx->st.bytes_per_jv32 = (double)N * 4.0 * jv_fields;
+        ctx->st.bytes_per_jv32 = (double)N * 4.0 * (jv_fields + (lin ? nu * nu : 0.0));
         ctx->st.bytes_per_residual = (double)N * 8.0 * (3.0 * nu + fields + (desc->gas_coupling ? 0.0 : 1.0));
     }
     *out = ctx;

@@ -307,6 +307,11 @@ __global__ void __launch_bounds__(kOrThreads) k_gram_schmidt(ArnoldiDev K, T* __
             *K.reorth = reorth ? 1 : 0;
             K.resid[2] = reorth ? 1.0 : 0.0;
             givens_column(K, col, scs, ssn, beta, j);
+            if (K.resid_host) {
+                K.resid_host[0] = K.resid[0];
+                K.resid_host[1] = K.resid[1];
+                K.resid_host[2] = K.resid[2];
+            }
         }
     }
     Acc<T> acc[NC];

@@ -67,6 +67,7 @@ struct ArnoldiDev {
     double* partials;    // one row per block of the first dots pass
     double* partials2;   // and of the second (residual) dots pass
     int* reorth;         // 1 when the second Gram-Schmidt pass runs
+    double* resid_host;  // if set: resid[0..2] also written here (mapped pinned host memory)
 };
 constexpr int kMaxGsBlocks = 4096;  // bound of ArnoldiDev::grid, rows of ArnoldiDev::partials
 // blocks of each Arnoldi step's passes for vectors of length n (occupancy of this device)
