@@ -55,7 +55,7 @@ typedef enum {
 typedef enum { M1_BC_OUTFLOW = 0, M1_BC_PERIODIC = 1, M1_BC_REFLECT = 2, M1_BC_DIRICHLET = 3 } m1_bc;
 typedef enum { M1_MEM_HOST = 0, M1_MEM_DEVICE = 1 } m1_mem;
 typedef enum { M1_PREC_FP64 = 0, M1_PREC_MIXED = 1 } m1_precision;
-typedef enum { M1_PRECOND_NONE = 0, M1_PRECOND_BJ = 1, M1_PRECOND_LEARNED = 2 } m1_precond;
+typedef enum { M1_PRECOND_NONE = 0, M1_PRECOND_BJ = 1, M1_PRECOND_LEARNED = 2, M1_PRECOND_MG = 3 } m1_precond;
 
 /* Grid and discretisation flags (one context per grid). */
 typedef struct {
@@ -81,7 +81,9 @@ typedef struct {
     int gmres_max;        /* 3000 total Arnoldi iterations per linear solve */
     double gmres_rtol;    /* 1e-4: forcing term ||J d + R|| <= rtol ||R|| */
     int precision;        /* m1_precision: FP64, or FP32 inner FGMRES under FP64 refinement */
-    int precond;          /* m1_precond; M1_PRECOND_LEARNED needs M1_PREC_MIXED and m1_set_preconditioner */
+    int precond;          /* m1_precond; M1_PRECOND_LEARNED needs M1_PREC_MIXED and m1_set_preconditioner;
+                             M1_PRECOND_MG needs M1_PREC_MIXED, dim 2, no gas coupling and frozen or fixed
+                             wave speeds (see m1_mg_apply) */
     int line_search;      /* 1: halve theta up to 6 times until the Armijo decrease holds */
     int advance;          /* 1: on success U^n <- U^{n+1}; 0: keep U^n (result in m1_get_solution) */
     int refine_max;       /* mixed precision: max FP64 refinement sweeps per Newton step (4) */
@@ -210,6 +212,28 @@ m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double
 /* Point blocks J_ii = dR_i/dU_i of m1_residual at U (Sect. 3.3.2 block Jacobi):
  * n_u*n_u*N doubles laid out blocks[(row*n_u + col)*N + cell]. */
 m1_status m1_diag_blocks(m1_ctx* ctx, double dt, const double* U, double* blocks, m1_mem mem);
+
+/* The multigrid preconditioner (M1_PRECOND_MG): the structured-grid analogue of
+ * the algebraic multigrid the paper found best among its preconditioners
+ * (Sect. 3.3.2, Sect. 4). 2D, radiation only, frozen or fixed wave speeds, FP32.
+ * Level 0 is J(U) itself (applied as J v) with the point-block inverses as
+ * smoother; its 5-point stencil of n_u x n_u blocks is read off J v by coloured
+ * probes; levels >= 1 aggregate 2 x 2 cells (piecewise-constant prolongation,
+ * summing restriction, Galerkin stencil P^T A P) until both sides are <= 32
+ * cells. One application is a V(1,1) cycle from zero with damped point-block
+ * Jacobi (omega 0.7) and 10 damped sweeps on the coarsest level; it is linear in
+ * r. Periodic axes need at least 3 cells.
+ *
+ * m1_mg_apply builds the hierarchy at U (U NULL = the time-n state) for step
+ * size dt and returns z = one cycle applied to r (n_u*N doubles each, rounded to
+ * FP32 and widened back). */
+m1_status m1_mg_apply(m1_ctx* ctx, double dt, const double* U, const double* r, double* z, m1_mem mem);
+
+/* After m1_mg_apply: the number of levels, and the stencil of one level as
+ * 5*n_u*n_u*N_level doubles, A[((s*n_u + row)*n_u + col)*N_level + cell] with s =
+ * 0..4 the (self, -x, +x, -y, +y) neighbour; N_level = nx*ny of that level
+ * (sizes halve with ceil from the grid's). A NULL out only reports nlev. */
+m1_status m1_mg_blocks(m1_ctx* ctx, int level, int* nlev, double* out, m1_mem mem);
 
 /* Solve J(U) x = b with the step's GMRES (U NULL = the time-n state).
  * x is the output (initial guess 0). */

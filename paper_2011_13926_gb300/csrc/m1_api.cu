@@ -79,6 +79,11 @@ struct m1_ctx {
     float* Z32 = nullptr;       // flexible-GMRES basis of preconditioned vectors
     double* pj64 = nullptr;     // dP/dU at the Newton iterate (2D frozen wave speeds), FP64
     float* pj32 = nullptr;      // the same in FP32
+    // multigrid preconditioner (allocated on first use)
+    MgHierarchy mg;
+    bool mg_alloc = false;
+    double* mg_inv64 = nullptr;  // FP64 scratch of the coarse block inverses
+    Dev<float> mg_g32{};         // the step's FP32 descriptor the level-0 J v uses
     float *pair_x = nullptr, *pair_t = nullptr;  // staging of one training pair (4N and 3N floats)
     double* vel[3] = {nullptr, nullptr, nullptr};  // prescribed face velocities (gas advection)
     double* partials = nullptr;
@@ -385,6 +390,64 @@ m1_status pressure_jacobian(m1_ctx* ctx, const Dev<double>& g, const double* U, 
     return M1_OK;
 }
 
+// ---------------------------------------------------------------- multigrid
+bool mg_supported(const m1_ctx* ctx, const Dev<double>& g) {
+    if (!jv_linear_available(g) || ctx->dim != 2 || ctx->d.gas_coupling) return false;
+    for (int a = 0; a < 2; ++a) {
+        if (ctx->d.bc[a][0] == M1_BC_PERIODIC && ctx->d.n[a] < 3) return false;
+        // the level cap keeps the coarsest level within one CTA (<= 32 cells a side)
+        if ((long long)ctx->d.n[a] > (32LL << (kMgMaxLevels - 1))) return false;
+    }
+    return true;
+}
+
+void mg_jv_apply(void* c, const float* in, float* out, cudaStream_t s) {
+    m1_ctx* ctx = static_cast<m1_ctx*>(c);
+    launch_jv_linear_f32(ctx->mg_g32, ctx->U32, ctx->pj32, in, out, s);
+}
+
+m1_status ensure_mg(m1_ctx* ctx) {
+    if (ctx->mg_alloc) return M1_OK;
+    MgHierarchy& H = ctx->mg;
+    mg_plan(H, ctx->nu, ctx->d.n[0], ctx->d.n[1], ctx->d.bc[0][0] == M1_BC_PERIODIC,
+            ctx->d.bc[1][0] == M1_BC_PERIODIC);
+    const size_t nu = (size_t)ctx->nu;
+    for (int l = 0; l < H.nlev; ++l) {
+        const size_t N = (size_t)H.nx[l] * H.ny[l];
+        CKS(dalloc(ctx, &H.A[l], 5 * nu * nu * N));
+        if (l > 0) {
+            CKS(dalloc(ctx, &H.Dinv[l], nu * nu * N));
+            CKS(dalloc(ctx, &H.r[l], nu * N));
+        }
+        CKS(dalloc(ctx, &H.z[l], nu * N));
+        CKS(dalloc(ctx, &H.z2[l], nu * N));
+    }
+    CKS(dalloc(ctx, &H.w0, nu * ctx->N));
+    CKS(dalloc(ctx, &H.probe, nu * ctx->N));
+    const size_t N1 = H.nlev > 1 ? (size_t)H.nx[1] * H.ny[1] : 1;
+    CKS(dalloc(ctx, &ctx->mg_inv64, nu * nu * N1));
+    ctx->mg_alloc = true;
+    return M1_OK;
+}
+
+// the hierarchy at the FP32 state U32 (pj32 and binv32 already built for it)
+m1_status build_mg(m1_ctx* ctx, const Dev<float>& g32) {
+    CKS(ensure_mg(ctx));
+    TK t(ctx, M1_K_PC_BUILD);
+    ctx->mg_g32 = g32;
+    ctx->mg.Dinv[0] = ctx->binv32;
+    const MgJvOp op{ctx, mg_jv_apply};
+    mg_build(ctx->mg, op, ctx->mg_inv64, ctx->singular, ctx->s);
+    count(ctx, mg_launches_per_build(ctx->mg));
+    return M1_OK;
+}
+
+void mg_apply(m1_ctx* ctx, const float* in, float* out) {
+    const MgJvOp op{ctx, mg_jv_apply};
+    mg_cycle(ctx->mg, op, in, out, ctx->s);
+    count(ctx, mg_launches_per_cycle(ctx->mg));
+}
+
 m1_status build_precond(m1_ctx* ctx, const Dev<double>& g, const double* U) {
     TK t(ctx, M1_K_PC_BUILD);
     launch_diag_f64(g, U, ctx->blocks, ctx->s);
@@ -433,8 +496,9 @@ struct Ops32 {
     bool precond;
     bool learned = false;
     const float* pj = nullptr;  // dP/dU at U in FP32: J v as a linear stencil, else by dual numbers
+    bool mg = false;            // M^-1: one multigrid cycle instead of point-block Jacobi
     // J M^-1 v in one stencil (point-block Jacobi applied while staging)
-    bool fused() const { return pj && precond && !learned; }
+    bool fused() const { return pj && precond && !learned && !mg; }
     void AM(const float* in, float* out) {
         TK t(ctx, M1_K_JV32);
         launch_jv_linear_pre_f32(g, U, pj, ctx->binv32, in, out, ctx->s);
@@ -452,6 +516,10 @@ struct Ops32 {
     }
     void M(const float* in, float* out) {
         TK t(ctx, M1_K_PC_APPLY);
+        if (mg) {
+            mg_apply(ctx, in, out);
+            return;
+        }
         if (precond) {
             launch_bj_apply_f32(ctx->nu, ctx->N, ctx->binv32, in, out, ctx->s);
         } else {
@@ -702,6 +770,12 @@ m1_status gmres_mixed(m1_ctx* ctx, Ops64& ops64, Ops32& ops32, const double* b, 
             *iters += k;
             if (flexible) {  // tmp = Z y already holds the preconditioned combination
                 launch_axpy_f64(1.0, ctx->tmp, ctx->xacc, n, s);
+            } else if (ops32.mg) {  // M^-1 (V y): the same FP32 cycle the Krylov space used
+                launch_f64_to_f32(ctx->tmp, ctx->tmp32, n, s);
+                ops32.M(ctx->tmp32, ctx->z32);
+                launch_f32_to_f64(ctx->z32, ctx->z, n, s);
+                launch_axpy_f64(1.0, ctx->z, ctx->xacc, n, s);
+                count(ctx, 2);
             } else {
                 ops64.M(ctx->tmp, ctx->z);
                 launch_axpy_f64(1.0, ctx->z, ctx->xacc, n, s);
@@ -915,6 +989,13 @@ m1_status m1_destroy(m1_ctx* ctx) {
                     ctx->partials, ctx->scal_base, ctx->singular, ctx->viol, ctx->ar_partials,
                     ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32};
     for (void* q : ptrs)
+        if (q) cudaFree(q);
+    for (int l = 0; l < kMgMaxLevels; ++l) {
+        for (float* q : {ctx->mg.A[l], ctx->mg.r[l], ctx->mg.z[l], ctx->mg.z2[l]})
+            if (q) cudaFree(q);
+        if (l > 0 && ctx->mg.Dinv[l]) cudaFree(ctx->mg.Dinv[l]);
+    }
+    for (void* q : {(void*)ctx->mg.w0, (void*)ctx->mg.probe, (void*)ctx->mg_inv64})
         if (q) cudaFree(q);
     for (int a = 0; a < 3; ++a) {
         void* fp[] = {ctx->f64.alpha[a], ctx->f64.lam_p[a], ctx->f64.lam_m[a],
@@ -1136,6 +1217,56 @@ m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double
     return sync(ctx);
 }
 
+m1_status m1_mg_apply(m1_ctx* ctx, double dt, const double* U, const double* r, double* z, m1_mem mem) {
+    if (!ctx || !r || !z) return M1_ERR_ARG;
+    CKS(prepare(ctx));
+    CKS(ensure_work(ctx));
+    CKS(ensure_work32(ctx));
+    if (U)
+        CKS(copy_in(ctx, ctx->U, U, sizeof(double) * ctx->n, mem));
+    else
+        CK(cudaMemcpyAsync(ctx->U, ctx->Un, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s));
+    const Dev<double> g = dev64(ctx, dt);
+    if (!mg_supported(ctx, g))
+        return fail(ctx, M1_ERR_ARG,
+                    "multigrid needs dim 2, no gas coupling, frozen or fixed wave speeds and >= 3 cells along "
+                    "periodic axes");
+    bool lin = false;
+    CKS(pressure_jacobian(ctx, g, ctx->U, true, &lin));
+    launch_f64_to_f32(ctx->U, ctx->U32, ctx->n, ctx->s);
+    const Dev<float> g32 = dev32(ctx, dt);
+    launch_diag_f32(g32, ctx->U32, reinterpret_cast<float*>(ctx->blocks), ctx->s);
+    CK(cudaMemsetAsync(ctx->singular, 0, sizeof(int), ctx->s));
+    launch_block_inverse_f32(ctx->nu, ctx->N, reinterpret_cast<const float*>(ctx->blocks), ctx->binv, ctx->binv32,
+                             ctx->singular, ctx->s);
+    count(ctx, 3);
+    CKS(build_mg(ctx, g32));
+    CKS(copy_in(ctx, ctx->tmp, r, sizeof(double) * ctx->n, mem));
+    launch_f64_to_f32(ctx->tmp, ctx->tmp32, ctx->n, ctx->s);
+    mg_apply(ctx, ctx->tmp32, ctx->z32);
+    launch_f32_to_f64(ctx->z32, ctx->w, ctx->n, ctx->s);
+    count(ctx, 2);
+    CKS(copy_out(ctx, z, ctx->w, sizeof(double) * ctx->n, mem));
+    return sync(ctx);
+}
+
+m1_status m1_mg_blocks(m1_ctx* ctx, int level, int* nlev, double* out, m1_mem mem) {
+    if (!ctx) return M1_ERR_ARG;
+    if (!ctx->mg_alloc) return fail(ctx, M1_ERR_STATE, "no multigrid hierarchy built yet (m1_mg_apply)");
+    if (nlev) *nlev = ctx->mg.nlev;
+    if (!out) return M1_OK;
+    if (level < 0 || level >= ctx->mg.nlev) return fail(ctx, M1_ERR_ARG, "level out of range");
+    const size_t cnt = (size_t)5 * ctx->nu * ctx->nu * ctx->mg.nx[level] * ctx->mg.ny[level];
+    // widened through the level-0 FP64 block scratch when it is large enough, else in pieces
+    const size_t chunk = (size_t)ctx->nu * ctx->nu * ctx->N;
+    for (size_t off = 0; off < cnt; off += chunk) {
+        const size_t k = std::min(chunk, cnt - off);
+        launch_f32_to_f64(ctx->mg.A[level] + off, ctx->blocks, (long long)k, ctx->s);
+        CKS(copy_out(ctx, out + off, ctx->blocks, sizeof(double) * k, mem));
+    }
+    return sync(ctx);
+}
+
 m1_status m1_diag_blocks(m1_ctx* ctx, double dt, const double* U, double* blocks, m1_mem mem) {
     if (!ctx || !U || !blocks) return M1_ERR_ARG;
     CKS(prepare(ctx));
@@ -1151,13 +1282,18 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
                               const m1_solver_opts* o, int* iters, int* refinements, double* bnorm, double* res,
                               bool* conv) {
     const bool learned = o->precond == M1_PRECOND_LEARNED;
-    const bool pre = o->precond == M1_PRECOND_BJ || learned;
+    const bool use_mg = o->precond == M1_PRECOND_MG;
+    const bool pre = o->precond == M1_PRECOND_BJ || learned || use_mg;
     if (o->restart < 1 || o->restart > kMaxRestart)
         return fail(ctx, M1_ERR_ARG, "restart must be in [1, 30]");
     if (learned && (o->precision != M1_PREC_MIXED || !ctx->nn))
         return fail(ctx, M1_ERR_ARG, "the learned preconditioner needs M1_PREC_MIXED and m1_set_preconditioner");
     if (learned) CKS(dalloc(ctx, &ctx->Z32, (size_t)ctx->ld * (kMaxRestart + 1)));
     Dev<double> g = dev64(ctx, dt);
+    if (use_mg && (o->precision != M1_PREC_MIXED || !mg_supported(ctx, g)))
+        return fail(ctx, M1_ERR_ARG,
+                    "M1_PRECOND_MG needs M1_PREC_MIXED, dim 2, no gas coupling, frozen or fixed wave speeds and "
+                    ">= 3 cells along periodic axes");
     Ops64 ops{ctx, g, Ud, pre};
     bool lin = false;
     CKS(pressure_jacobian(ctx, g, Ud, o->precision == M1_PREC_MIXED, &lin));
@@ -1177,8 +1313,10 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
             count(ctx, 2);
             ctx->st.precond_builds++;
         }
+        if (use_mg) CKS(build_mg(ctx, g32));
         Ops32 ops32{ctx, g32, ctx->U32, pre};
         ops32.learned = learned;
+        ops32.mg = use_mg;
         if (lin) ops32.pj = ctx->pj32;
         return gmres_mixed(ctx, ops, ops32, b, x, o->gmres_rtol, o->restart, o->gmres_max, o->refine_max, iters,
                            refinements, bnorm, res, conv);

@@ -34,6 +34,35 @@ void launch_jv_linear_f32(const Dev<float>& g, const float* U, const float* pj, 
 // applied to v inside the stencil (M^-1 v is never stored)
 void launch_jv_linear_pre_f32(const Dev<float>& g, const float* U, const float* pj, const float* binv,
                               const float* v, float* Jv, cudaStream_t s);
+// ----------------------------------------------------------------- multigrid (m1_mg.cu)
+constexpr int kMgMaxLevels = 16;
+// the level-0 operator of the V-cycle: out = J in (FP32, the solver's linear J v)
+struct MgJvOp {
+    void* ctx;
+    void (*apply)(void* ctx, const float* in, float* out, cudaStream_t s);
+};
+// aggregation hierarchy of a 2D grid (FP32): level l is nx[l] x ny[l] cells; A[l]
+// the 5-point block stencil (5 n_u^2 planes; A[0] only feeds the coarsening),
+// Dinv[l] the inverses of its C blocks (Dinv[0]: the block-Jacobi inverses),
+// r/z/z2 per-level work vectors, w0 and probe level-0 work vectors
+struct MgHierarchy {
+    int nu = 0, nlev = 0;
+    bool px = false, py = false;
+    int nx[kMgMaxLevels] = {}, ny[kMgMaxLevels] = {};
+    float* A[kMgMaxLevels] = {};
+    float* Dinv[kMgMaxLevels] = {};
+    float* r[kMgMaxLevels] = {};
+    float* z[kMgMaxLevels] = {};
+    float* z2[kMgMaxLevels] = {};
+    float* w0 = nullptr;
+    float* probe = nullptr;
+};
+void mg_plan(MgHierarchy& H, int nu, int nx, int ny, bool px, bool py);
+int mg_colour_period(int n, bool periodic);
+void mg_build(MgHierarchy& H, const MgJvOp& J, double* inv64_scratch, int* singular, cudaStream_t s);
+void mg_cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float* zout, cudaStream_t s);
+int mg_launches_per_build(const MgHierarchy& H);
+int mg_launches_per_cycle(const MgHierarchy& H);
 // partial-sum entries the residual may need for this grid
 long long residual_partial_count(int dim, const int n[3]);
 void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s);

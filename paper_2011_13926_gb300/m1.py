@@ -23,7 +23,7 @@ STATUS_NAMES = ["M1_OK", "M1_ERR_ARG", "M1_ERR_CUDA", "M1_ERR_NOMEM", "M1_ERR_NO
 BC = {"outflow": 0, "periodic": 1, "reflect": 2, "dirichlet": 3}
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
-PRECOND_NONE, PRECOND_BJ, PRECOND_LEARNED = 0, 1, 2
+PRECOND_NONE, PRECOND_BJ, PRECOND_LEARNED, PRECOND_MG = 0, 1, 2, 3
 
 EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "m1_set_state", "m1_get_state",
             "m1_get_solution", "m1_set_boundary", "m1_set_emission", "m1_set_source", "m1_explicit_step",
@@ -148,6 +148,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_residual": (I, [P, D, P, P, I]),
         "m1_jv": (I, [P, D, P, P, P, I, I]),
         "m1_diag_blocks": (I, [P, D, P, P, I]),
+        "m1_mg_apply": (I, [P, D, P, P, P, I]),
+        "m1_mg_blocks": (I, [P, I, C.POINTER(I), P, I]),
         "m1_gmres_solve": (I, [P, D, P, P, P, C.POINTER(SolverOpts), C.POINTER(SolveInfo), I]),
         "m1_stats": (I, [P, C.POINTER(Stats)]),
         "m1_profile": (I, [P, I]),
@@ -356,6 +358,28 @@ class Context:
         po, mo, ko = _ptr(out)
         self._call("m1_diag_blocks", C.c_double(dt), pu, po, _check_mem(mu, mo))
         return out
+
+    def mg_apply(self, dt: float, r, U=None, out=None):
+        """One multigrid cycle z ~ J(U)^-1 r, the hierarchy built at U (None: time-n state)."""
+        pu, mu, ku = _ptr(U)
+        pr, mr, kr = _ptr(r)
+        if out is None:
+            out = np.empty(self.nu * self.N)
+        po, mo, ko = _ptr(out)
+        self._call("m1_mg_apply", C.c_double(dt), pu, pr, po, _check_mem(mu, mr, mo))
+        return out
+
+    def mg_levels(self) -> int:
+        n = C.c_int(0)
+        self._call("m1_mg_blocks", 0, C.byref(n), None, MEM_HOST)
+        return n.value
+
+    def mg_blocks(self, level: int, nx: int, ny: int):
+        """Stencil of one level after mg_apply, shaped (5, n_u, n_u, nx * ny)."""
+        out = np.empty(5 * self.nu * self.nu * nx * ny)
+        n = C.c_int(0)
+        self._call("m1_mg_blocks", level, C.byref(n), out.ctypes.data, MEM_HOST)
+        return out.reshape(5, self.nu, self.nu, nx * ny)
 
     def gmres_solve(self, dt: float, b, U=None, out=None, opts: Optional[SolverOpts] = None,
                     raise_on_fail: bool = True):
