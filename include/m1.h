@@ -82,8 +82,8 @@ typedef struct {
     double gmres_rtol;    /* 1e-4: forcing term ||J d + R|| <= rtol ||R|| */
     int precision;        /* m1_precision: FP64, or FP32 inner FGMRES under FP64 refinement */
     int precond;          /* m1_precond; M1_PRECOND_LEARNED needs M1_PREC_MIXED and m1_set_preconditioner;
-                             M1_PRECOND_MG needs M1_PREC_MIXED, dim 2, no gas coupling and frozen or fixed
-                             wave speeds (see m1_mg_apply) */
+                             M1_PRECOND_MG needs M1_PREC_MIXED, dim 2 and frozen or fixed wave speeds
+                             (see m1_mg_apply) */
     int line_search;      /* 1: halve theta up to 6 times until the Armijo decrease holds */
     int advance;          /* 1: on success U^n <- U^{n+1}; 0: keep U^n (result in m1_get_solution) */
     int refine_max;       /* mixed precision: max FP64 refinement sweeps per Newton step (4) */
@@ -215,11 +215,12 @@ m1_status m1_diag_blocks(m1_ctx* ctx, double dt, const double* U, double* blocks
 
 /* The multigrid preconditioner (M1_PRECOND_MG): the structured-grid analogue of
  * the algebraic multigrid the paper found best among its preconditioners
- * (Sect. 3.3.2, Sect. 4). 2D, radiation only, frozen or fixed wave speeds, FP32.
- * Level 0 is J(U) itself (applied as J v) with the point-block inverses as
- * smoother; its 5-point stencil of n_u x n_u blocks is read off J v by coloured
- * probes; levels >= 1 aggregate 2 x 2 cells (piecewise-constant prolongation,
- * summing restriction, Galerkin stencil P^T A P) until both sides are <= 32
+ * (Sect. 3.3.2, Sect. 4). 2D, frozen or fixed wave speeds, FP32. Level 0 is
+ * J(U) itself (applied as J v) with the point-block inverses as smoother; its
+ * 5-point stencil of n_u x n_u blocks is assembled directly from the stored
+ * pressure Jacobian (radiation only) or read off J v by coloured probes (gas
+ * coupling); levels >= 1 aggregate 2 x 2 cells (piecewise-constant prolongation,
+ * summing restriction, Galerkin stencil P^T A P) until both sides are <= 16
  * cells. One application is a V(1,1) cycle from zero with damped point-block
  * Jacobi (omega 0.7) and 10 damped sweeps on the coarsest level; it is linear in
  * r. Periodic axes need at least 3 cells.

@@ -32,7 +32,7 @@ from typing import List, Tuple
 import numpy as np
 
 OMEGA = 0.7
-COARSEST = 32
+COARSEST = 16
 COARSE_SWEEPS = 10
 # stencil positions and their (dx, dy) offsets
 STENCIL = ((0, 0), (-1, 0), (1, 0), (0, -1), (0, 1))

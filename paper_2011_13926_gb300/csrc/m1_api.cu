@@ -84,6 +84,7 @@ struct m1_ctx {
     bool mg_alloc = false;
     double* mg_inv64 = nullptr;  // FP64 scratch of the coarse block inverses
     Dev<float> mg_g32{};         // the step's FP32 descriptor the level-0 J v uses
+    bool mg_probe = false;       // level-0 stencil by probes through J v instead of directly
     float *pair_x = nullptr, *pair_t = nullptr;  // staging of one training pair (4N and 3N floats)
     double* vel[3] = {nullptr, nullptr, nullptr};  // prescribed face velocities (gas advection)
     double* partials = nullptr;
@@ -392,11 +393,11 @@ m1_status pressure_jacobian(m1_ctx* ctx, const Dev<double>& g, const double* U, 
 
 // ---------------------------------------------------------------- multigrid
 bool mg_supported(const m1_ctx* ctx, const Dev<double>& g) {
-    if (!jv_linear_available(g) || ctx->dim != 2 || ctx->d.gas_coupling) return false;
+    if (!jv_linear_available(g) || ctx->dim != 2) return false;
     for (int a = 0; a < 2; ++a) {
         if (ctx->d.bc[a][0] == M1_BC_PERIODIC && ctx->d.n[a] < 3) return false;
-        // the level cap keeps the coarsest level within one CTA (<= 32 cells a side)
-        if ((long long)ctx->d.n[a] > (32LL << (kMgMaxLevels - 1))) return false;
+        // the level cap keeps the coarsest level within one CTA (<= 16 cells a side)
+        if ((long long)ctx->d.n[a] > (16LL << (kMgMaxLevels - 1))) return false;
     }
     return true;
 }
@@ -424,8 +425,7 @@ m1_status ensure_mg(m1_ctx* ctx) {
     }
     CKS(dalloc(ctx, &H.w0, nu * ctx->N));
     CKS(dalloc(ctx, &H.probe, nu * ctx->N));
-    const size_t N1 = H.nlev > 1 ? (size_t)H.nx[1] * H.ny[1] : 1;
-    CKS(dalloc(ctx, &ctx->mg_inv64, nu * nu * N1));
+    CKS(dalloc(ctx, &ctx->mg_inv64, nu * nu * (size_t)ctx->N));  // FP64 scratch of the block inverses
     ctx->mg_alloc = true;
     return M1_OK;
 }
@@ -435,10 +435,13 @@ m1_status build_mg(m1_ctx* ctx, const Dev<float>& g32) {
     CKS(ensure_mg(ctx));
     TK t(ctx, M1_K_PC_BUILD);
     ctx->mg_g32 = g32;
-    ctx->mg.Dinv[0] = ctx->binv32;
+    ctx->mg.Dinv[0] = ctx->binv32;  // written by the build from the level-0 C blocks
+    CK(cudaMemsetAsync(ctx->singular, 0, sizeof(int), ctx->s));
     const MgJvOp op{ctx, mg_jv_apply};
-    mg_build(ctx->mg, op, ctx->mg_inv64, ctx->singular, ctx->s);
-    count(ctx, mg_launches_per_build(ctx->mg));
+    const MgDirect direct{&ctx->mg_g32, ctx->U32, ctx->pj32};
+    const bool use_direct = ctx->nu == 3 && !ctx->mg_probe;
+    mg_build(ctx->mg, op, use_direct ? &direct : nullptr, ctx->mg_inv64, ctx->singular, ctx->s);
+    count(ctx, mg_launches_per_build(ctx->mg, use_direct));
     return M1_OK;
 }
 
@@ -1229,17 +1232,11 @@ m1_status m1_mg_apply(m1_ctx* ctx, double dt, const double* U, const double* r, 
     const Dev<double> g = dev64(ctx, dt);
     if (!mg_supported(ctx, g))
         return fail(ctx, M1_ERR_ARG,
-                    "multigrid needs dim 2, no gas coupling, frozen or fixed wave speeds and >= 3 cells along "
-                    "periodic axes");
+                    "multigrid needs dim 2, frozen or fixed wave speeds and >= 3 cells along periodic axes");
     bool lin = false;
     CKS(pressure_jacobian(ctx, g, ctx->U, true, &lin));
     launch_f64_to_f32(ctx->U, ctx->U32, ctx->n, ctx->s);
     const Dev<float> g32 = dev32(ctx, dt);
-    launch_diag_f32(g32, ctx->U32, reinterpret_cast<float*>(ctx->blocks), ctx->s);
-    CK(cudaMemsetAsync(ctx->singular, 0, sizeof(int), ctx->s));
-    launch_block_inverse_f32(ctx->nu, ctx->N, reinterpret_cast<const float*>(ctx->blocks), ctx->binv, ctx->binv32,
-                             ctx->singular, ctx->s);
-    count(ctx, 3);
     CKS(build_mg(ctx, g32));
     CKS(copy_in(ctx, ctx->tmp, r, sizeof(double) * ctx->n, mem));
     launch_f64_to_f32(ctx->tmp, ctx->tmp32, ctx->n, ctx->s);
@@ -1292,8 +1289,8 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
     Dev<double> g = dev64(ctx, dt);
     if (use_mg && (o->precision != M1_PREC_MIXED || !mg_supported(ctx, g)))
         return fail(ctx, M1_ERR_ARG,
-                    "M1_PRECOND_MG needs M1_PREC_MIXED, dim 2, no gas coupling, frozen or fixed wave speeds and "
-                    ">= 3 cells along periodic axes");
+                    "M1_PRECOND_MG needs M1_PREC_MIXED, dim 2, frozen or fixed wave speeds and >= 3 cells along "
+                    "periodic axes");
     Ops64 ops{ctx, g, Ud, pre};
     bool lin = false;
     CKS(pressure_jacobian(ctx, g, Ud, o->precision == M1_PREC_MIXED, &lin));
@@ -1304,7 +1301,7 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
         launch_f64_to_f32(Ud, ctx->U32, ctx->n, ctx->s);
         count(ctx, 1);
         const Dev<float> g32 = dev32(ctx, dt);
-        if (pre) {  // FP32 point blocks, inverted in FP64
+        if (pre && !use_mg) {  // FP32 point blocks, inverted in FP64 (multigrid takes them from its level 0)
             TK t(ctx, M1_K_PC_BUILD);
             launch_diag_f32(g32, ctx->U32, reinterpret_cast<float*>(ctx->blocks), ctx->s);
             CK(cudaMemsetAsync(ctx->singular, 0, sizeof(int), ctx->s));

@@ -59,9 +59,17 @@ struct MgHierarchy {
 };
 void mg_plan(MgHierarchy& H, int nu, int nx, int ny, bool px, bool py);
 int mg_colour_period(int n, bool periodic);
-void mg_build(MgHierarchy& H, const MgJvOp& J, double* inv64_scratch, int* singular, cudaStream_t s);
+// direct level-0 assembly from the FP32 descriptor, state and dP/dU (radiation
+// only); without it the level-0 stencil is probed through J
+struct MgDirect {
+    const Dev<float>* g;
+    const float* U;
+    const float* pj;
+};
+void mg_build(MgHierarchy& H, const MgJvOp& J, const MgDirect* direct, double* inv64_scratch, int* singular,
+              cudaStream_t s);
 void mg_cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float* zout, cudaStream_t s);
-int mg_launches_per_build(const MgHierarchy& H);
+int mg_launches_per_build(const MgHierarchy& H, bool direct);
 int mg_launches_per_cycle(const MgHierarchy& H);
 // partial-sum entries the residual may need for this grid
 long long residual_partial_count(int dim, const int n[3]);

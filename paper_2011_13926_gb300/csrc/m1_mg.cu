@@ -4,17 +4,18 @@
 // among its preconditioners (Sect. 3.3.2, Sect. 4):
 //   level 0: the Jacobian itself, applied matrix-free by the linear J v, its
 //     point-block inverses (the block-Jacobi ones) as smoother; its 5-point
-//     stencil of n_u x n_u blocks (C, W, E, S, N = self, -x, +x, -y, +y) is read
-//     off J v by coloured probes (a vector that is 1 on one unknown of every
-//     cell of one colour class; cells of a class are >= 3 apart, also across a
-//     periodic wrap, so each response entry belongs to one probed cell), only to
-//     build the coarse levels;
+//     stencil of n_u x n_u blocks (C, W, E, S, N = self, -x, +x, -y, +y), only
+//     needed to build the coarse levels, is assembled directly from the
+//     pressure Jacobian (radiation only, k_mg_assemble2d) or read off J v by
+//     coloured probes (a vector that is 1 on one unknown of every cell of one
+//     colour class; cells of a class are >= 3 apart, also across a periodic
+//     wrap, so each response entry belongs to one probed cell);
 //   levels >= 1: 2 x 2 cell aggregates, piecewise-constant prolongation P,
 //     restriction P^T (the sum over the aggregate) and the Galerkin stencil
 //     P^T A P — again a 5-point block stencil (a fine coupling inside the
 //     aggregate adds to C, one leaving it adds to the block of its direction);
 //   the cycle: V(1,1) with damped point-block Jacobi (omega = 0.7) from zero,
-//     10 damped sweeps from zero on the coarsest level (both sides <= 32 cells,
+//     10 damped sweeps from zero on the coarsest level (both sides <= 16 cells,
 //     one CTA, the iterate in shared memory).
 // Blocks are stored A[((s n_u + r) n_u + c) N + i]; the block inverses of the
 // C blocks [(r n_u + c) N + i] like the block-Jacobi ones.
@@ -25,7 +26,7 @@
 namespace m1 {
 
 constexpr float kMgOmega = 0.7f;
-constexpr int kMgCoarsest = 32;
+constexpr int kMgCoarsest = 16;
 constexpr int kMgCoarseSweeps = 10;
 constexpr int kMgThreads = 256;
 
@@ -72,6 +73,171 @@ __global__ void k_mg_extract(int nx, int ny, bool px, bool py, int mx, int my, i
             if ((jx % mx) + mx * (jy % my) != colour) continue;
 #pragma unroll
             for (int r = 0; r < NU; ++r) A[((long long)(s * NU + r) * NU + comp) * N + i] = y[r * N + i];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ level-0 stencil, direct
+// The linear J v of cell i (2D, radiation only, frozen or fixed wave speeds) is
+// a linear function of the staged derivative quantities (E, Fx, Fy, Pxx, Pxy,
+// Pyy) at five positions: the cell (0) and its faces' neighbours W, E, S, N
+// (1..4). mg_lin_out evaluates it with the formulas of the linear tiled J v.
+struct MgFace {
+    float lp, lm, al, sn;  // wave speeds, alpha, the neighbour's flux opacity
+    bool boundary;         // a non-periodic boundary face (the neighbour is a ghost)
+};
+
+__device__ __forceinline__ void mg_lin_out(const Dev<float>& g, const float (*st)[6], const MgFace* fc,
+                                           float sig_self, float sig_a, float* out) {
+    const float dt = g.dt, c = g.c, c2 = g.c * g.c;
+    float RE = st[0][0], RFx = st[0][1], RFy = st[0][2];
+    float phi[2] = {0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int p = 1 + 2 * a + side;
+            const float* me = st[0];
+            const float* nb = st[p];
+            const float* L = side ? me : nb;
+            const float* Rr = side ? nb : me;
+            const MgFace& f = fc[p - 1];
+            const float den = f.lp - f.lm;
+            const float inv = den >= Tiny<float>::den() ? 1.f / den : 0.f;
+            const float pm = f.lp * f.lm * inv;
+            const float FaL = a == 0 ? L[1] : L[2], FaR = a == 0 ? Rr[1] : Rr[2];
+            const float Fs = (f.lp * FaL - f.lm * FaR) * inv + pm * (Rr[0] - L[0]);
+            const float PaxL = a == 0 ? L[3] : L[4], PaxR = a == 0 ? Rr[3] : Rr[4];
+            const float PayL = a == 0 ? L[4] : L[5], PayR = a == 0 ? Rr[4] : Rr[5];
+            const float Psx = c2 * (f.lp * PaxL - f.lm * PaxR) * inv + pm * (Rr[1] - L[1]);
+            const float Psy = c2 * (f.lp * PayL - f.lm * PayR) * inv + pm * (Rr[2] - L[2]);
+            const float w = (side ? dt : -dt) * g.inv_dx[a];
+            RE = RE + (w * f.al) * Fs;
+            RFx = RFx + w * Psx;
+            RFy = RFy + w * Psy;
+            if (g.wb) {
+                if (f.boundary && g.wb_boundary) {
+                    const float PR = a == 0 ? Rr[3] : Rr[5], PL = a == 0 ? L[3] : L[5];
+                    phi[a] = phi[a] - c * g.inv_dx[a] * (PR - PL);
+                } else {
+                    phi[a] = phi[a] + (0.25f * (sig_self + f.sn)) * (FaL + FaR);
+                }
+            }
+        }
+    }
+    const float cdt = c * dt;
+    if (g.wb) {
+        RFx = RFx + cdt * (0.5f * phi[0]);
+        RFy = RFy + cdt * (0.5f * phi[1]);
+    } else {
+        RFx = RFx + cdt * (sig_self * st[0][1]);
+        RFy = RFy + cdt * (sig_self * st[0][2]);
+    }
+    const float exch = (cdt * sig_a) * (0.f - st[0][0]);
+    out[0] = RE - exch;
+    out[1] = RFx;
+    out[2] = RFy;
+}
+
+// A0 blocks of every cell: column c of block s is mg_lin_out with a unit
+// derivative of unknown c at that position's cell (its pressure derivative the
+// column of dP/dU there); a boundary ghost depends on the cell itself (dual
+// numbers through the boundary rule), so it enters the C block.
+__global__ void k_mg_assemble2d(Dev<float> g, const float* __restrict__ U, const float* __restrict__ pj,
+                                float* __restrict__ A) {
+    const int nx = g.n[0];
+    const long long N = g.N;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nx), iy = (int)(i / nx);
+        const int coord[3] = {ix, iy, 0};
+        const float sig_self = g.sig_f[i], sig_a = g.sig_a[i];
+        MgFace fc[4];
+        long long nbi[4];
+        bool any_boundary = false;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                MgFace& f = fc[2 * a + side];
+                const int ca = coord[a] + (side ? 1 : -1);
+                const bool inside = ca >= 0 && ca < g.n[a];
+                const bool periodic = g.bc[a][side] == BC_PERIODIC;
+                f.boundary = !inside && !periodic;
+                any_boundary |= f.boundary;
+                long long j = -1;
+                if (inside)
+                    j = i + (side ? g.stride[a] : -g.stride[a]);
+                else if (periodic)
+                    j = i + (side ? -(long long)(g.n[a] - 1) : (long long)(g.n[a] - 1)) * g.stride[a];
+                nbi[2 * a + side] = j;
+                f.sn = j >= 0 ? g.sig_f[j] : sig_self;
+                const long long fidx = face_index(g.n, coord, a, coord[a] + side);
+                if (g.fixed_eigs) {
+                    f.lp = g.c;
+                    f.lm = -g.c;
+                } else {
+                    f.lp = g.lam_p[a][fidx];
+                    f.lm = g.lam_m[a][fidx];
+                }
+                f.al = g.alpha[a][fidx];
+            }
+        }
+        // ghost derivatives: gd[face][seed c][quantity]
+        float gd[4][3][6];
+        if (any_boundary) {
+            const LoadSeed<float> ld{U, N, -1};  // in-domain loads (not taken on a boundary face): no seed
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                if (!fc[p].boundary) continue;
+                const int a = p / 2, side = p % 2;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    St<Dual<float>, 2> self;
+                    self.E = Dual<float>{U[i], c == 0 ? 1.f : 0.f};
+                    self.F[0] = Dual<float>{U[N + i], c == 1 ? 1.f : 0.f};
+                    self.F[1] = Dual<float>{U[2 * N + i], c == 2 ? 1.f : 0.f};
+                    float sn;
+                    bool bnd;
+                    const St<Dual<float>, 2> gh = neighbour<Dual<float>, 2, false>(g, ld, self, i, coord, a, side, sn, bnd);
+                    const Cl<Dual<float>, 2> k = closure(gh, g.c);
+                    gd[p][c][0] = gh.E.d;
+                    gd[p][c][1] = gh.F[0].d;
+                    gd[p][c][2] = gh.F[1].d;
+                    gd[p][c][3] = pressure(k, 0, 0).d;
+                    gd[p][c][4] = pressure(k, 0, 1).d;
+                    gd[p][c][5] = pressure(k, 1, 1).d;
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const long long X = s == 0 ? i : nbi[s - 1];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float out[3] = {0.f, 0.f, 0.f};
+                if (X >= 0) {
+                    float st[5][6];
+#pragma unroll
+                    for (int p = 0; p < 5; ++p)
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) st[p][k] = 0.f;
+                    st[s][0] = c == 0 ? 1.f : 0.f;
+                    st[s][1] = c == 1 ? 1.f : 0.f;
+                    st[s][2] = c == 2 ? 1.f : 0.f;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) st[s][3 + r] = pj[(long long)(3 * r + c) * N + X];
+                    if (s == 0) {
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)
+                            if (fc[p].boundary)
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) st[1 + p][k] = gd[p][c][k];
+                    }
+                    mg_lin_out(g, st, fc, sig_self, sig_a, out);
+                }
+#pragma unroll
+                for (int r = 0; r < 3; ++r) A[((long long)(s * 3 + r) * 3 + c) * N + i] = out[r];
+            }
         }
     }
 }
@@ -141,122 +307,188 @@ __global__ void k_mg_jacobi0(long long N, const float* __restrict__ Dinv, const 
     }
 }
 
-// (A z)_i on an assembled level, z optionally plus the prolonged coarse zc
+// coarsest level: sweeps of z <- z + omega D^-1 (r - A z) from zero, one CTA
+// with one thread per cell (N <= kMgCoarsest^2): each thread keeps its stencil
+// row, block inverse and residual in registers, the iterate is double-buffered
+// in shared memory
 template <int NU>
-__device__ __forceinline__ void mg_apply_cell(const float* __restrict__ A, const float* __restrict__ z,
-                                              const float* __restrict__ zc, int nx, int ny, bool px, bool py,
-                                              int nxc, int ix, int iy, long long N, long long Nc, float* out) {
-    const long long i = (long long)iy * nx + ix;
-#pragma unroll
-    for (int r = 0; r < NU; ++r) out[r] = 0.f;
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const long long j = mg_nb(ix, iy, s, nx, ny, px, py);
-        if (j < 0) continue;
-        float zj[NU];
-        const long long J = zc ? (long long)((j / nx) / 2) * nxc + (j % nx) / 2 : 0;
-#pragma unroll
-        for (int c = 0; c < NU; ++c) zj[c] = z[c * N + j] + (zc ? zc[c * Nc + J] : 0.f);
-#pragma unroll
-        for (int r = 0; r < NU; ++r)
-#pragma unroll
-            for (int c = 0; c < NU; ++c) out[r] += A[((long long)(s * NU + r) * NU + c) * N + i] * zj[c];
-    }
-}
-
-// rc = P^T (r - A z) on an assembled level (one thread per coarse cell)
-template <int NU>
-__global__ void k_mg_resid_restrict(int nx, int ny, bool px, bool py, const float* __restrict__ A,
-                                    const float* __restrict__ r, const float* __restrict__ z, int nxc, int nyc,
-                                    float* __restrict__ rc) {
-    const long long N = (long long)nx * ny, Nc = (long long)nxc * nyc;
-    for (long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x; I < Nc; I += (long long)gridDim.x * blockDim.x) {
-        const int Ix = (int)(I % nxc), Iy = (int)(I / nxc);
-        float acc[NU];
-#pragma unroll
-        for (int c = 0; c < NU; ++c) acc[c] = 0.f;
-        for (int dy = 0; dy < 2; ++dy)
-            for (int dx = 0; dx < 2; ++dx) {
-                const int ix = 2 * Ix + dx, iy = 2 * Iy + dy;
-                if (ix >= nx || iy >= ny) continue;
-                const long long i = (long long)iy * nx + ix;
-                float az[NU];
-                mg_apply_cell<NU>(A, z, nullptr, nx, ny, px, py, nxc, ix, iy, N, Nc, az);
-#pragma unroll
-                for (int c = 0; c < NU; ++c) acc[c] += r[c * N + i] - az[c];
-            }
-#pragma unroll
-        for (int c = 0; c < NU; ++c) rc[c * Nc + I] = acc[c];
-    }
-}
-
-// zout = zz + omega D^-1 (r - A zz), zz = z + P zc, on an assembled level
-template <int NU>
-__global__ void k_mg_prolong_post(int nx, int ny, bool px, bool py, const float* __restrict__ A,
-                                  const float* __restrict__ Dinv, const float* __restrict__ r,
-                                  const float* __restrict__ z, const float* __restrict__ zc, int nxc, int nyc,
-                                  float* __restrict__ zout) {
-    const long long N = (long long)nx * ny, Nc = (long long)nxc * nyc;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int ix = (int)(i % nx), iy = (int)(i / nx);
-        float az[NU], res[NU];
-        mg_apply_cell<NU>(A, z, zc, nx, ny, px, py, nxc, ix, iy, N, Nc, az);
-        const long long I = (long long)(iy / 2) * nxc + ix / 2;
-#pragma unroll
-        for (int c = 0; c < NU; ++c) res[c] = r[c * N + i] - az[c];
-#pragma unroll
-        for (int q = 0; q < NU; ++q) {
-            float a = 0.f;
-#pragma unroll
-            for (int c = 0; c < NU; ++c) a += Dinv[(long long)(q * NU + c) * N + i] * res[c];
-            zout[q * N + i] = z[q * N + i] + zc[q * Nc + I] + kMgOmega * a;
-        }
-    }
-}
-
-// coarsest level: sweeps of z <- z + omega D^-1 (r - A z) from zero, one CTA,
-// the iterate double-buffered in shared memory (N <= kMgCoarsest^2)
-template <int NU>
-__global__ void __launch_bounds__(1024) k_mg_coarsest(int nx, int ny, bool px, bool py, const float* __restrict__ A,
-                                                      const float* __restrict__ Dinv, const float* __restrict__ r,
-                                                      float* __restrict__ zout, int sweeps) {
+__global__ void __launch_bounds__(kMgCoarsest* kMgCoarsest) k_mg_coarsest(int nx, int ny, bool px, bool py,
+                                                                          const float* __restrict__ A,
+                                                                          const float* __restrict__ Dinv,
+                                                                          const float* __restrict__ r,
+                                                                          float* __restrict__ zout, int sweeps) {
     __shared__ float zs[2][NU][kMgCoarsest * kMgCoarsest];
     const int N = nx * ny;
-    for (int i = threadIdx.x; i < N; i += blockDim.x)
+    const int i = threadIdx.x;
+    const bool own = i < N;
+    float a[5][NU][NU], d[NU][NU], ri[NU];
+    long long nb[5];
+    if (own) {
+        const int ix = i % nx, iy = i / nx;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            nb[s] = mg_nb(ix, iy, s, nx, ny, px, py);
+#pragma unroll
+            for (int q = 0; q < NU; ++q)
+#pragma unroll
+                for (int c = 0; c < NU; ++c) a[s][q][c] = A[((long long)(s * NU + q) * NU + c) * N + i];
+        }
+#pragma unroll
+        for (int q = 0; q < NU; ++q) {
+            ri[q] = r[q * N + i];
+#pragma unroll
+            for (int c = 0; c < NU; ++c) d[q][c] = Dinv[(long long)(q * NU + c) * N + i];
+        }
 #pragma unroll
         for (int c = 0; c < NU; ++c) zs[0][c][i] = 0.f;
+    }
     __syncthreads();
     int cur = 0;
     for (int k = 0; k < sweeps; ++k) {
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            const int ix = i % nx, iy = i / nx;
+        if (own) {
             float res[NU];
 #pragma unroll
-            for (int q = 0; q < NU; ++q) res[q] = r[q * N + i];
+            for (int q = 0; q < NU; ++q) res[q] = ri[q];
 #pragma unroll
             for (int s = 0; s < 5; ++s) {
-                const long long j = mg_nb(ix, iy, s, nx, ny, px, py);
-                if (j < 0) continue;
+                if (nb[s] < 0) continue;
 #pragma unroll
                 for (int q = 0; q < NU; ++q)
 #pragma unroll
-                    for (int c = 0; c < NU; ++c)
-                        res[q] -= A[((long long)(s * NU + q) * NU + c) * N + i] * zs[cur][c][j];
+                    for (int c = 0; c < NU; ++c) res[q] -= a[s][q][c] * zs[cur][c][nb[s]];
             }
 #pragma unroll
             for (int q = 0; q < NU; ++q) {
-                float a = 0.f;
+                float t = 0.f;
 #pragma unroll
-                for (int c = 0; c < NU; ++c) a += Dinv[(long long)(q * NU + c) * N + i] * res[c];
-                zs[cur ^ 1][q][i] = zs[cur][q][i] + kMgOmega * a;
+                for (int c = 0; c < NU; ++c) t += d[q][c] * res[c];
+                zs[cur ^ 1][q][i] = zs[cur][q][i] + kMgOmega * t;
             }
         }
         __syncthreads();
         cur ^= 1;
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x)
+    if (own)
 #pragma unroll
         for (int c = 0; c < NU; ++c) zout[c * N + i] = zs[cur][c][i];
+}
+
+// ------------------------------------------------------------------ tiled assembled levels
+// A 32 x 8 tile of cells plus its axis halo (a periodic side wraps, a cell
+// beyond a non-periodic side holds 0: its couplings are zero) in shared memory.
+constexpr int kMgTX = 32, kMgTY = 8;
+
+// halo index (hx, hy) of a tile at (x0, y0) -> cell, or -1
+__device__ __forceinline__ long long mg_halo_cell(int x0, int y0, int hx, int hy, int nx, int ny, bool px, bool py) {
+    int gx = x0 + hx - 1, gy = y0 + hy - 1;
+    if (px) gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+    if (py) gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+    if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) return -1;
+    return (long long)gy * nx + gx;
+}
+
+// down: z = omega D^-1 r (written), rc = P^T (r - A z) — pre-smoothing,
+// residual and restriction of one assembled level in one pass
+template <int NU>
+__global__ void __launch_bounds__(kMgTX* kMgTY) k_mg_down(int nx, int ny, bool px, bool py,
+                                                        const float* __restrict__ A, const float* __restrict__ Dinv,
+                                                        const float* __restrict__ r, float* __restrict__ z,
+                                                        int nxc, int nyc, float* __restrict__ rc) {
+    __shared__ float zt[kMgTY + 2][kMgTX + 2][NU];
+    __shared__ float rs[kMgTY][kMgTX][NU];
+    const long long N = (long long)nx * ny, Nc = (long long)nxc * nyc;
+    const int x0 = blockIdx.x * kMgTX, y0 = blockIdx.y * kMgTY;
+    const int tid = threadIdx.y * kMgTX + threadIdx.x;
+    for (int t = tid; t < (kMgTX + 2) * (kMgTY + 2); t += kMgTX * kMgTY) {
+        const int hx = t % (kMgTX + 2), hy = t / (kMgTX + 2);
+        if ((hx == 0 || hx == kMgTX + 1) && (hy == 0 || hy == kMgTY + 1)) continue;  // corners
+        const long long j = mg_halo_cell(x0, y0, hx, hy, nx, ny, px, py);
+        float rj[NU];
+#pragma unroll
+        for (int c = 0; c < NU; ++c) rj[c] = j >= 0 ? r[c * N + j] : 0.f;
+#pragma unroll
+        for (int q = 0; q < NU; ++q) {
+            float a = 0.f;
+            if (j >= 0)
+#pragma unroll
+                for (int c = 0; c < NU; ++c) a += Dinv[(long long)(q * NU + c) * N + j] * rj[c];
+            zt[hy][hx][q] = kMgOmega * a;
+        }
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ix = x0 + tx, iy = y0 + ty;
+    float res[NU];
+#pragma unroll
+    for (int c = 0; c < NU; ++c) res[c] = 0.f;
+    if (ix < nx && iy < ny) {
+        const long long i = (long long)iy * nx + ix;
+#pragma unroll
+        for (int c = 0; c < NU; ++c) {
+            z[c * N + i] = zt[ty + 1][tx + 1][c];
+            res[c] = r[c * N + i];
+        }
+        const int hx[5] = {tx + 1, tx, tx + 2, tx + 1, tx + 1}, hy[5] = {ty + 1, ty + 1, ty + 1, ty, ty + 2};
+#pragma unroll
+        for (int s = 0; s < 5; ++s)
+#pragma unroll
+            for (int q = 0; q < NU; ++q)
+#pragma unroll
+                for (int c = 0; c < NU; ++c)
+                    res[q] -= A[((long long)(s * NU + q) * NU + c) * N + i] * zt[hy[s]][hx[s]][c];
+    }
+#pragma unroll
+    for (int c = 0; c < NU; ++c) rs[ty][tx][c] = res[c];
+    __syncthreads();
+    if ((tx & 1) == 0 && (ty & 1) == 0 && ix < nx && iy < ny) {
+        const long long I = (long long)(iy / 2) * nxc + ix / 2;
+#pragma unroll
+        for (int c = 0; c < NU; ++c)
+            rc[c * Nc + I] = (rs[ty][tx][c] + rs[ty][tx + 1][c]) + (rs[ty + 1][tx][c] + rs[ty + 1][tx + 1][c]);
+    }
+}
+
+// up: zz = z + P zc, zout = zz + omega D^-1 (r - A zz) on one assembled level
+template <int NU>
+__global__ void __launch_bounds__(kMgTX* kMgTY) k_mg_up(int nx, int ny, bool px, bool py,
+                                                      const float* __restrict__ A, const float* __restrict__ Dinv,
+                                                      const float* __restrict__ r, const float* __restrict__ z,
+                                                      const float* __restrict__ zc, int nxc, int nyc,
+                                                      float* __restrict__ zout) {
+    __shared__ float zt[kMgTY + 2][kMgTX + 2][NU];
+    const long long N = (long long)nx * ny, Nc = (long long)nxc * nyc;
+    const int x0 = blockIdx.x * kMgTX, y0 = blockIdx.y * kMgTY;
+    const int tid = threadIdx.y * kMgTX + threadIdx.x;
+    for (int t = tid; t < (kMgTX + 2) * (kMgTY + 2); t += kMgTX * kMgTY) {
+        const int hx = t % (kMgTX + 2), hy = t / (kMgTX + 2);
+        if ((hx == 0 || hx == kMgTX + 1) && (hy == 0 || hy == kMgTY + 1)) continue;  // corners
+        const long long j = mg_halo_cell(x0, y0, hx, hy, nx, ny, px, py);
+        const long long J = j >= 0 ? (long long)((j / nx) / 2) * nxc + (j % nx) / 2 : 0;
+#pragma unroll
+        for (int c = 0; c < NU; ++c) zt[hy][hx][c] = j >= 0 ? z[c * N + j] + zc[c * Nc + J] : 0.f;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ix = x0 + tx, iy = y0 + ty;
+    if (ix >= nx || iy >= ny) return;
+    const long long i = (long long)iy * nx + ix;
+    float res[NU];
+#pragma unroll
+    for (int c = 0; c < NU; ++c) res[c] = r[c * N + i];
+    const int hx[5] = {tx + 1, tx, tx + 2, tx + 1, tx + 1}, hy[5] = {ty + 1, ty + 1, ty + 1, ty, ty + 2};
+#pragma unroll
+    for (int s = 0; s < 5; ++s)
+#pragma unroll
+        for (int q = 0; q < NU; ++q)
+#pragma unroll
+            for (int c = 0; c < NU; ++c) res[q] -= A[((long long)(s * NU + q) * NU + c) * N + i] * zt[hy[s]][hx[s]][c];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) {
+        float a = 0.f;
+#pragma unroll
+        for (int c = 0; c < NU; ++c) a += Dinv[(long long)(q * NU + c) * N + i] * res[c];
+        zout[q * N + i] = zt[ty + 1][tx + 1][q] + kMgOmega * a;
+    }
 }
 
 // level 0: rc = P^T (r - w) with w = J z computed by the linear J v
@@ -346,6 +578,8 @@ static void assemble_level0(MgHierarchy& H, const MgJvOp& J, cudaStream_t s) {
 
 template <int NU>
 static void build_coarse(MgHierarchy& H, double* inv64_scratch, int* singular, cudaStream_t s) {
+    // level 0's smoother: the inverses of A0's C blocks (the point-block Jacobi ones)
+    launch_block_inverse_f32(NU, (long long)H.nx[0] * H.ny[0], H.A[0], inv64_scratch, H.Dinv[0], singular, s);
     for (int l = 1; l < H.nlev; ++l) {
         const long long Nc = (long long)H.nx[l] * H.ny[l];
         k_mg_galerkin<NU><<<grid_for(Nc), kMgThreads, 0, s>>>(H.nx[l - 1], H.ny[l - 1], H.px, H.py, H.A[l - 1],
@@ -354,14 +588,21 @@ static void build_coarse(MgHierarchy& H, double* inv64_scratch, int* singular, c
     }
 }
 
-int mg_launches_per_build(const MgHierarchy& H) {
+int mg_launches_per_build(const MgHierarchy& H, bool direct) {
     const int mx = mg_colour_period(H.nx[0], H.px), my = mg_colour_period(H.ny[0], H.py);
-    return 1 + 2 * mx * my * H.nu + 2 * (H.nlev - 1);  // memset aside: probes + extracts, Galerkin + inverse
+    // direct assembly or probes + extracts (their J v counted by the caller's operator), Galerkin + inverse
+    return (direct ? 1 : 2 * mx * my * H.nu) + 1 + 2 * (H.nlev - 1);
 }
 
-void mg_build(MgHierarchy& H, const MgJvOp& J, double* inv64_scratch, int* singular, cudaStream_t s) {
+void mg_build(MgHierarchy& H, const MgJvOp& J, const MgDirect* direct, double* inv64_scratch, int* singular,
+              cudaStream_t s) {
     if (H.nu == 3) {
-        assemble_level0<3>(H, J, s);
+        if (direct) {
+            const long long N = (long long)H.nx[0] * H.ny[0];
+            k_mg_assemble2d<<<grid_for(N), kMgThreads, 0, s>>>(*direct->g, direct->U, direct->pj, H.A[0]);
+        } else {
+            assemble_level0<3>(H, J, s);
+        }
         build_coarse<3>(H, inv64_scratch, singular, s);
     } else {
         assemble_level0<4>(H, J, s);
@@ -395,20 +636,18 @@ static void cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float*
     k_mg_restrict_diff<NU><<<grid_for(N1), kMgThreads, 0, s>>>(nx0, ny0, r0, H.w0, H.nx[1], H.ny[1], H.r[1]);
     // down the assembled levels
     for (int l = 1; l < H.nlev - 1; ++l) {
-        const long long N = (long long)H.nx[l] * H.ny[l], Nc = (long long)H.nx[l + 1] * H.ny[l + 1];
-        k_mg_jacobi0<NU><<<grid_for(N), kMgThreads, 0, s>>>(N, H.Dinv[l], H.r[l], H.z[l]);
-        k_mg_resid_restrict<NU><<<grid_for(Nc), kMgThreads, 0, s>>>(H.nx[l], H.ny[l], H.px, H.py, H.A[l], H.r[l],
-                                                                     H.z[l], H.nx[l + 1], H.ny[l + 1], H.r[l + 1]);
+        const dim3 grid((H.nx[l] + kMgTX - 1) / kMgTX, (H.ny[l] + kMgTY - 1) / kMgTY), block(kMgTX, kMgTY);
+        k_mg_down<NU><<<grid, block, 0, s>>>(H.nx[l], H.ny[l], H.px, H.py, H.A[l], H.Dinv[l], H.r[l], H.z[l],
+                                              H.nx[l + 1], H.ny[l + 1], H.r[l + 1]);
     }
     const int L = H.nlev - 1;
-    k_mg_coarsest<NU><<<1, 1024, 0, s>>>(H.nx[L], H.ny[L], H.px, H.py, H.A[L], H.Dinv[L], H.r[L], H.z2[L],
-                                         kMgCoarseSweeps);
+    k_mg_coarsest<NU><<<1, kMgCoarsest * kMgCoarsest, 0, s>>>(H.nx[L], H.ny[L], H.px, H.py, H.A[L], H.Dinv[L],
+                                                               H.r[L], H.z2[L], kMgCoarseSweeps);
     // up
     for (int l = L - 1; l >= 1; --l) {
-        const long long N = (long long)H.nx[l] * H.ny[l];
-        k_mg_prolong_post<NU><<<grid_for(N), kMgThreads, 0, s>>>(H.nx[l], H.ny[l], H.px, H.py, H.A[l], H.Dinv[l],
-                                                                  H.r[l], H.z[l], H.z2[l + 1], H.nx[l + 1],
-                                                                  H.ny[l + 1], H.z2[l]);
+        const dim3 grid((H.nx[l] + kMgTX - 1) / kMgTX, (H.ny[l] + kMgTY - 1) / kMgTY), block(kMgTX, kMgTY);
+        k_mg_up<NU><<<grid, block, 0, s>>>(H.nx[l], H.ny[l], H.px, H.py, H.A[l], H.Dinv[l], H.r[l], H.z[l],
+                                            H.z2[l + 1], H.nx[l + 1], H.ny[l + 1], H.z2[l]);
     }
     // level 0: prolong, J v, post-smoothing
     k_mg_prolong_add<NU><<<grid_for(N0), kMgThreads, 0, s>>>(nx0, ny0, H.z2[1], H.nx[1], H.ny[1], H.z[0]);
@@ -418,7 +657,7 @@ static void cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float*
 
 int mg_launches_per_cycle(const MgHierarchy& H) {
     if (H.nlev == 1) return 1 + 2 * (kMgCoarseSweeps - 1);
-    return 6 + 2 * (H.nlev - 2) + 1 + (H.nlev - 2);
+    return 6 + (H.nlev - 2) + 1 + (H.nlev - 2);
 }
 
 void mg_cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float* zout, cudaStream_t s) {

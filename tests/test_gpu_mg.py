@@ -1,6 +1,6 @@
 """GPU parity of the multigrid preconditioner (M1_PRECOND_MG) against oracle/mg.py.
 
-Tolerances: stencil blocks come from FP32 J v probes, so each block row is
+Tolerances: stencil blocks are FP32 (assembled, or read off FP32 J v probes), so each block row is
 compared to 2e-5 of its largest entry; one V-cycle runs in FP32 through
 ~30 damped sweeps of the level operators, compared to 2e-4 in the 2-norm.
 The implicit step with the multigrid preconditioner meets the FP64 implicit
@@ -13,7 +13,7 @@ import pytest
 import seeded_inputs as si
 from oracle import Scheme, newton_solve
 from oracle import mg as omg
-from tests.m1_cases import gas_3d, perturbed_state
+from tests.m1_cases import gas_2d, gas_3d, perturbed_state
 
 pytestmark = pytest.mark.gpu
 
@@ -79,6 +79,21 @@ def test_cycle_matches_oracle(m1mod, shape):
         assert np.linalg.norm(got - ref) <= 2e-4 * np.linalg.norm(ref)
 
 
+def test_cycle_with_gas_coupling_matches_oracle(m1mod):
+    # n_u = 4: the level-0 stencil is probed through J v
+    p = gas_2d()
+    s = Scheme(p)
+    u = perturbed_state(p, 27)
+    px, py = _periodic(p)
+    ctx = _ctx(m1mod, p)
+    H = omg.Hierarchy(lambda v: s.jv(u, v), s.nu, p.n[0], p.n[1], px, py)
+    r = np.random.default_rng(28).standard_normal(u.size)
+    got = ctx.mg_apply(p.dt, r, U=u)
+    for lvl, (A, (lx, ly)) in enumerate(zip(H.ops, H.sizes)):
+        assert _row_rel(ctx.mg_blocks(lvl, lx, ly), A) < 2e-5, lvl
+    assert np.linalg.norm(got - H.cycle(r)) <= 2e-4 * np.linalg.norm(H.cycle(r))
+
+
 def test_cycle_is_linear_on_gpu(m1mod):
     p = si.beam_lognormal_2d(80, 72, dt_factor=10.0)
     u = perturbed_state(p, 25)
@@ -115,7 +130,7 @@ def test_implicit_step_with_multigrid(m1mod):
 
 
 def test_multigrid_rejects_unsupported(m1mod):
-    p3 = gas_3d()
+    p3 = gas_3d()  # 3D
     ctx = _ctx(m1mod, p3)
     o = m1mod.default_opts(precision=m1mod.PREC_MIXED, precond=m1mod.PRECOND_MG, advance=0)
     st, info = ctx.implicit_step(p3.dt, o, raise_on_fail=False)
