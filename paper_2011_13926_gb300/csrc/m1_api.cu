@@ -378,14 +378,25 @@ m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g, const double* U, doub
 
 // dP/dU at U for the linear J v (2D, frozen or fixed wave speeds); false
 // when J v stays on dual numbers
-m1_status pressure_jacobian(m1_ctx* ctx, const Dev<double>& g, const double* U, bool fp32, bool* made) {
+// dP/dU for the linear J v (2D, frozen or fixed wave speeds), in FP64 at U or
+// in FP32 at U32 (the FP32 inner solver's own operator); false when J v stays
+// on dual numbers
+m1_status pressure_jacobian64(m1_ctx* ctx, const Dev<double>& g, const double* U, bool* made) {
     *made = false;
     if (!jv_linear_available(g)) return M1_OK;
-    const size_t planes = (size_t)pressure_jacobian_size(g);
-    CKS(dalloc(ctx, &ctx->pj64, planes * ctx->N));
-    if (fp32) CKS(dalloc(ctx, &ctx->pj32, planes * ctx->N));
+    CKS(dalloc(ctx, &ctx->pj64, (size_t)pressure_jacobian_size(g) * ctx->N));
     TK t(ctx, M1_K_PC_BUILD);
-    launch_pressure_jacobian(g, U, ctx->pj64, fp32 ? ctx->pj32 : nullptr, ctx->s);
+    launch_pressure_jacobian_f64(g, U, ctx->pj64, ctx->s);
+    count(ctx, 1);
+    *made = true;
+    return M1_OK;
+}
+m1_status pressure_jacobian32(m1_ctx* ctx, const Dev<double>& g, const Dev<float>& g32, const float* U32, bool* made) {
+    *made = false;
+    if (!jv_linear_available(g)) return M1_OK;
+    CKS(dalloc(ctx, &ctx->pj32, (size_t)pressure_jacobian_size(g) * ctx->N));
+    TK t(ctx, M1_K_PC_BUILD);
+    launch_pressure_jacobian_f32(g32, U32, ctx->pj32, ctx->s);
     count(ctx, 1);
     *made = true;
     return M1_OK;
@@ -1197,11 +1208,11 @@ m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double
     // the operator the solvers apply: a linear stencil of dP/dU at U where
     // available (2D, frozen or fixed wave speeds), else dual numbers
     bool lin = false;
-    CKS(pressure_jacobian(ctx, dev64(ctx, dt), ctx->U, precision == M1_PREC_MIXED, &lin));
     if (precision == M1_PREC_MIXED) {
         CKS(ensure_work32(ctx));
         launch_f64_to_f32(ctx->U, ctx->U32, ctx->n, ctx->s);
         launch_f64_to_f32(ctx->z, ctx->z32, ctx->n, ctx->s);
+        CKS(pressure_jacobian32(ctx, dev64(ctx, dt), dev32(ctx, dt), ctx->U32, &lin));
         if (lin)
             launch_jv_linear_f32(dev32(ctx, dt), ctx->U32, ctx->pj32, ctx->z32, ctx->w32, ctx->s);
         else
@@ -1209,6 +1220,7 @@ m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double
         launch_f32_to_f64(ctx->w32, ctx->w, ctx->n, ctx->s);
         count(ctx, 4);
     } else {
+        CKS(pressure_jacobian64(ctx, dev64(ctx, dt), ctx->U, &lin));
         if (lin)
             launch_jv_linear_f64(dev64(ctx, dt), ctx->U, ctx->pj64, ctx->z, ctx->w, ctx->s);
         else
@@ -1233,10 +1245,10 @@ m1_status m1_mg_apply(m1_ctx* ctx, double dt, const double* U, const double* r, 
     if (!mg_supported(ctx, g))
         return fail(ctx, M1_ERR_ARG,
                     "multigrid needs dim 2, frozen or fixed wave speeds and >= 3 cells along periodic axes");
-    bool lin = false;
-    CKS(pressure_jacobian(ctx, g, ctx->U, true, &lin));
     launch_f64_to_f32(ctx->U, ctx->U32, ctx->n, ctx->s);
     const Dev<float> g32 = dev32(ctx, dt);
+    bool lin = false;
+    CKS(pressure_jacobian32(ctx, g, g32, ctx->U32, &lin));
     CKS(build_mg(ctx, g32));
     CKS(copy_in(ctx, ctx->tmp, r, sizeof(double) * ctx->n, mem));
     launch_f64_to_f32(ctx->tmp, ctx->tmp32, ctx->n, ctx->s);
@@ -1293,14 +1305,15 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
                     "periodic axes");
     Ops64 ops{ctx, g, Ud, pre};
     bool lin = false;
-    CKS(pressure_jacobian(ctx, g, Ud, o->precision == M1_PREC_MIXED, &lin));
-    if (lin) ops.pj = ctx->pj64;
     *refinements = 0;
     if (o->precision == M1_PREC_MIXED) {
+        // the FP32 operator from dP/dU in FP32; the one FP64 J v per refinement
+        // sweep stays on dual numbers (cheaper than an FP64 dP/dU per Newton step)
         CKS(ensure_work32(ctx));
         launch_f64_to_f32(Ud, ctx->U32, ctx->n, ctx->s);
         count(ctx, 1);
         const Dev<float> g32 = dev32(ctx, dt);
+        CKS(pressure_jacobian32(ctx, g, g32, ctx->U32, &lin));
         if (pre && !use_mg) {  // FP32 point blocks, inverted in FP64 (multigrid takes them from its level 0)
             TK t(ctx, M1_K_PC_BUILD);
             launch_diag_f32(g32, ctx->U32, reinterpret_cast<float*>(ctx->blocks), ctx->s);
@@ -1318,6 +1331,8 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
         return gmres_mixed(ctx, ops, ops32, b, x, o->gmres_rtol, o->restart, o->gmres_max, o->refine_max, iters,
                            refinements, bnorm, res, conv);
     }
+    CKS(pressure_jacobian64(ctx, g, Ud, &lin));
+    if (lin) ops.pj = ctx->pj64;
     if (pre) CKS(build_precond(ctx, g, Ud));
     return gmres64(ctx, ops, b, x, o->gmres_rtol, o->restart, o->gmres_max, iters, bnorm, res, conv);
 }

@@ -20,12 +20,14 @@ void launch_faces_time_n(const Dev<double>& g, double* const lam_p[3], double* c
 int launch_residual_f64(const Dev<double>& g, const double* U, double* R, double* partials, long long capacity,
                         cudaStream_t s);
 // J v from the pressure Jacobian dP/dU frozen at the Newton iterate (2D,
-// frozen or fixed wave speeds): launch_pressure_jacobian fills dP/dU at U
-// (pressure_jacobian_size(g) planes of N, FP64 and optionally FP32), the
-// linear kernels apply it; U (in the kernel's precision) serves the ghosts
+// frozen or fixed wave speeds): launch_pressure_jacobian_f64/_f32 fill dP/dU
+// at U (pressure_jacobian_size(g) planes of N, in the precision of the J v
+// that applies it), the linear kernels apply it; U (in the kernel's precision)
+// serves the ghosts
 bool jv_linear_available(const Dev<double>& g);
 int pressure_jacobian_size(const Dev<double>& g);
-void launch_pressure_jacobian(const Dev<double>& g, const double* U, double* pj64, float* pj32, cudaStream_t s);
+void launch_pressure_jacobian_f64(const Dev<double>& g, const double* U, double* pj, cudaStream_t s);
+void launch_pressure_jacobian_f32(const Dev<float>& g, const float* U, float* pj, cudaStream_t s);
 void launch_jv_linear_f64(const Dev<double>& g, const double* U, const double* pj, const double* v, double* Jv,
                           cudaStream_t s);
 void launch_jv_linear_f32(const Dev<float>& g, const float* U, const float* pj, const float* v, float* Jv,

@@ -143,33 +143,29 @@ struct CellT {
 };
 
 // dP/dU of one cell in 2D: row r of (Pxx, Pxy, Pyy), column c of (E, Fx, Fy)
-// at pj[(3 r + c) N + idx]; with gas, d(a_r T^4)/dT at pj[9 N + idx]
-template <bool GAS>
-__global__ void __launch_bounds__(kThreads) k_pressure_jacobian2d(Dev<double> g, const double* __restrict__ U,
-                                                                   double* __restrict__ pj64, float* __restrict__ pj32) {
+// at pj[(3 r + c) N + idx]; with gas, d(a_r T^4)/dT at pj[9 N + idx]; in the
+// precision R of the J v that applies it
+template <class R, bool GAS>
+__global__ void __launch_bounds__(kThreads) k_pressure_jacobian2d(Dev<R> g, const R* __restrict__ U,
+                                                                   R* __restrict__ pj) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
     const long long N = g.N;
-    const double E = U[idx], Fx = U[N + idx], Fy = U[2 * N + idx];
+    const R E = U[idx], Fx = U[N + idx], Fy = U[2 * N + idx];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        St<Dual<double>, 2> u;
-        u.E = Dual<double>{E, c == 0 ? 1.0 : 0.0};
-        u.F[0] = Dual<double>{Fx, c == 1 ? 1.0 : 0.0};
-        u.F[1] = Dual<double>{Fy, c == 2 ? 1.0 : 0.0};
-        const Cl<Dual<double>, 2> k = closure(u, g.c);
-        const double d[3] = {pressure(k, 0, 0).d, pressure(k, 0, 1).d, pressure(k, 1, 1).d};
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            pj64[(3 * r + c) * N + idx] = d[r];
-            if (pj32) pj32[(3 * r + c) * N + idx] = (float)d[r];
-        }
+        St<Dual<R>, 2> u;
+        u.E = Dual<R>{E, c == 0 ? R(1) : R(0)};
+        u.F[0] = Dual<R>{Fx, c == 1 ? R(1) : R(0)};
+        u.F[1] = Dual<R>{Fy, c == 2 ? R(1) : R(0)};
+        const Cl<Dual<R>, 2> k = closure(u, g.c);
+        pj[(3 * 0 + c) * N + idx] = pressure(k, 0, 0).d;
+        pj[(3 * 1 + c) * N + idx] = pressure(k, 0, 1).d;
+        pj[(3 * 2 + c) * N + idx] = pressure(k, 1, 1).d;
     }
     if constexpr (GAS) {
-        const double T = U[3 * N + idx];
-        const double dB = 4.0 * g.a_r * T * T * T;
-        pj64[9 * N + idx] = dB;
-        if (pj32) pj32[9 * N + idx] = (float)dB;
+        const R T = U[3 * N + idx];
+        pj[9 * N + idx] = R(4) * g.a_r * T * T * T;
     }
 }
 
@@ -529,12 +525,19 @@ bool jv_linear_available(const Dev<double>& g) { return tiled2d(g); }
 
 int pressure_jacobian_size(const Dev<double>& g) { return 9 + (g.gas ? 1 : 0); }
 
-void launch_pressure_jacobian(const Dev<double>& g, const double* U, double* pj64, float* pj32, cudaStream_t s) {
+template <class R>
+static void pressure_jacobian_launch(const Dev<R>& g, const R* U, R* pj, cudaStream_t s) {
     const int nb = stencil_blocks(g.N);
     if (g.gas)
-        k_pressure_jacobian2d<true><<<nb, kThreads, 0, s>>>(g, U, pj64, pj32);
+        k_pressure_jacobian2d<R, true><<<nb, kThreads, 0, s>>>(g, U, pj);
     else
-        k_pressure_jacobian2d<false><<<nb, kThreads, 0, s>>>(g, U, pj64, pj32);
+        k_pressure_jacobian2d<R, false><<<nb, kThreads, 0, s>>>(g, U, pj);
+}
+void launch_pressure_jacobian_f64(const Dev<double>& g, const double* U, double* pj, cudaStream_t s) {
+    pressure_jacobian_launch<double>(g, U, pj, s);
+}
+void launch_pressure_jacobian_f32(const Dev<float>& g, const float* U, float* pj, cudaStream_t s) {
+    pressure_jacobian_launch<float>(g, U, pj, s);
 }
 
 template <class R>
