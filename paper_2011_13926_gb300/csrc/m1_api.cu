@@ -417,6 +417,20 @@ void mg_jv_apply(void* c, const float* in, float* out, cudaStream_t s) {
     m1_ctx* ctx = static_cast<m1_ctx*>(c);
     launch_jv_linear_f32(ctx->mg_g32, ctx->U32, ctx->pj32, in, out, s);
 }
+void mg_down0(void* c, const float* r, float omega, float* z, int nxc, int nyc, float* rc, cudaStream_t s) {
+    m1_ctx* ctx = static_cast<m1_ctx*>(c);
+    launch_mg_down0_f32(ctx->mg_g32, ctx->U32, ctx->pj32, ctx->binv32, r, omega, z, nxc, nyc, rc, s);
+}
+void mg_up0(void* c, const float* r, const float* z, const float* zc, int nxc, int nyc, float omega, float* zout,
+            cudaStream_t s) {
+    m1_ctx* ctx = static_cast<m1_ctx*>(c);
+    launch_mg_up0_f32(ctx->mg_g32, ctx->U32, ctx->pj32, ctx->binv32, r, z, zc, nxc, nyc, omega, zout, s);
+}
+// the level-0 operator of the cycle: fused passes for radiation only
+MgJvOp mg_op(m1_ctx* ctx) {
+    const bool fused = ctx->nu == 3;
+    return MgJvOp{ctx, mg_jv_apply, fused ? mg_down0 : nullptr, fused ? mg_up0 : nullptr};
+}
 
 m1_status ensure_mg(m1_ctx* ctx) {
     if (ctx->mg_alloc) return M1_OK;
@@ -448,7 +462,7 @@ m1_status build_mg(m1_ctx* ctx, const Dev<float>& g32) {
     ctx->mg_g32 = g32;
     ctx->mg.Dinv[0] = ctx->binv32;  // written by the build from the level-0 C blocks
     CK(cudaMemsetAsync(ctx->singular, 0, sizeof(int), ctx->s));
-    const MgJvOp op{ctx, mg_jv_apply};
+    const MgJvOp op = mg_op(ctx);
     const MgDirect direct{&ctx->mg_g32, ctx->U32, ctx->pj32};
     const bool use_direct = ctx->nu == 3 && !ctx->mg_probe;
     mg_build(ctx->mg, op, use_direct ? &direct : nullptr, ctx->mg_inv64, ctx->singular, ctx->s);
@@ -457,9 +471,9 @@ m1_status build_mg(m1_ctx* ctx, const Dev<float>& g32) {
 }
 
 void mg_apply(m1_ctx* ctx, const float* in, float* out) {
-    const MgJvOp op{ctx, mg_jv_apply};
+    const MgJvOp op = mg_op(ctx);
     mg_cycle(ctx->mg, op, in, out, ctx->s);
-    count(ctx, mg_launches_per_cycle(ctx->mg));
+    count(ctx, mg_launches_per_cycle(ctx->mg, op.down0 != nullptr));
 }
 
 m1_status build_precond(m1_ctx* ctx, const Dev<double>& g, const double* U) {

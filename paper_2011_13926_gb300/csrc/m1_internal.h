@@ -42,6 +42,10 @@ constexpr int kMgMaxLevels = 16;
 struct MgJvOp {
     void* ctx;
     void (*apply)(void* ctx, const float* in, float* out, cudaStream_t s);
+    // optional fused level-0 passes (with Dinv[0] as M^-1); null: J v plus separate kernels
+    void (*down0)(void* ctx, const float* r, float omega, float* z, int nxc, int nyc, float* rc, cudaStream_t s);
+    void (*up0)(void* ctx, const float* r, const float* z, const float* zc, int nxc, int nyc, float omega,
+                float* zout, cudaStream_t s);
 };
 // aggregation hierarchy of a 2D grid (FP32): level l is nx[l] x ny[l] cells; A[l]
 // the 5-point block stencil (5 n_u^2 planes; A[0] only feeds the coarsening),
@@ -72,7 +76,14 @@ void mg_build(MgHierarchy& H, const MgJvOp& J, const MgDirect* direct, double* i
               cudaStream_t s);
 void mg_cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float* zout, cudaStream_t s);
 int mg_launches_per_build(const MgHierarchy& H, bool direct);
-int mg_launches_per_cycle(const MgHierarchy& H);
+int mg_launches_per_cycle(const MgHierarchy& H, bool fused);
+// level 0 of the multigrid cycle in one tiled pass each (radiation only, FP32):
+// down: z = omega M^-1 r, rc = P^T (r - J z); up: zz = z + P zc,
+// zout = zz + omega M^-1 (r - J zz); M^-1 the block inverses binv
+void launch_mg_down0_f32(const Dev<float>& g, const float* U, const float* pj, const float* binv, const float* r,
+                         float omega, float* z, int nxc, int nyc, float* rc, cudaStream_t s);
+void launch_mg_up0_f32(const Dev<float>& g, const float* U, const float* pj, const float* binv, const float* r,
+                       const float* z, const float* zc, int nxc, int nyc, float omega, float* zout, cudaStream_t s);
 // partial-sum entries the residual may need for this grid
 long long residual_partial_count(int dim, const int n[3]);
 void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s);

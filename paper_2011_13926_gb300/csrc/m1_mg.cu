@@ -615,7 +615,8 @@ static void cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float*
     // level 0 pre-smoothing and restriction
     const int nx0 = H.nx[0], ny0 = H.ny[0];
     const long long N0 = (long long)nx0 * ny0;
-    k_mg_jacobi0<NU><<<grid_for(N0), kMgThreads, 0, s>>>(N0, H.Dinv[0], r0, H.z[0]);
+    const bool fused = J.down0 && J.up0 && H.nlev > 1;  // level 0 in two tiled passes
+    if (!fused) k_mg_jacobi0<NU><<<grid_for(N0), kMgThreads, 0, s>>>(N0, H.Dinv[0], r0, H.z[0]);
     if (H.nlev == 1) {
         // the fine grid is already the coarsest: the coarsest level's sweeps with J
         // itself, ping-ponging between z[0] and z2[0], the last one into zout
@@ -631,9 +632,13 @@ static void cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float*
         if (kMgCoarseSweeps == 1) cudaMemcpyAsync(zout, a, sizeof(float) * NU * N0, cudaMemcpyDeviceToDevice, s);
         return;
     }
-    J.apply(J.ctx, H.z[0], H.w0, s);
     const long long N1 = (long long)H.nx[1] * H.ny[1];
-    k_mg_restrict_diff<NU><<<grid_for(N1), kMgThreads, 0, s>>>(nx0, ny0, r0, H.w0, H.nx[1], H.ny[1], H.r[1]);
+    if (fused) {
+        J.down0(J.ctx, r0, kMgOmega, H.z[0], H.nx[1], H.ny[1], H.r[1], s);
+    } else {
+        J.apply(J.ctx, H.z[0], H.w0, s);
+        k_mg_restrict_diff<NU><<<grid_for(N1), kMgThreads, 0, s>>>(nx0, ny0, r0, H.w0, H.nx[1], H.ny[1], H.r[1]);
+    }
     // down the assembled levels
     for (int l = 1; l < H.nlev - 1; ++l) {
         const dim3 grid((H.nx[l] + kMgTX - 1) / kMgTX, (H.ny[l] + kMgTY - 1) / kMgTY), block(kMgTX, kMgTY);
@@ -650,14 +655,18 @@ static void cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float*
                                             H.z2[l + 1], H.nx[l + 1], H.ny[l + 1], H.z2[l]);
     }
     // level 0: prolong, J v, post-smoothing
+    if (fused) {
+        J.up0(J.ctx, r0, H.z[0], H.z2[1], H.nx[1], H.ny[1], kMgOmega, zout, s);
+        return;
+    }
     k_mg_prolong_add<NU><<<grid_for(N0), kMgThreads, 0, s>>>(nx0, ny0, H.z2[1], H.nx[1], H.ny[1], H.z[0]);
     J.apply(J.ctx, H.z[0], H.w0, s);
     k_mg_post0<NU><<<grid_for(N0), kMgThreads, 0, s>>>(N0, H.Dinv[0], r0, H.w0, H.z[0], zout);
 }
 
-int mg_launches_per_cycle(const MgHierarchy& H) {
+int mg_launches_per_cycle(const MgHierarchy& H, bool fused) {
     if (H.nlev == 1) return 1 + 2 * (kMgCoarseSweeps - 1);
-    return 6 + (H.nlev - 2) + 1 + (H.nlev - 2);
+    return (fused ? 2 : 6) + (H.nlev - 2) + 1 + (H.nlev - 2);
 }
 
 void mg_cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float* zout, cudaStream_t s) {

@@ -136,6 +136,35 @@ __global__ void __launch_bounds__(kThreads) k_jv(Dev<R> g, const R* __restrict__
 // the block's partial sum of squares.
 constexpr int kTX = 32, kTY = 8;
 constexpr int kTileResidual = 0, kTileJvDual = 1, kTileJvLinear = 2, kTileJvLinearPre = 3;
+// level 0 of the multigrid cycle (radiation only): down = pre-smoothing
+// z = omega M^-1 r (written), residual r - J z and its 2 x 2 restriction;
+// up = z + P zc, residual, post-smoothing into zout
+constexpr int kTileMgDown0 = 4, kTileMgUp0 = 5;
+
+template <class R>
+struct TileMg {
+    const R* r = nullptr;   // level-0 right-hand side
+    const R* z = nullptr;   // up: the pre-smoothed iterate
+    const R* zc = nullptr;  // up: the level-1 correction
+    int nxc = 0, nyc = 0;   // level-1 sizes
+    R* rc = nullptr;        // down: level-1 right-hand side
+    R* zout = nullptr;      // down: z; up: the smoothed iterate
+    R omega = R(0);
+};
+
+// Loader of U + eps (z + P zc) for the ghosts of the multigrid up pass
+template <class R>
+struct LoadProlong {
+    const R* U;
+    const R* z;
+    const R* zc;
+    long long N, Nc;
+    int nx, nxc;
+    __device__ __forceinline__ Dual<R> get(int comp, long long idx, long long) const {
+        const long long I = (long long)((idx / nx) / 2) * nxc + (idx % nx) / 2;
+        return {U[comp * N + idx], z[comp * N + idx] + zc[comp * Nc + I]};
+    }
+};
 
 template <class S>
 struct CellT {
@@ -190,11 +219,13 @@ __global__ void __launch_bounds__(kTX* kTY)
     k_stencil2d_tiled(Dev<typename RealOf<S>::type> g, const typename RealOf<S>::type* __restrict__ U,
                       const typename RealOf<S>::type* __restrict__ v, const typename RealOf<S>::type* __restrict__ pj,
                       const typename RealOf<S>::type* __restrict__ binv, typename RealOf<S>::type* __restrict__ out,
-                      double* __restrict__ partials) {
+                      double* __restrict__ partials, TileMg<typename RealOf<S>::type> mgp) {
     using R = typename RealOf<S>::type;
     constexpr bool RES = MODE == kTileResidual;
-    constexpr bool LIN = MODE == kTileJvLinear || MODE == kTileJvLinearPre;
-    constexpr bool PRE = MODE == kTileJvLinearPre;
+    constexpr bool MGD = MODE == kTileMgDown0, MGU = MODE == kTileMgUp0;
+    constexpr bool LIN = MODE == kTileJvLinear || MODE == kTileJvLinearPre || MGD || MGU;
+    constexpr bool PRE = MODE == kTileJvLinearPre || MGD;
+    static_assert(!(MGD || MGU) || !GAS, "the fused multigrid level 0 is radiation only");
     constexpr int NU = GAS ? 4 : 3;
     static_assert((MODE == kTileJvDual) == std::is_same<S, Dual<R>>::value, "dual numbers only for kTileJvDual");
     __shared__ CellT<S> cs[kTY + 2][kTX + 2];
@@ -250,7 +281,12 @@ __global__ void __launch_bounds__(kTX* kTY)
                 staged = true;
                 const long long k = (long long)gy * nx + gx;
                 R z[3];
-                if constexpr (PRE) {  // z = M^-1 v at this cell (rows E, Fx, Fy of the block inverse)
+                if constexpr (MGU) {  // z + P zc
+                    const long long Nc = (long long)mgp.nxc * mgp.nyc;
+                    const long long I = (long long)(gy / 2) * mgp.nxc + gx / 2;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) z[r] = mgp.z[r * N + k] + mgp.zc[r * Nc + I];
+                } else if constexpr (PRE) {  // z = M^-1 v at this cell (rows E, Fx, Fy of the block inverse)
                     R vv[NU];
 #pragma unroll
                     for (int q = 0; q < NU; ++q) vv[q] = v[q * N + k];
@@ -281,12 +317,16 @@ __global__ void __launch_bounds__(kTX* kTY)
             // residual: plain values; dual J v: dual numbers; linear J v: the
             // ghosts by dual numbers through the boundary rules
             using SD = std::conditional_t<RES, R, Dual<R>>;
-            using L = std::conditional_t<RES, LoadPlain<R>, std::conditional_t<PRE, LoadPre<R, NU>, LoadDir<R>>>;
+            using L = std::conditional_t<
+                RES, LoadPlain<R>,
+                std::conditional_t<PRE, LoadPre<R, NU>, std::conditional_t<MGU, LoadProlong<R>, LoadDir<R>>>>;
             L ld;
             if constexpr (RES) {
                 ld = L{U, N};
             } else if constexpr (PRE) {
                 ld = L{U, v, binv, N};
+            } else if constexpr (MGU) {
+                ld = L{U, mgp.z, mgp.zc, N, (long long)mgp.nxc * mgp.nyc, nx, mgp.nxc};
             } else {
                 ld = L{U, v, N};
             }
@@ -326,6 +366,7 @@ __global__ void __launch_bounds__(kTX* kTY)
     }
     __syncthreads();
     double ss = 0.0;
+    R mg_res[3] = {R(0), R(0), R(0)};
     if (valid) {
         const CellT<S>& me = cs[threadIdx.y + 1][threadIdx.x + 1];
         const R dt = g.dt, c = g.c, c2 = g.c * g.c;
@@ -413,6 +454,27 @@ __global__ void __launch_bounds__(kTX* kTY)
             out[N + idx] = RFx.d;
             out[2 * N + idx] = RFy.d;
             if constexpr (GAS) out[3 * N + idx] = (g.rho_cv[idx] * T + exch).d;
+        } else if constexpr (MGD) {
+            // z = omega z', residual r - omega J z' (kept for the restriction)
+            const R zr[3] = {me.E, me.Fx, me.Fy}, jz[3] = {RE, RFx, RFy};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                mgp.zout[q * N + idx] = mgp.omega * zr[q];
+                mg_res[q] = mgp.r[q * N + idx] - mgp.omega * jz[q];
+            }
+        } else if constexpr (MGU) {
+            // zout = zz + omega M^-1 (r - J zz)
+            const R zz[3] = {me.E, me.Fx, me.Fy}, jz[3] = {RE, RFx, RFy};
+            R res[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) res[q] = mgp.r[q * N + idx] - jz[q];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                R a = R(0);
+#pragma unroll
+                for (int c2i = 0; c2i < 3; ++c2i) a += binv[(long long)(q * 3 + c2i) * N + idx] * res[c2i];
+                mgp.zout[q * N + idx] = zz[q] + mgp.omega * a;
+            }
         } else if constexpr (LIN) {
             out[idx] = RE;
             out[N + idx] = RFx;
@@ -435,6 +497,21 @@ __global__ void __launch_bounds__(kTX* kTY)
         if (partials) {
             const double t = block_sum_linear(ss, tid, kTX * kTY);
             if (tid == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+        }
+    }
+    if constexpr (MGD) {
+        // 2 x 2 aggregates of the tile (origins even): the root thread sums them
+        __shared__ R rs[kTY][kTX][3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) rs[threadIdx.y][threadIdx.x][q] = mg_res[q];
+        __syncthreads();
+        const int tx = threadIdx.x, ty = threadIdx.y;
+        if ((tx & 1) == 0 && (ty & 1) == 0 && valid) {
+            const long long Nc = (long long)mgp.nxc * mgp.nyc;
+            const long long I = (long long)(iy / 2) * mgp.nxc + ix / 2;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                mgp.rc[q * Nc + I] = (rs[ty][tx][q] + rs[ty][tx + 1][q]) + (rs[ty + 1][tx][q] + rs[ty + 1][tx + 1][q]);
         }
     }
 }
@@ -496,10 +573,10 @@ int launch_residual_f64(const Dev<double>& g, const double* U, double* R, double
         if (!partials || nb <= capacity) {
             if (g.gas)
                 k_stencil2d_tiled<double, true, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, nullptr,
-                                                                                     R, partials);
+                                                                                     R, partials, {});
             else
                 k_stencil2d_tiled<double, false, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, nullptr,
-                                                                                      R, partials);
+                                                                                      R, partials, {});
             return (int)nb;
         }
     }
@@ -515,9 +592,11 @@ static bool jv_tiled(const Dev<R>& g, const R* U, const R* v, R* Jv, cudaStream_
     if (g.dim != 2 || (g.implicit_eigs && !g.fixed_eigs)) return false;
     dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
     if (g.gas)
-        k_stencil2d_tiled<Dual<R>, true, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, nullptr, Jv, nullptr);
+        k_stencil2d_tiled<Dual<R>, true, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, nullptr, Jv, nullptr,
+                                                                           {});
     else
-        k_stencil2d_tiled<Dual<R>, false, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, nullptr, Jv, nullptr);
+        k_stencil2d_tiled<Dual<R>, false, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, nullptr, Jv, nullptr,
+                                                                            {});
     return true;
 }
 
@@ -545,14 +624,14 @@ static void jv_linear(const Dev<R>& g, const R* U, const R* pj, const R* binv, c
     const dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
     if (binv) {
         if (g.gas)
-            k_stencil2d_tiled<R, true, kTileJvLinearPre><<<grid, block, 0, s>>>(g, U, v, pj, binv, Jv, nullptr);
+            k_stencil2d_tiled<R, true, kTileJvLinearPre><<<grid, block, 0, s>>>(g, U, v, pj, binv, Jv, nullptr, {});
         else
-            k_stencil2d_tiled<R, false, kTileJvLinearPre><<<grid, block, 0, s>>>(g, U, v, pj, binv, Jv, nullptr);
+            k_stencil2d_tiled<R, false, kTileJvLinearPre><<<grid, block, 0, s>>>(g, U, v, pj, binv, Jv, nullptr, {});
     } else {
         if (g.gas)
-            k_stencil2d_tiled<R, true, kTileJvLinear><<<grid, block, 0, s>>>(g, U, v, pj, nullptr, Jv, nullptr);
+            k_stencil2d_tiled<R, true, kTileJvLinear><<<grid, block, 0, s>>>(g, U, v, pj, nullptr, Jv, nullptr, {});
         else
-            k_stencil2d_tiled<R, false, kTileJvLinear><<<grid, block, 0, s>>>(g, U, v, pj, nullptr, Jv, nullptr);
+            k_stencil2d_tiled<R, false, kTileJvLinear><<<grid, block, 0, s>>>(g, U, v, pj, nullptr, Jv, nullptr, {});
     }
 }
 void launch_jv_linear_f64(const Dev<double>& g, const double* U, const double* pj, const double* v, double* Jv,
@@ -566,6 +645,33 @@ void launch_jv_linear_f32(const Dev<float>& g, const float* U, const float* pj, 
 void launch_jv_linear_pre_f32(const Dev<float>& g, const float* U, const float* pj, const float* binv,
                               const float* v, float* Jv, cudaStream_t s) {
     jv_linear<float>(g, U, pj, binv, v, Jv, s);
+}
+
+void launch_mg_down0_f32(const Dev<float>& g, const float* U, const float* pj, const float* binv, const float* r,
+                         float omega, float* z, int nxc, int nyc, float* rc, cudaStream_t s) {
+    const dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
+    TileMg<float> m;
+    m.r = r;
+    m.nxc = nxc;
+    m.nyc = nyc;
+    m.rc = rc;
+    m.zout = z;
+    m.omega = omega;
+    k_stencil2d_tiled<float, false, kTileMgDown0><<<grid, block, 0, s>>>(g, U, r, pj, binv, nullptr, nullptr, m);
+}
+
+void launch_mg_up0_f32(const Dev<float>& g, const float* U, const float* pj, const float* binv, const float* r,
+                       const float* z, const float* zc, int nxc, int nyc, float omega, float* zout, cudaStream_t s) {
+    const dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
+    TileMg<float> m;
+    m.r = r;
+    m.z = z;
+    m.zc = zc;
+    m.nxc = nxc;
+    m.nyc = nyc;
+    m.zout = zout;
+    m.omega = omega;
+    k_stencil2d_tiled<float, false, kTileMgUp0><<<grid, block, 0, s>>>(g, U, nullptr, pj, binv, nullptr, nullptr, m);
 }
 
 void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s) {
