@@ -272,12 +272,13 @@ def main():
             "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
             "peak_source": peak_src, "profiled_steps": a.profile_steps,
             "profiled_ms_per_step": prof_ms / max(1, a.profile_steps), "kernel_ms": kms, "kernel_count": kcount}
-    bytes_map = {"jv32": p1["bytes_per_jv32"], "jv64": p1["bytes_per_jv"], "residual": p1["bytes_per_residual"]}
+    bytes_map = {"jv32": p1["bytes_per_jv32"], "jv64": p1["bytes_per_jv"], "residual": p1["bytes_per_residual"],
+                 "pc_apply": p1.get("bytes_per_mg_cycle", 0.0) if use_mg else 0.0}
     if dom == "ortho":
         ob = p1.get("ortho_bytes", 0.0) - p0.get("ortho_bytes", 0.0)
         if ob and kms[dom] > 0:
             roof["achieved"] = ob / (kms[dom] / 1e3) / 1e9
-    elif dom in bytes_map and kcount[dom] > 0:
+    elif bytes_map.get(dom) and kcount[dom] > 0:
         roof["achieved"] = bytes_map[dom] / (kms[dom] / kcount[dom] / 1e3) / 1e9
     if roof["achieved"] is not None:
         roof["frac"] = roof["achieved"] / peak

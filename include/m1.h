@@ -117,8 +117,8 @@ typedef enum {
     M1_K_RESIDUAL = 0,   /* FP64 residual stencil */
     M1_K_JV64 = 1,       /* FP64 J v stencil */
     M1_K_JV32 = 2,       /* FP32 J v stencil */
-    M1_K_PC_BUILD = 3,   /* point-block extraction + inversion */
-    M1_K_PC_APPLY = 4,   /* block-Jacobi apply */
+    M1_K_PC_BUILD = 3,   /* point blocks, dP/dU, multigrid levels and their inverses */
+    M1_K_PC_APPLY = 4,   /* block-Jacobi apply or one multigrid cycle */
     M1_K_ORTHO = 5,      /* Gram-Schmidt dots, updates, norms, Givens */
     M1_K_VECTOR = 6,     /* other vector kernels (axpy, conversions) */
     M1_K_EXPLICIT = 7,   /* semi-implicit step kernels */
@@ -135,6 +135,7 @@ typedef struct {
     double kernel_ms[M1_K_CLASSES];
     long long kernel_count[M1_K_CLASSES];
     double ortho_bytes;   /* algorithmic bytes moved by the Gram-Schmidt kernels so far */
+    double bytes_per_mg_cycle;  /* algorithmic bytes of one multigrid cycle (0 before a hierarchy is built) */
 } m1_stats_t;
 
 typedef struct m1_ctx m1_ctx;

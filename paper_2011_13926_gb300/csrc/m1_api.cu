@@ -467,6 +467,7 @@ m1_status build_mg(m1_ctx* ctx, const Dev<float>& g32) {
     const bool use_direct = ctx->nu == 3 && !ctx->mg_probe;
     mg_build(ctx->mg, op, use_direct ? &direct : nullptr, ctx->mg_inv64, ctx->singular, ctx->s);
     count(ctx, mg_launches_per_build(ctx->mg, use_direct));
+    ctx->st.bytes_per_mg_cycle = mg_cycle_bytes(ctx->mg, op.down0 != nullptr, ctx->d.fixed_eigs != 0);
     return M1_OK;
 }
 

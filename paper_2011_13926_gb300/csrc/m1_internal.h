@@ -77,6 +77,7 @@ void mg_build(MgHierarchy& H, const MgJvOp& J, const MgDirect* direct, double* i
 void mg_cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float* zout, cudaStream_t s);
 int mg_launches_per_build(const MgHierarchy& H, bool direct);
 int mg_launches_per_cycle(const MgHierarchy& H, bool fused);
+double mg_cycle_bytes(const MgHierarchy& H, bool fused, bool fixed_eigs);
 // level 0 of the multigrid cycle in one tiled pass each (radiation only, FP32):
 // down: z = omega M^-1 r, rc = P^T (r - J z); up: zz = z + P zc,
 // zout = zz + omega M^-1 (r - J zz); M^-1 the block inverses binv

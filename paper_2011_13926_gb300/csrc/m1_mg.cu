@@ -39,6 +39,30 @@ int mg_colour_period(int n, bool periodic) {
     return n;
 }
 
+// Programmatic dependent launch within the cycle's chain of coarse-level
+// kernels: each lets its successor launch as soon as all of its own blocks
+// run, and the successor waits for it (a hardware grid dependency) before
+// reading anything the chain writes; before the wait a kernel only reads the
+// hierarchy (stencils, block inverses), written before the cycle began. A
+// kernel launched without the attribute passes both at once.
+__device__ __forceinline__ void mg_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void mg_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // neighbour s of cell (ix, iy) on an nx x ny level, -1 beyond a non-periodic side
 __device__ __forceinline__ long long mg_nb(int ix, int iy, int s, int nx, int ny, bool px, bool py) {
     int jx = ix + (s == 1 ? -1 : s == 2 ? 1 : 0);
@@ -323,6 +347,7 @@ __global__ void __launch_bounds__(kMgCoarsest* kMgCoarsest) k_mg_coarsest(int nx
     const bool own = i < N;
     float a[5][NU][NU], d[NU][NU], ri[NU];
     long long nb[5];
+    mg_pdl_trigger();
     if (own) {
         const int ix = i % nx, iy = i / nx;
 #pragma unroll
@@ -334,14 +359,16 @@ __global__ void __launch_bounds__(kMgCoarsest* kMgCoarsest) k_mg_coarsest(int nx
                 for (int c = 0; c < NU; ++c) a[s][q][c] = A[((long long)(s * NU + q) * NU + c) * N + i];
         }
 #pragma unroll
-        for (int q = 0; q < NU; ++q) {
-            ri[q] = r[q * N + i];
+        for (int q = 0; q < NU; ++q)
 #pragma unroll
             for (int c = 0; c < NU; ++c) d[q][c] = Dinv[(long long)(q * NU + c) * N + i];
-        }
 #pragma unroll
         for (int c = 0; c < NU; ++c) zs[0][c][i] = 0.f;
     }
+    mg_pdl_wait();
+    if (own)
+#pragma unroll
+        for (int q = 0; q < NU; ++q) ri[q] = r[q * N + i];
     __syncthreads();
     int cur = 0;
     for (int k = 0; k < sweeps; ++k) {
@@ -399,6 +426,26 @@ __global__ void __launch_bounds__(kMgTX* kMgTY) k_mg_down(int nx, int ny, bool p
     const long long N = (long long)nx * ny, Nc = (long long)nxc * nyc;
     const int x0 = blockIdx.x * kMgTX, y0 = blockIdx.y * kMgTY;
     const int tid = threadIdx.y * kMgTX + threadIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ix = x0 + tx, iy = y0 + ty;
+    const bool valid = ix < nx && iy < ny;
+    const long long i = valid ? (long long)iy * nx + ix : 0;
+    mg_pdl_trigger();
+    // this cell's stencil row (in flight during the wait and the staging), then
+    // its right-hand side
+    float a[5][NU][NU], ri[NU];
+    if (valid) {
+#pragma unroll
+        for (int s = 0; s < 5; ++s)
+#pragma unroll
+            for (int q = 0; q < NU; ++q)
+#pragma unroll
+                for (int c = 0; c < NU; ++c) a[s][q][c] = A[((long long)(s * NU + q) * NU + c) * N + i];
+    }
+    mg_pdl_wait();
+    if (valid)
+#pragma unroll
+        for (int c = 0; c < NU; ++c) ri[c] = r[c * N + i];
     for (int t = tid; t < (kMgTX + 2) * (kMgTY + 2); t += kMgTX * kMgTY) {
         const int hx = t % (kMgTX + 2), hy = t / (kMgTX + 2);
         if ((hx == 0 || hx == kMgTX + 1) && (hy == 0 || hy == kMgTY + 1)) continue;  // corners
@@ -416,17 +463,14 @@ __global__ void __launch_bounds__(kMgTX* kMgTY) k_mg_down(int nx, int ny, bool p
         }
     }
     __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int ix = x0 + tx, iy = y0 + ty;
     float res[NU];
 #pragma unroll
     for (int c = 0; c < NU; ++c) res[c] = 0.f;
-    if (ix < nx && iy < ny) {
-        const long long i = (long long)iy * nx + ix;
+    if (valid) {
 #pragma unroll
         for (int c = 0; c < NU; ++c) {
             z[c * N + i] = zt[ty + 1][tx + 1][c];
-            res[c] = r[c * N + i];
+            res[c] = ri[c];
         }
         const int hx[5] = {tx + 1, tx, tx + 2, tx + 1, tx + 1}, hy[5] = {ty + 1, ty + 1, ty + 1, ty, ty + 2};
 #pragma unroll
@@ -434,13 +478,12 @@ __global__ void __launch_bounds__(kMgTX* kMgTY) k_mg_down(int nx, int ny, bool p
 #pragma unroll
             for (int q = 0; q < NU; ++q)
 #pragma unroll
-                for (int c = 0; c < NU; ++c)
-                    res[q] -= A[((long long)(s * NU + q) * NU + c) * N + i] * zt[hy[s]][hx[s]][c];
+                for (int c = 0; c < NU; ++c) res[q] -= a[s][q][c] * zt[hy[s]][hx[s]][c];
     }
 #pragma unroll
     for (int c = 0; c < NU; ++c) rs[ty][tx][c] = res[c];
     __syncthreads();
-    if ((tx & 1) == 0 && (ty & 1) == 0 && ix < nx && iy < ny) {
+    if ((tx & 1) == 0 && (ty & 1) == 0 && valid) {
         const long long I = (long long)(iy / 2) * nxc + ix / 2;
 #pragma unroll
         for (int c = 0; c < NU; ++c)
@@ -459,6 +502,30 @@ __global__ void __launch_bounds__(kMgTX* kMgTY) k_mg_up(int nx, int ny, bool px,
     const long long N = (long long)nx * ny, Nc = (long long)nxc * nyc;
     const int x0 = blockIdx.x * kMgTX, y0 = blockIdx.y * kMgTY;
     const int tid = threadIdx.y * kMgTX + threadIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ix = x0 + tx, iy = y0 + ty;
+    const bool valid = ix < nx && iy < ny;
+    const long long i = valid ? (long long)iy * nx + ix : 0;
+    mg_pdl_trigger();
+    // this cell's stencil row and block inverse (in flight during the wait and
+    // the staging), then its right-hand side
+    float a[5][NU][NU], d[NU][NU], ri[NU];
+    if (valid) {
+#pragma unroll
+        for (int s = 0; s < 5; ++s)
+#pragma unroll
+            for (int q = 0; q < NU; ++q)
+#pragma unroll
+                for (int c = 0; c < NU; ++c) a[s][q][c] = A[((long long)(s * NU + q) * NU + c) * N + i];
+#pragma unroll
+        for (int q = 0; q < NU; ++q)
+#pragma unroll
+            for (int c = 0; c < NU; ++c) d[q][c] = Dinv[(long long)(q * NU + c) * N + i];
+    }
+    mg_pdl_wait();
+    if (valid)
+#pragma unroll
+        for (int q = 0; q < NU; ++q) ri[q] = r[q * N + i];
     for (int t = tid; t < (kMgTX + 2) * (kMgTY + 2); t += kMgTX * kMgTY) {
         const int hx = t % (kMgTX + 2), hy = t / (kMgTX + 2);
         if ((hx == 0 || hx == kMgTX + 1) && (hy == 0 || hy == kMgTY + 1)) continue;  // corners
@@ -468,26 +535,23 @@ __global__ void __launch_bounds__(kMgTX* kMgTY) k_mg_up(int nx, int ny, bool px,
         for (int c = 0; c < NU; ++c) zt[hy][hx][c] = j >= 0 ? z[c * N + j] + zc[c * Nc + J] : 0.f;
     }
     __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int ix = x0 + tx, iy = y0 + ty;
-    if (ix >= nx || iy >= ny) return;
-    const long long i = (long long)iy * nx + ix;
+    if (!valid) return;
     float res[NU];
 #pragma unroll
-    for (int c = 0; c < NU; ++c) res[c] = r[c * N + i];
+    for (int c = 0; c < NU; ++c) res[c] = ri[c];
     const int hx[5] = {tx + 1, tx, tx + 2, tx + 1, tx + 1}, hy[5] = {ty + 1, ty + 1, ty + 1, ty, ty + 2};
 #pragma unroll
     for (int s = 0; s < 5; ++s)
 #pragma unroll
         for (int q = 0; q < NU; ++q)
 #pragma unroll
-            for (int c = 0; c < NU; ++c) res[q] -= A[((long long)(s * NU + q) * NU + c) * N + i] * zt[hy[s]][hx[s]][c];
+            for (int c = 0; c < NU; ++c) res[q] -= a[s][q][c] * zt[hy[s]][hx[s]][c];
 #pragma unroll
     for (int q = 0; q < NU; ++q) {
-        float a = 0.f;
+        float t = 0.f;
 #pragma unroll
-        for (int c = 0; c < NU; ++c) a += Dinv[(long long)(q * NU + c) * N + i] * res[c];
-        zout[q * N + i] = zt[ty + 1][tx + 1][q] + kMgOmega * a;
+        for (int c = 0; c < NU; ++c) t += d[q][c] * res[c];
+        zout[q * N + i] = zt[ty + 1][tx + 1][q] + kMgOmega * t;
     }
 }
 
@@ -642,17 +706,18 @@ static void cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float*
     // down the assembled levels
     for (int l = 1; l < H.nlev - 1; ++l) {
         const dim3 grid((H.nx[l] + kMgTX - 1) / kMgTX, (H.ny[l] + kMgTY - 1) / kMgTY), block(kMgTX, kMgTY);
-        k_mg_down<NU><<<grid, block, 0, s>>>(H.nx[l], H.ny[l], H.px, H.py, H.A[l], H.Dinv[l], H.r[l], H.z[l],
-                                              H.nx[l + 1], H.ny[l + 1], H.r[l + 1]);
+        launch_pdl(k_mg_down<NU>, grid, block, s, H.nx[l], H.ny[l], H.px, H.py, (const float*)H.A[l],
+                   (const float*)H.Dinv[l], (const float*)H.r[l], H.z[l], H.nx[l + 1], H.ny[l + 1], H.r[l + 1]);
     }
     const int L = H.nlev - 1;
-    k_mg_coarsest<NU><<<1, kMgCoarsest * kMgCoarsest, 0, s>>>(H.nx[L], H.ny[L], H.px, H.py, H.A[L], H.Dinv[L],
-                                                               H.r[L], H.z2[L], kMgCoarseSweeps);
+    launch_pdl(k_mg_coarsest<NU>, dim3(1), dim3(kMgCoarsest * kMgCoarsest), s, H.nx[L], H.ny[L], H.px, H.py,
+               (const float*)H.A[L], (const float*)H.Dinv[L], (const float*)H.r[L], H.z2[L], kMgCoarseSweeps);
     // up
     for (int l = L - 1; l >= 1; --l) {
         const dim3 grid((H.nx[l] + kMgTX - 1) / kMgTX, (H.ny[l] + kMgTY - 1) / kMgTY), block(kMgTX, kMgTY);
-        k_mg_up<NU><<<grid, block, 0, s>>>(H.nx[l], H.ny[l], H.px, H.py, H.A[l], H.Dinv[l], H.r[l], H.z[l],
-                                            H.z2[l + 1], H.nx[l + 1], H.ny[l + 1], H.z2[l]);
+        launch_pdl(k_mg_up<NU>, grid, block, s, H.nx[l], H.ny[l], H.px, H.py, (const float*)H.A[l],
+                   (const float*)H.Dinv[l], (const float*)H.r[l], (const float*)H.z[l], (const float*)H.z2[l + 1],
+                   H.nx[l + 1], H.ny[l + 1], H.z2[l]);
     }
     // level 0: prolong, J v, post-smoothing
     if (fused) {
@@ -667,6 +732,25 @@ static void cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float*
 int mg_launches_per_cycle(const MgHierarchy& H, bool fused) {
     if (H.nlev == 1) return 1 + 2 * (kMgCoarseSweeps - 1);
     return (fused ? 2 : 6) + (H.nlev - 2) + 1 + (H.nlev - 2);
+}
+
+double mg_cycle_bytes(const MgHierarchy& H, bool fused, bool fixed_eigs) {
+    // minimum traffic in FP32 words: level 0 reads r, M^-1, dP/dU and the face
+    // data (sigma_a, sigma_f, alpha per axis, lambda+- per axis unless fixed)
+    // and writes z in the down pass and zout in the up pass; assembled levels
+    // read A (5 n_u^2), M^-1 (n_u^2), r and z per pass; restriction and
+    // prolongation add n_u words per coarse cell
+    const double nu = H.nu, faces = 2.0 + 2.0 + (fixed_eigs ? 0.0 : 4.0);
+    auto cells = [&](int l) { return (double)H.nx[l] * H.ny[l]; };
+    if (H.nlev == 1) return 4.0 * cells(0) * kMgCoarseSweeps * (3.0 * nu + nu * nu + 9.0 + faces);
+    double w = 0.0;
+    const double lvl0 = fused ? (nu + nu * nu + 9.0 + faces + nu) + (2.0 * nu + nu * nu + 9.0 + faces + nu)
+                              : 2.0 * (3.0 * nu + nu * nu + 9.0 + faces) + 4.0 * nu;
+    w += cells(0) * lvl0 + 2.0 * nu * cells(1);
+    for (int l = 1; l < H.nlev - 1; ++l)
+        w += cells(l) * 2.0 * (5.0 * nu * nu + nu * nu + 3.0 * nu) + 2.0 * nu * cells(l + 1);
+    w += cells(H.nlev - 1) * (5.0 * nu * nu + nu * nu + 2.0 * nu);
+    return 4.0 * w;
 }
 
 void mg_cycle(const MgHierarchy& H, const MgJvOp& J, const float* r0, float* zout, cudaStream_t s) {

@@ -84,11 +84,13 @@ class Stats(C.Structure):
                 ("explicit_steps", C.c_longlong), ("implicit_steps", C.c_longlong),
                 ("kernel_launches", C.c_longlong), ("bytes_per_jv", C.c_double),
                 ("bytes_per_residual", C.c_double), ("bytes_per_jv32", C.c_double),
-                ("kernel_ms", C.c_double * 8), ("kernel_count", C.c_longlong * 8), ("ortho_bytes", C.c_double)]
+                ("kernel_ms", C.c_double * 8), ("kernel_count", C.c_longlong * 8), ("ortho_bytes", C.c_double),
+                ("bytes_per_mg_cycle", C.c_double)]
 
     def as_dict(self):
         out = {k: getattr(self, k) for k, _ in self._fields_[:11]}
         out["ortho_bytes"] = self.ortho_bytes
+        out["bytes_per_mg_cycle"] = self.bytes_per_mg_cycle
         out["kernel_ms"] = dict(zip(KERNEL_CLASSES, list(self.kernel_ms)))
         out["kernel_count"] = dict(zip(KERNEL_CLASSES, list(self.kernel_count)))
         return out
