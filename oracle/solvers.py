@@ -92,6 +92,53 @@ def gmres(A: Callable, b: np.ndarray, Minv: Callable, rtol: float = 1e-10, resta
         x = x + Minv(V[:k_used].T @ y)
 
 
+def bicgstab(A: Callable, b: np.ndarray, Minv: Callable, rtol: float = 1e-10, maxiter: int = 3000
+             ) -> GmresResult:
+    """Right-preconditioned BiCGStab (the paper's Krylov solver, Sect. 3.3.1) for A x = b.
+
+    van der Vorst's recurrence on A M^-1 y = b, x = M^-1 y, from x = 0 with the shadow
+    residual equal to b; one iteration is two products with A and two with M^-1. Stops when
+    ||r|| (the recurred residual, checked after each half step) is at most rtol ||b||.
+    The returned count is the number of full or half iterations taken.
+    """
+    n = b.size
+    x = np.zeros(n)
+    bnorm = np.linalg.norm(b)
+    hist = [bnorm]
+    if bnorm == 0.0:
+        return GmresResult(x, 0, True, 0.0, hist)
+    target = rtol * bnorm
+    r = b.copy()
+    rhat = b.copy()
+    rho = alpha = omega = 1.0
+    v = np.zeros(n)
+    p = np.zeros(n)
+    it = 0
+    while it < maxiter:
+        rho_new = rhat @ r
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        phat = Minv(p)
+        v = A(phat)
+        alpha = rho_new / (rhat @ v)
+        s = r - alpha * v
+        it += 1
+        if np.linalg.norm(s) <= target:
+            x = x + alpha * phat
+            hist.append(np.linalg.norm(s))
+            return GmresResult(x, it, True, np.linalg.norm(s), hist)
+        shat = Minv(s)
+        t = A(shat)
+        omega = (t @ s) / (t @ t)
+        x = x + alpha * phat + omega * shat
+        r = s - omega * t
+        rho = rho_new
+        hist.append(np.linalg.norm(r))
+        if hist[-1] <= target:
+            return GmresResult(x, it, True, hist[-1], hist)
+    return GmresResult(x, it, False, hist[-1], hist)
+
+
 def block_jacobi(blocks: np.ndarray, N: int, nu: int) -> Callable:
     """K^-1 r with K the point-block diagonal of the Jacobian."""
     inv = np.linalg.inv(blocks)  # (N, nu, nu)

@@ -301,6 +301,44 @@ def test_gmres_matches_dense_lu(dim):
     assert np.linalg.norm(res.x - x_lu) <= 1e-10 * np.linalg.norm(x_lu)
 
 
+@pytest.mark.parametrize("dim", [1, 2])
+def test_bicgstab_matches_dense_lu(dim):
+    from oracle.solvers import bicgstab
+    rng = np.random.default_rng(60 + dim)
+    p = _gas_case(rng, dim)
+    s = Scheme(p)
+    u = s.pack(s.Un)
+    b = rng.standard_normal(u.size)
+    x_lu = dense_solve(s, u, b)
+    Minv = block_jacobi(s.diag_blocks(u), s.N, s.nu)
+    res = bicgstab(lambda v: s.jv(u, v), b, Minv, rtol=1e-13, maxiter=5000)
+    assert res.converged
+    assert np.linalg.norm(res.x - x_lu) <= 1e-9 * np.linalg.norm(x_lu)
+
+
+def test_bicgstab_exact_preconditioner_takes_one_step():
+    # M^-1 = A^-1 makes A M^-1 the identity: the first half step leaves s = 0
+    from oracle.solvers import bicgstab
+    rng = np.random.default_rng(61)
+    A = rng.standard_normal((12, 12)) + 12.0 * np.eye(12)
+    Ainv = np.linalg.inv(A)
+    b = rng.standard_normal(12)
+    res = bicgstab(lambda v: A @ v, b, lambda r: Ainv @ r, rtol=1e-12)
+    assert res.converged and res.iters == 1
+    assert np.linalg.norm(res.x - np.linalg.solve(A, b)) <= 1e-12 * np.linalg.norm(res.x)
+
+
+def test_bicgstab_nonsymmetric_dense():
+    from oracle.solvers import bicgstab
+    rng = np.random.default_rng(62)
+    n = 40
+    A = rng.standard_normal((n, n)) + 3.0 * np.sqrt(n) * np.eye(n)
+    b = rng.standard_normal(n)
+    res = bicgstab(lambda v: A @ v, b, lambda r: r, rtol=1e-12, maxiter=500)
+    assert res.converged
+    assert np.linalg.norm(res.x - np.linalg.solve(A, b)) <= 1e-10 * np.linalg.norm(res.x)
+
+
 def test_newton_quadratic_tail():
     rng = np.random.default_rng(4)
     p = si.make_problem(1, (48,), bc=[("periodic", "periodic")], dt_factor=2.0, gas=True)
