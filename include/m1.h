@@ -55,6 +55,10 @@ typedef enum {
 typedef enum { M1_BC_OUTFLOW = 0, M1_BC_PERIODIC = 1, M1_BC_REFLECT = 2, M1_BC_DIRICHLET = 3 } m1_bc;
 typedef enum { M1_MEM_HOST = 0, M1_MEM_DEVICE = 1 } m1_mem;
 typedef enum { M1_PREC_FP64 = 0, M1_PREC_MIXED = 1 } m1_precision;
+/* Krylov method of the Newton linear solves: restarted GMRES(restart), or the
+ * paper's BiCGStab (Sect. 3.3.1), right-preconditioned, the recurrence scalars on
+ * the device; gmres_max and gmres_rtol bound either. */
+typedef enum { M1_KRYLOV_GMRES = 0, M1_KRYLOV_BICGSTAB = 1 } m1_krylov;
 typedef enum { M1_PRECOND_NONE = 0, M1_PRECOND_BJ = 1, M1_PRECOND_LEARNED = 2, M1_PRECOND_MG = 3 } m1_precond;
 
 /* Grid and discretisation flags (one context per grid). */
@@ -87,6 +91,7 @@ typedef struct {
     int line_search;      /* 1: halve theta up to 6 times until the Armijo decrease holds */
     int advance;          /* 1: on success U^n <- U^{n+1}; 0: keep U^n (result in m1_get_solution) */
     int refine_max;       /* mixed precision: max FP64 refinement sweeps per Newton step (4) */
+    int krylov;           /* an m1_krylov value, default M1_KRYLOV_GMRES; the learned preconditioner needs GMRES */
 } m1_solver_opts;
 
 #define M1_HIST 64  /* length of the per-Newton-iteration histories */

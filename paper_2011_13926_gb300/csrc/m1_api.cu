@@ -82,7 +82,9 @@ struct m1_ctx {
     // multigrid preconditioner (allocated on first use)
     MgHierarchy mg;
     bool mg_alloc = false;
-    double* mg_inv64 = nullptr;  // FP64 scratch of the coarse block inverses
+    double* mg_inv64 = nullptr;  // FP64 scratch of the block inverses of every level
+    double* bs_part = nullptr;   // BiCGStab: dot-product partials
+    double* bs_sc = nullptr;     // BiCGStab: recurrence scalars
     Dev<float> mg_g32{};         // the step's FP32 descriptor the level-0 J v uses
     bool mg_probe = false;       // level-0 stencil by probes through J v instead of directly
     float *pair_x = nullptr, *pair_t = nullptr;  // staging of one training pair (4N and 3N floats)
@@ -737,9 +739,116 @@ m1_status gmres64(m1_ctx* ctx, Ops64& ops, const double* b, double* x, double rt
 // Mixed precision: FP32 inner GMRES (FP32 Jv, FP32 basis and block inverse,
 // FP64 dot accumulation and Hessenberg) on r / ||r||, refined against the
 // FP64 linear residual r = b - J x (FP64 Jv) until rtol is met.
+// ---------------------------------------------------------------- BiCGStab
+inline void bs_dots(const double* a0, const double* b0, const double* a1, const double* b1, long long n, int nd,
+                    double* part, int mode, double* sc, double* slot, cudaStream_t s) {
+    launch_bs_dots_f64(a0, b0, a1, b1, n, nd, part, mode, sc, slot, s);
+}
+inline void bs_dots(const float* a0, const float* b0, const float* a1, const float* b1, long long n, int nd,
+                    double* part, int mode, double* sc, double* slot, cudaStream_t s) {
+    launch_bs_dots_f32(a0, b0, a1, b1, n, nd, part, mode, sc, slot, s);
+}
+inline void bs_p(double* p, const double* r, const double* v, const double* sc, long long n, cudaStream_t s) {
+    launch_bs_p_f64(p, r, v, sc, n, s);
+}
+inline void bs_p(float* p, const float* r, const float* v, const double* sc, long long n, cudaStream_t s) {
+    launch_bs_p_f32(p, r, v, sc, n, s);
+}
+inline void bs_s(double* sv, const double* r, const double* v, const double* sc, long long n, cudaStream_t s) {
+    launch_bs_s_f64(sv, r, v, sc, n, s);
+}
+inline void bs_s(float* sv, const float* r, const float* v, const double* sc, long long n, cudaStream_t s) {
+    launch_bs_s_f32(sv, r, v, sc, n, s);
+}
+inline void bs_xr(double* x, double* r, const double* ph, const double* sh, const double* sv, const double* t,
+                  const double* rh, double* sc, long long n, double* part, double* slot, cudaStream_t s) {
+    launch_bs_xr_f64(x, r, ph, sh, sv, t, rh, sc, n, part, slot, s);
+}
+inline void bs_xr(double* x, float* r, const float* ph, const float* sh, const float* sv, const float* t,
+                  const float* rh, double* sc, long long n, double* part, double* slot, cudaStream_t s) {
+    launch_bs_xr_f32(x, r, ph, sh, sv, t, rh, sc, n, part, slot, s);
+}
+
+// Right-preconditioned BiCGStab (Sect. 3.3.1) on A M^-1 from x = 0: x (FP64) +=
+// the solution of A x = b to ||r|| <= target; the eight work vectors are rows of
+// `work` (stride ld). The host reads ||r||^2 and the breakdown flag once per
+// iteration (every scalar of the recurrence stays on the device).
+template <class T, class Ops>
+m1_status bicgstab_solve(m1_ctx* ctx, Ops& ops, const T* b, double* x, double target, int maxit, T* work,
+                         int* iters, double* res_out, bool* conv) {
+    const long long n = ctx->n, ld = ctx->ld;
+    cudaStream_t s = ctx->s;
+    CKS(dalloc(ctx, &ctx->bs_part, (size_t)bs_partial_rows()));
+    CKS(dalloc(ctx, &ctx->bs_sc, (size_t)kBsScalars));
+    T *r = work, *rh = work + ld, *p = work + 2 * ld, *v = work + 3 * ld, *ph = work + 4 * ld, *sv = work + 5 * ld,
+      *sh = work + 6 * ld, *t = work + 7 * ld;
+    CK(cudaMemcpyAsync(r, b, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(rh, b, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(p, 0, sizeof(T) * n, s));
+    CK(cudaMemsetAsync(v, 0, sizeof(T) * n, s));
+    const double init[kBsScalars] = {1.0, 1.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // rho, alpha, omega
+    CK(cudaMemcpyAsync(ctx->bs_sc, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    double* slot = ctx->hpin_dev ? ctx->hpin_dev + 8 : nullptr;
+    auto read_slot = [&](double* rr, double* brk) -> m1_status {
+        if (!slot) {
+            CK(cudaMemcpyAsync(ctx->hpin + 8, ctx->bs_sc + kBsRR, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(ctx->hpin + 9, ctx->bs_sc + kBsBreak, sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+        CK(cudaEventRecord(ctx->ev_res[0], s));
+        CK(cudaGetLastError());
+        CK(cudaEventSynchronize(ctx->ev_res[0]));
+        *rr = ctx->hpin[8];
+        *brk = ctx->hpin[9];
+        return M1_OK;
+    };
+    {
+        TK tk(ctx, M1_K_ORTHO);
+        bs_dots(rh, r, r, r, n, 2, ctx->bs_part, kBsModeRho, ctx->bs_sc, slot, s);  // rho = (rhat, r), ||r||^2
+    }
+    count(ctx, 2);
+    double rr, brk;
+    CKS(read_slot(&rr, &brk));
+    *iters = 0;
+    *conv = sqrt(rr) <= target;
+    *res_out = sqrt(rr);
+    while (!*conv && *iters < maxit) {
+        {
+            TK tk(ctx, M1_K_VECTOR);
+            bs_p(p, r, v, ctx->bs_sc, n, s);
+        }
+        ops.M(p, ph);
+        ops.A(ph, v);
+        {
+            TK tk(ctx, M1_K_ORTHO);
+            bs_dots(rh, v, (const T*)nullptr, (const T*)nullptr, n, 1, ctx->bs_part, kBsModeAlpha, ctx->bs_sc,
+                    nullptr, s);
+        }
+        {
+            TK tk(ctx, M1_K_VECTOR);
+            bs_s(sv, r, v, ctx->bs_sc, n, s);
+        }
+        ops.M(sv, sh);
+        ops.A(sh, t);
+        {
+            TK tk(ctx, M1_K_ORTHO);
+            bs_dots(t, sv, t, t, n, 2, ctx->bs_part, kBsModeOmega, ctx->bs_sc, nullptr, s);
+            bs_xr(x, r, ph, sh, sv, t, rh, ctx->bs_sc, n, ctx->bs_part, slot, s);
+        }
+        count(ctx, 8);
+        CKS(read_slot(&rr, &brk));
+        ++*iters;
+        ctx->st.gmres_iters++;
+        if (!(rr == rr)) return fail(ctx, M1_ERR_NONFINITE, "non-finite BiCGStab residual");
+        *res_out = sqrt(rr);
+        *conv = *res_out <= target;
+        if (brk != 0.0) break;  // a zero denominator: stop with the iterate reached
+    }
+    return M1_OK;
+}
+
 m1_status gmres_mixed(m1_ctx* ctx, Ops64& ops64, Ops32& ops32, const double* b, double* x, double rtol,
                       int restart, int maxit, int refine_max, int* iters, int* refinements, double* bnorm_out,
-                      double* res_out, bool* conv) {
+                      double* res_out, bool* conv, bool bicg = false) {
     const bool flexible = ops32.learned;
     const long long n = ctx->n;
     cudaStream_t s = ctx->s;
@@ -771,7 +880,15 @@ m1_status gmres_mixed(m1_ctx* ctx, Ops64& ops64, Ops32& ops32, const double* b, 
         launch_scale_f64_to_f32(ctx->rhs, ctx->sc.nrm2, ctx->w32, n, s);  // unit right-hand side
         CK(cudaMemsetAsync(ctx->xacc, 0, sizeof(double) * n, s));
         count(ctx, 1);
-        for (bool first = true;; first = false) {
+        if (bicg) {  // FP32 BiCGStab on the unit right-hand side, its iterate accumulated in FP64
+            int k = 0;
+            double est = 0.0;
+            bool c = false;
+            CKS(bicgstab_solve<float>(ctx, ops32, ctx->w32, ctx->xacc, inner_rtol, maxit - *iters, ctx->V32, &k, &est,
+                                      &c));
+            *iters += k;
+        }
+        for (bool first = true; !bicg; first = false) {
             // r32 = unit rhs - J32 xacc
             if (first) {
                 CK(cudaMemcpyAsync(ctx->tmp32, ctx->w32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
@@ -888,6 +1005,7 @@ void m1_default_opts(m1_solver_opts* o) {
     o->line_search = 1;
     o->advance = 1;
     o->refine_max = 4;
+    o->krylov = M1_KRYLOV_GMRES;
 }
 
 m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out) {
@@ -1016,7 +1134,7 @@ m1_status m1_destroy(m1_ctx* ctx) {
                     ctx->delta, ctx->rhs, ctx->w, ctx->z, ctx->tmp, ctx->V, ctx->xacc, ctx->blocks, ctx->binv,
                     ctx->binv32, ctx->V32, ctx->w32, ctx->z32, ctx->U32, ctx->tmp32, ctx->Fstar, ctx->linework,
                     ctx->partials, ctx->scal_base, ctx->singular, ctx->viol, ctx->ar_partials,
-                    ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32};
+                    ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32, ctx->bs_part, ctx->bs_sc};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int l = 0; l < kMgMaxLevels; ++l) {
@@ -1310,6 +1428,10 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
     const bool pre = o->precond == M1_PRECOND_BJ || learned || use_mg;
     if (o->restart < 1 || o->restart > kMaxRestart)
         return fail(ctx, M1_ERR_ARG, "restart must be in [1, 30]");
+    if (o->krylov != M1_KRYLOV_GMRES && o->krylov != M1_KRYLOV_BICGSTAB)
+        return fail(ctx, M1_ERR_ARG, "unknown Krylov method");
+    if (learned && o->krylov != M1_KRYLOV_GMRES)
+        return fail(ctx, M1_ERR_ARG, "the learned preconditioner needs flexible GMRES");
     if (learned && (o->precision != M1_PREC_MIXED || !ctx->nn))
         return fail(ctx, M1_ERR_ARG, "the learned preconditioner needs M1_PREC_MIXED and m1_set_preconditioner");
     if (learned) CKS(dalloc(ctx, &ctx->Z32, (size_t)ctx->ld * (kMaxRestart + 1)));
@@ -1344,11 +1466,19 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
         ops32.mg = use_mg;
         if (lin) ops32.pj = ctx->pj32;
         return gmres_mixed(ctx, ops, ops32, b, x, o->gmres_rtol, o->restart, o->gmres_max, o->refine_max, iters,
-                           refinements, bnorm, res, conv);
+                           refinements, bnorm, res, conv, o->krylov == M1_KRYLOV_BICGSTAB);
     }
     CKS(pressure_jacobian64(ctx, g, Ud, &lin));
     if (lin) ops.pj = ctx->pj64;
     if (pre) CKS(build_precond(ctx, g, Ud));
+    if (o->krylov == M1_KRYLOV_BICGSTAB) {
+        double bn;
+        CKS(norm_f64(ctx, b, &bn));
+        *bnorm = bn;
+        CK(cudaMemsetAsync(x, 0, sizeof(double) * ctx->n, ctx->s));
+        if (!(bn == bn)) return fail(ctx, M1_ERR_NONFINITE, "non-finite right-hand side");
+        return bicgstab_solve<double>(ctx, ops, b, x, o->gmres_rtol * bn, o->gmres_max, ctx->V, iters, res, conv);
+    }
     return gmres64(ctx, ops, b, x, o->gmres_rtol, o->restart, o->gmres_max, iters, bnorm, res, conv);
 }
 

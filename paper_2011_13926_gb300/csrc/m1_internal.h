@@ -36,6 +36,28 @@ void launch_jv_linear_f32(const Dev<float>& g, const float* U, const float* pj, 
 // applied to v inside the stencil (M^-1 v is never stored)
 void launch_jv_linear_pre_f32(const Dev<float>& g, const float* U, const float* pj, const float* binv,
                               const float* v, float* Jv, cudaStream_t s);
+// ----------------------------------------------------------------- BiCGStab (m1_bicgstab.cu)
+// device scalars of the recurrence (doubles) and the finish modes
+constexpr int kBsRho = 0, kBsAlpha = 1, kBsOmega = 2, kBsBeta = 3, kBsRR = 4, kBsBreak = 5, kBsScalars = 8;
+constexpr int kBsModeRho = 0, kBsModeAlpha = 1, kBsModeOmega = 2;
+int bs_partial_rows();  // doubles of the partials buffer
+// nd (1 or 2) dot products (a0, b0) [, (a1, b1)] summed in a fixed order, then the
+// mode's scalar update; kBsModeRho also copies (||r||^2, breakdown) to host_slot if set
+void launch_bs_dots_f64(const double* a0, const double* b0, const double* a1, const double* b1, long long n, int nd,
+                        double* part, int mode, double* sc, double* host_slot, cudaStream_t s);
+void launch_bs_dots_f32(const float* a0, const float* b0, const float* a1, const float* b1, long long n, int nd,
+                        double* part, int mode, double* sc, double* host_slot, cudaStream_t s);
+void launch_bs_p_f64(double* p, const double* r, const double* v, const double* sc, long long n, cudaStream_t s);
+void launch_bs_p_f32(float* p, const float* r, const float* v, const double* sc, long long n, cudaStream_t s);
+void launch_bs_s_f64(double* sv, const double* r, const double* v, const double* sc, long long n, cudaStream_t s);
+void launch_bs_s_f32(float* sv, const float* r, const float* v, const double* sc, long long n, cudaStream_t s);
+// x (FP64) += alpha phat + omega shat; r = s - omega t; then the kBsModeRho finish
+void launch_bs_xr_f64(double* x, double* r, const double* phat, const double* shat, const double* sv,
+                      const double* t, const double* rhat, double* sc, long long n, double* part, double* host_slot,
+                      cudaStream_t s);
+void launch_bs_xr_f32(double* x, float* r, const float* phat, const float* shat, const float* sv, const float* t,
+                      const float* rhat, double* sc, long long n, double* part, double* host_slot, cudaStream_t s);
+
 // ----------------------------------------------------------------- multigrid (m1_mg.cu)
 constexpr int kMgMaxLevels = 16;
 // the level-0 operator of the V-cycle: out = J in (FP32, the solver's linear J v)

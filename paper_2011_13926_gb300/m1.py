@@ -24,6 +24,7 @@ BC = {"outflow": 0, "periodic": 1, "reflect": 2, "dirichlet": 3}
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 PRECOND_NONE, PRECOND_BJ, PRECOND_LEARNED, PRECOND_MG = 0, 1, 2, 3
+KRYLOV_GMRES, KRYLOV_BICGSTAB = 0, 1
 
 EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "m1_set_state", "m1_get_state",
             "m1_get_solution", "m1_set_boundary", "m1_set_emission", "m1_set_source", "m1_explicit_step",
@@ -47,7 +48,7 @@ class SolverOpts(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("restart", C.c_int),
                 ("gmres_max", C.c_int), ("gmres_rtol", C.c_double), ("precision", C.c_int),
                 ("precond", C.c_int), ("line_search", C.c_int), ("advance", C.c_int),
-                ("refine_max", C.c_int)]
+                ("refine_max", C.c_int), ("krylov", C.c_int)]
 
 
 M1_HIST = 64

@@ -139,8 +139,9 @@ def test_explicit_step_periodic_and_degenerate(m1mod):
             assert np.abs(F[b * p.ncell:(b + 1) * p.ncell] - want).max() <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("krylov", [0, 1], ids=["gmres", "bicgstab"])
 @pytest.mark.parametrize("shape", [(8,), (4, 4), (3, 3, 3)])
-def test_gmres_matches_dense_lu(m1mod, shape):
+def test_gmres_matches_dense_lu(m1mod, shape, krylov):
     dim = len(shape)
     if dim == 3:
         p = gas_3d(shape, seed=7)
@@ -156,7 +157,7 @@ def test_gmres_matches_dense_lu(m1mod, shape):
     b = np.random.default_rng(10).standard_normal(u.size)
     x_lu = dense_solve(s, u, b)
     ctx = ctx_for(m1mod, p)
-    opts = m1mod.default_opts(gmres_rtol=1e-13, gmres_max=5000)
+    opts = m1mod.default_opts(gmres_rtol=1e-13, gmres_max=5000, krylov=krylov)
     x, info = ctx.gmres_solve(p.dt, b, U=u, opts=opts)
     assert info.converged
     assert np.linalg.norm(x - x_lu) <= 1e-10 * np.linalg.norm(x_lu)
@@ -255,3 +256,21 @@ def test_krylov_is_deterministic(m1mod, prec):
     x2, i2 = ctx.gmres_solve(p.dt, b, opts=opts, raise_on_fail=False)
     assert i1.iters == i2.iters
     assert np.array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("prec,pc", [(0, 1), (1, 1), (1, 3)], ids=["fp64-bj", "mixed-bj", "mixed-mg"])
+def test_implicit_step_bicgstab(m1mod, prec, pc):
+    # the paper's Krylov solver inside the same Newton step meets the implicit parity bar
+    p = CASES["beam2d"]()
+    s = Scheme(p)
+    ref = newton_solve(s, rtol=1e-10, gmres_rtol=1e-8)
+    assert ref.converged
+    ctx = ctx_for(m1mod, p)
+    opts = m1mod.default_opts(newton_rtol=1e-10, gmres_rtol=1e-8, advance=0, precision=prec, precond=pc,
+                              krylov=m1mod.KRYLOV_BICGSTAB)
+    st, info = ctx.implicit_step(p.dt, opts)
+    assert info.converged
+    u = ctx.get_solution()
+    assert np.linalg.norm(s.residual(u)) <= 1e-8 * ref.res0
+    errs = rel_by_component(u, ref.u, s.nu, s.N)
+    assert max(errs[:1 + p.dim]) < 1e-7, errs
