@@ -483,6 +483,39 @@ class Scheme:
             div = div + self.diff(flux, a) / self.dx[a]
         return (e - self.dt * div) / p.rho_cv
 
+    def velocity_sources(self, u_faces):
+        """Explicit velocity-dependent radiation sources over dt (Sect. 2.1 with the first-order
+        expansion in u/c; applied explicitly after the implicit step, step 3 of the splitting of
+        Sect. 2.3). Cell velocity u = mean of the two face velocities along each axis; with the
+        closure pressure P of the current state, B = a_r T^4 (gas) or the frozen emission, and
+        sigma the flux opacity:
+            S_E = (sigma / c) u.F + (sigma / c) E |u|^2 + (sigma / c) u.(P u)
+            S_F = sigma P u + sigma B u + (sigma / c^2) u (u.F)
+            E' = E + dt S_E,  F' = F + c dt S_F,  rho c_v T' = rho c_v T - dt S_E (gas).
+        Returns the new state as a list of components."""
+        p, d, c, dt = self.p, self.d, self.c, self.dt
+        U = [np.array(x, dtype=float) for x in self.Un]
+        E, F = U[0], U[1:1 + d]
+        u = []
+        for a in range(d):
+            lo, hi = self.LR(np.asarray(u_faces[a], dtype=float), a)  # the two faces of every cell
+            u.append(0.5 * (lo + hi))
+        cl = Closure(E, F, c)
+        Pu = [sum(cl.pressure(a, b) * u[b] for b in range(d)) for a in range(d)]
+        uF = sum(u[a] * F[a] for a in range(d))
+        uu = sum(u[a] * u[a] for a in range(d))
+        uPu = sum(u[a] * Pu[a] for a in range(d))
+        sig = np.asarray(p.sigma_f, dtype=float)
+        B = p.a_r * U[1 + d] ** 4 if p.gas else np.asarray(p.B, dtype=float)
+        SE = (sig / c) * uF + (sig / c) * E * uu + (sig / c) * uPu
+        out = [E + dt * SE]
+        for a in range(d):
+            SF = sig * Pu[a] + sig * B * u[a] + (sig / c ** 2) * u[a] * uF
+            out.append(F[a] + c * dt * SF)
+        if p.gas:
+            out.append(U[1 + d] - dt * SE / np.asarray(p.rho_cv, dtype=float))
+        return out
+
     # ------------------------------------------------------------ diagnostics
     def realizability_violations(self, u) -> int:
         """Number of cells with |F| > c E (admissibility is not guaranteed, Sect. 3.1.3)."""

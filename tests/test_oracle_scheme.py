@@ -385,3 +385,91 @@ def test_advection_upwind_shift():
     u = np.full(n + 1, p.dx[0] / p.dt)  # CFL 1 to the right: e moves one cell
     T = Scheme(p).advect_internal_energy([u])
     assert np.allclose(T, np.roll(p.T, 1), rtol=1e-14)
+
+
+# ------------------------------------------------------------ velocity-dependent sources
+def _vel_case(d, gas, rng, F_scale=0.0):
+    n = {1: (8,), 2: (6, 5), 3: (4, 3, 3)}[d]
+    p = si.make_problem(d, n, bc=[("periodic", "periodic")] * d, gas=gas, dt_factor=3.0)
+    p.E = rng.uniform(0.5, 2.0, p.shape)
+    p.F = F_scale * p.c * p.E * rng.uniform(-1, 1, (d,) + p.shape) / np.sqrt(d)
+    p.sigma_a = 10.0 ** rng.uniform(-1, 1, p.shape)
+    p.sigma_f = p.sigma_a.copy()
+    if gas:
+        p.T = p.E ** 0.25  # a_r = 1: a_r T^4 = E
+        p.rho_cv = rng.uniform(0.5, 2.0, p.shape)
+    else:
+        p.B = p.E.copy()
+    return p
+
+
+def _faces_from_cells(p, ucell):
+    """Face velocities whose two-face mean is the given uniform cell velocity."""
+    out = []
+    for a in range(p.dim):
+        shp = list(p.shape)
+        shp[p.dim - 1 - a] += 1
+        out.append(np.full(shp, ucell[a]))
+    return out
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_velocity_sources_vanish_at_rest(d):
+    rng = np.random.default_rng(70 + d)
+    p = _vel_case(d, True, rng, F_scale=0.5)
+    s = Scheme(p)
+    out = s.velocity_sources(_faces_from_cells(p, [0.0] * d))
+    for k in range(s.nu):
+        assert np.array_equal(out[k], s.Un[k])
+
+
+@pytest.mark.parametrize("gas", [False, True])
+def test_velocity_sources_isotropic_equilibrium(gas):
+    # F = 0, P = E/3 I, a_r T^4 = E: S_E = (4/3)(sigma/c) E |u|^2, S_F = (4/3) sigma E u
+    rng = np.random.default_rng(80 + gas)
+    p = _vel_case(2, gas, rng)
+    s = Scheme(p)
+    uc = np.array([3e-3, -2e-3])
+    out = s.velocity_sources(_faces_from_cells(p, uc))
+    E, sig, c, dt = p.E, p.sigma_f, p.c, p.dt
+    SE = 4.0 / 3.0 * sig / c * E * (uc @ uc)
+    np.testing.assert_allclose(out[0], E + dt * SE, rtol=1e-14, atol=0)
+    for a in range(2):
+        np.testing.assert_allclose(out[1 + a], c * dt * 4.0 / 3.0 * sig * E * uc[a], rtol=1e-13, atol=0)
+    if gas:  # the matter energy gives what the radiation gains
+        np.testing.assert_allclose(p.rho_cv * out[3] + out[0], p.rho_cv * p.T + E, rtol=1e-14)
+
+
+def test_velocity_sources_free_streaming():
+    # f = 1 along x (P = E x x, F = c E x), u = u_x x: S_E = sigma u_x E + 2 (sigma/c) E u_x^2,
+    # S_F,x = sigma E u_x + sigma B u_x + sigma u_x^2 E / c, S_F,y = 0
+    rng = np.random.default_rng(90)
+    p = _vel_case(2, False, rng)
+    p.F = np.stack([p.c * p.E, np.zeros(p.shape)])
+    s = Scheme(p)
+    ux = 2e-3
+    out = s.velocity_sources(_faces_from_cells(p, [ux, 0.0]))
+    E, B, sig, c, dt = p.E, p.B, p.sigma_f, p.c, p.dt
+    np.testing.assert_allclose(out[0], E + dt * (sig * ux * E + 2.0 * sig / c * E * ux ** 2), rtol=1e-13)
+    np.testing.assert_allclose(out[1], c * E + c * dt * (sig * E * ux + sig * B * ux + sig * ux ** 2 * E / c),
+                               rtol=1e-13)
+    np.testing.assert_allclose(out[2], 0.0, atol=1e-300)
+
+
+def test_velocity_sources_rotate_with_the_state():
+    # rotating u and F by 90 degrees in the plane rotates the flux source and keeps S_E
+    rng = np.random.default_rng(91)
+    p = _vel_case(2, False, rng, F_scale=0.6)
+    p.E = np.full(p.shape, 1.3)
+    p.sigma_f = np.full(p.shape, 0.7)
+    p.sigma_a = p.sigma_f.copy()
+    p.B = np.full(p.shape, 0.9)
+    F0 = np.array([0.31, -0.17])
+    p.F = np.stack([np.full(p.shape, F0[0]), np.full(p.shape, F0[1])])
+    uc = np.array([1.5e-3, 0.6e-3])
+    out1 = Scheme(p).velocity_sources(_faces_from_cells(p, uc))
+    p.F = np.stack([np.full(p.shape, -F0[1]), np.full(p.shape, F0[0])])  # R F, R = rotation by +90
+    out2 = Scheme(p).velocity_sources(_faces_from_cells(p, [-uc[1], uc[0]]))
+    np.testing.assert_allclose(out2[0], out1[0], rtol=1e-14)
+    np.testing.assert_allclose(out2[1], -out1[2], rtol=1e-13)
+    np.testing.assert_allclose(out2[2], out1[1], rtol=1e-13)
