@@ -185,15 +185,27 @@ m1_status m1_set_emission(m1_ctx* ctx, const double* B, m1_mem mem);
 /* External energy source S added to dE/dt (N doubles, NULL = none). */
 m1_status m1_set_source(m1_ctx* ctx, const double* S, m1_mem mem);
 
-/* Prescribed gas velocity on the faces (gas coupling only): u[a] holds the
- * normal velocity of every face of axis a (N / n_a * (n_a + 1) doubles, the
- * face index runs fastest along x as for cells, with n_a + 1 faces along a). */
+/* Prescribed gas velocity on the faces: u[a] holds the normal velocity of every
+ * face of axis a (N / n_a * (n_a + 1) doubles, the face index runs fastest
+ * along x as for cells, with n_a + 1 faces along a). Used by m1_advect (gas
+ * coupling) and m1_velocity_sources. */
 m1_status m1_set_velocity(m1_ctx* ctx, const double* ux, const double* uy, const double* uz, m1_mem mem);
 
 /* Explicit first-order upwind transport of the gas internal energy rho c_v T by
  * the prescribed velocity over dt (the frozen-hydrodynamics step of the
  * operator split of Sect. 3.2); updates T of the current state. */
 m1_status m1_advect(m1_ctx* ctx, double dt);
+
+/* The explicit velocity-dependent radiation sources over dt (Sect. 2.1 at first
+ * order in u/c, applied after the implicit step: step 3 of the splitting of
+ * Sect. 2.3). With u the mean of a cell's two face velocities per axis, P the
+ * closure pressure of the current state, B = a_r T^4 (gas coupling) or the
+ * frozen emission and sigma the flux opacity:
+ *   S_E = (sigma/c) u.F + (sigma/c) E |u|^2 + (sigma/c) u.(P u)
+ *   S_F = sigma P u + sigma B u + (sigma/c^2) u (u.F)
+ * E += dt S_E, F += c dt S_F and, with gas coupling, rho c_v T -= dt S_E.
+ * Updates the current state; needs m1_set_velocity. */
+m1_status m1_velocity_sources(m1_ctx* ctx, double dt);
 
 /* One semi-implicit step of size dt (Sect. 3.1): HLL fluxes and alpha at time n,
  * backward-Euler exchange and flux source (tridiagonal WB solves along each

@@ -1267,7 +1267,6 @@ m1_status m1_set_source(m1_ctx* ctx, const double* S, m1_mem mem) {
 
 m1_status m1_set_velocity(m1_ctx* ctx, const double* ux, const double* uy, const double* uz, m1_mem mem) {
     if (!ctx) return M1_ERR_ARG;
-    if (!ctx->d.gas_coupling) return fail(ctx, M1_ERR_ARG, "advection needs gas coupling");
     const double* u[3] = {ux, uy, uz};
     for (int a = 0; a < ctx->dim; ++a) {
         if (!u[a]) return fail(ctx, M1_ERR_ARG, "a velocity component is missing");
@@ -1280,6 +1279,7 @@ m1_status m1_set_velocity(m1_ctx* ctx, const double* ux, const double* uy, const
 m1_status m1_advect(m1_ctx* ctx, double dt) {
     if (!ctx) return M1_ERR_ARG;
     if (!(dt > 0.0)) return fail(ctx, M1_ERR_ARG, "dt must be positive");
+    if (!ctx->d.gas_coupling) return fail(ctx, M1_ERR_ARG, "advection needs gas coupling");
     if (!ctx->vel[0]) return fail(ctx, M1_ERR_STATE, "no velocity: call m1_set_velocity");
     CKS(prepare(ctx));
     Dev<double> g = dev64(ctx, dt);
@@ -1291,6 +1291,22 @@ m1_status m1_advect(m1_ctx* ctx, double dt) {
         count(ctx, 1);
     }
     CK(cudaMemcpyAsync(Tn, Tnew, sizeof(double) * ctx->N, cudaMemcpyDeviceToDevice, ctx->s));
+    ctx->dirty = true;
+    return sync(ctx);
+}
+
+m1_status m1_velocity_sources(m1_ctx* ctx, double dt) {
+    if (!ctx) return M1_ERR_ARG;
+    if (!(dt > 0.0)) return fail(ctx, M1_ERR_ARG, "dt must be positive");
+    if (!ctx->vel[0]) return fail(ctx, M1_ERR_STATE, "no velocity: call m1_set_velocity");
+    CKS(prepare(ctx));
+    const Dev<double> g = dev64(ctx, dt);
+    {
+        TK t(ctx, M1_K_EXPLICIT);
+        launch_velocity_sources(g, ctx->vel, ctx->Unew, ctx->s);
+        count(ctx, 1);
+    }
+    CK(cudaMemcpyAsync(ctx->Un, ctx->Unew, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s));
     ctx->dirty = true;
     return sync(ctx);
 }

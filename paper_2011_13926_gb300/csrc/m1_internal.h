@@ -127,6 +127,8 @@ void launch_wb_lines(const Dev<double>& g, int b, const double* Fstar, double* F
                      cudaStream_t s);
 int stencil_blocks(long long N);
 // upwind transport of rho c_v T by face velocities u[a] (gas coupling): T* into Tout
+// the explicit velocity-dependent radiation sources of the current state into Uout
+void launch_velocity_sources(const Dev<double>& g, const double* const u[3], double* Uout, cudaStream_t s);
 void launch_advect(const Dev<double>& g, const double* const u[3], double* Tout, cudaStream_t s);
 
 // ----------------------------------------------------------------- Arnoldi (m1_arnoldi.cu)

@@ -891,6 +891,69 @@ void launch_advect(const Dev<double>& g, const double* const u[3], double* Tout,
     }
 }
 
+// Explicit velocity-dependent radiation sources over dt (Sect. 2.1, first order
+// in u/c; step 3 of the splitting of Sect. 2.3): with the cell velocity u the
+// mean of its two face velocities, the closure pressure P of the current state,
+// B = a_r T^4 (gas) or the frozen emission and sigma the flux opacity,
+//   S_E = (sigma/c) u.F + (sigma/c) E |u|^2 + (sigma/c) u.(P u)
+//   S_F = sigma P u + sigma B u + (sigma/c^2) u (u.F)
+//   E' = E + dt S_E, F' = F + c dt S_F, rho c_v T' = rho c_v T - dt S_E (gas).
+template <int DIM, bool GAS>
+__global__ void k_velocity_sources(Dev<double> g, const double* __restrict__ u0, const double* __restrict__ u1,
+                                   const double* __restrict__ u2, double* __restrict__ Uout) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    const long long N = g.N;
+    int coord[3];
+    cell_coord(idx, g.n[0], g.n[1], coord);
+    const double* uf[3] = {u0, u1, u2};
+    double u[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+        u[a] = 0.5 * (uf[a][face_index(g.n, coord, a, coord[a])] + uf[a][face_index(g.n, coord, a, coord[a] + 1)]);
+    St<double, DIM> st;
+    st.E = g.Un[idx];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) st.F[b] = g.Un[(1 + b) * N + idx];
+    st.T = GAS ? g.Un[(1 + DIM) * N + idx] : 0.0;
+    const Cl<double, DIM> k = closure(st, g.c);
+    double Pu[DIM], uF = 0.0, uu = 0.0, uPu = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        double t = 0.0;
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) t += pressure(k, a, b) * u[b];
+        Pu[a] = t;
+        uF += u[a] * st.F[a];
+        uu += u[a] * u[a];
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) uPu += u[a] * Pu[a];
+    const double c = g.c, dt = g.dt, sig = g.sig_f[idx];
+    double B;
+    if constexpr (GAS) {
+        const double T2 = st.T * st.T;
+        B = g.a_r * (T2 * T2);
+    } else {
+        B = g.B ? g.B[idx] : 0.0;
+    }
+    const double SE = (sig / c) * uF + (sig / c) * st.E * uu + (sig / c) * uPu;
+    Uout[idx] = st.E + dt * SE;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const double SF = sig * Pu[a] + sig * B * u[a] + (sig / (c * c)) * u[a] * uF;
+        Uout[(1 + a) * N + idx] = st.F[a] + c * dt * SF;
+    }
+    if constexpr (GAS) Uout[(1 + DIM) * N + idx] = st.T - dt * SE / g.rho_cv[idx];
+}
+
+void launch_velocity_sources(const Dev<double>& g, const double* const u[3], double* Uout, cudaStream_t s) {
+    const int nb = stencil_blocks(g.N);
+#define CALL(D, G) k_velocity_sources<D, G><<<nb, kThreads, 0, s>>>(g, u[0], u[1], u[2], Uout)
+    M1_DISPATCH(g.dim, g.gas, CALL);
+#undef CALL
+}
+
 // One thread per grid line along axis b: solve (I + c dt W_b) F_b = F*_b, the
 // Appendix B tridiagonal form with r_{j+1/2} = c sigma_{j+1/2} dt / 4 (interior
 // faces), Eq. (boundaryCondition) at time n on non-periodic boundary faces (or

@@ -179,6 +179,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_batch_num_classes": (I, [P]),
         "m1_batch_last_error": (C.c_char_p, [P]),
         "m1_advect": (I, [P, D]),
+        "m1_velocity_sources": (I, [P, D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -406,6 +407,10 @@ class Context:
 
     def advect(self, dt: float):
         self._call("m1_advect", C.c_double(dt))
+
+    def velocity_sources(self, dt: float):
+        """Apply the explicit velocity-dependent radiation sources over dt to the state."""
+        self._call("m1_velocity_sources", C.c_double(dt))
 
     def set_preconditioner(self, net):
         self._call("m1_set_preconditioner", net.h if net is not None else None)

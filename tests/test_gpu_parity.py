@@ -245,6 +245,29 @@ def test_advection(m1mod, name):
     assert np.abs(T - ref.ravel()).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("name", ["slab1d", "beam2d", "gas2d_frozen", "gas3d"])
+def test_velocity_sources(m1mod, name):
+    # explicit velocity-dependent sources (c = 1, |u| up to 0.3 c to exercise every term)
+    p = CASES[name]()
+    rng = np.random.default_rng(13)
+    u = []
+    for a in range(p.dim):
+        shp = list(p.shape)
+        shp[p.dim - 1 - a] += 1
+        u.append(rng.uniform(-0.3, 0.3, shp))
+    ref = Scheme(p).velocity_sources(u)
+    ctx = ctx_for(m1mod, p)
+    ctx.set_velocity(*[np.ascontiguousarray(x).ravel() for x in u])
+    ctx.velocity_sources(p.dt)
+    E, F, T = ctx.get_state()
+    scale_E = np.abs(ref[0]).max()
+    assert np.abs(E - ref[0].ravel()).max() <= 1e-12 * scale_E
+    Fr = np.stack([np.asarray(x).ravel() for x in ref[1:1 + p.dim]])
+    assert np.abs(np.asarray(F).reshape(p.dim, -1) - Fr).max() <= 1e-12 * p.c * scale_E
+    if p.gas:
+        assert np.abs(T - ref[1 + p.dim].ravel()).max() <= 1e-12 * np.abs(ref[1 + p.dim]).max()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_krylov_is_deterministic(m1mod, prec):
     # fixed-order reductions: the same solve twice gives bit-identical results
