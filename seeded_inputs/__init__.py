@@ -245,6 +245,78 @@ def beam_lognormal_2d(nx: int = 1024, ny: Optional[int] = None, seed: int = 2,
     return p
 
 
+def beam_45_2d(n: int = 128, fixed_eigs: bool = False) -> Problem:
+    """The 2D beam verification problem of Sect. 5.3 in code units (c = a_r = 1).
+
+    Domain [-1, 1]^2, n x n cells, sigma = 0. Background T = 300 K, F = 0, scaled
+    to E = 1; the beam has T = 1000 K, so E = (1000/300)^4, with |F| = cE at 45
+    degrees. It enters through x = -1 for y in [-0.875, -0.75] (8 cells at
+    n = 128). The rest of the x = -1 side is a background ghost (E = 1, F = 0);
+    the other sides are outflow. With sigma = 0 neither the asymptotic
+    correction nor the well-balanced source act, so the WB boundary closure is
+    off. dt is the explicit CFL step (the semi-implicit scheme).
+    """
+    p = make_problem(2, (n, n), lo=[-1.0, -1.0], hi=[1.0, 1.0],
+                     bc=[("dirichlet", "outflow"), ("outflow", "outflow")],
+                     E=np.ones((n, n)), dt_factor=1.0,
+                     name=f"beam_45_2d_{n}_{'fixed' if fixed_eigs else 'computed'}")
+    p.B = np.ones(p.shape)
+    p.fixed_eigs = fixed_eigs
+    p.wb_boundary = False
+    p.implicit_eigs = False
+    y = p.centers(1)
+    inside = (y >= -0.875) & (y <= -0.75)
+    Eb = (1000.0 / 300.0) ** 4
+    Eg = np.where(inside, Eb, 1.0)
+    Fg = np.zeros((2, n))
+    Fg[0] = np.where(inside, p.c * Eb / np.sqrt(2.0), 0.0)
+    Fg[1] = Fg[0].copy()
+    p.boundary[(0, 0)] = (Eg, Fg, np.ones(n, np.uint8))
+    return p
+
+
+def marshak_1d(n: int = 400, ap_correction: bool = True, rho_cv: float = 1.0,
+               sigma_dx: float = 25.0) -> Problem:
+    """The Marshak wave of Sect. 5.1 in code units (c = a_r = 1, domain [0, 1]).
+
+    n cells with sigma dx = ``sigma_dx`` (25 at n = 400, sigma = 1e4), gas coupled
+    with constant rho c_v, initial equilibrium T = T_r = 0.3 (300 K scaled by
+    1000 K), F = 0. The left side is a Dirichlet ghost at T_r = 1 (E = 1, F = 0),
+    the right side outflow. The paper's cgs values (rho c_v = 1 J/K/cm^3,
+    sigma = 1e4 /cm) would move the front far less than one cell by its t_f; with
+    rho c_v = 1 in code units the front crosses about two thirds of the domain by
+    t = 3000. Wave speeds frozen at time n. ``dt`` holds the first step of
+    ``marshak_schedule``.
+    """
+    p = make_problem(1, (n,), bc=[("dirichlet", "outflow")], gas=True, dt=1.0,
+                     name=f"marshak_1d_{n}_{'ap' if ap_correction else 'hll'}")
+    T0 = 0.3
+    p.E = np.full(p.shape, p.a_r * T0 ** 4)
+    p.F = np.zeros((1, n))
+    p.T = np.full(p.shape, T0)
+    p.rho_cv = np.full(p.shape, float(rho_cv))
+    p.sigma_a = np.full(p.shape, sigma_dx / p.dx[0])
+    p.sigma_f = p.sigma_a.copy()
+    p.boundary[(0, 0)] = (np.array(p.a_r * 1.0 ** 4), np.array([0.0]), np.array(1, np.uint8))
+    p.ap_correction = ap_correction
+    p.implicit_eigs = False
+    p.dt = marshak_schedule()[0]
+    return p
+
+
+def marshak_schedule(t_end: float = 3000.0, dt0: float = 0.01, dt_max: float = 10.0,
+                     growth: float = 1.2) -> List[float]:
+    """Time steps of the Marshak run: from dt0, growing by ``growth`` per step up to
+    dt_max, the last one cut to end at t_end (the source is switched on at t = 0)."""
+    dts, t, d = [], 0.0, dt0
+    while t < t_end * (1.0 - 1e-12):
+        d = min(d, t_end - t)
+        dts.append(d)
+        t += d
+        d = min(d * growth, dt_max)
+    return dts
+
+
 def gaussian_lognormal_2d(n: int, seed: int, span=(1e-2, 1e3), dt_factor: float = 50.0,
                           ell: Optional[float] = None, center=None) -> Problem:
     """2D radiation-only problem with a Gaussian E pulse in a lognormal opacity

@@ -78,3 +78,24 @@ def cases():
         "gas3d": gas_3d,
         "gas2d_frozen": gas_2d,
     }
+
+
+def midheight_fwhm(E2d: np.ndarray) -> int:
+    """Width in cells of a beam in a horizontal cut at mid-height (Sect. 5.3):
+    the cut is the mean of the two rows next to y = 0; the width counts the cells
+    whose excess over the background E = 1 is above half the cut's peak excess."""
+    ny = E2d.shape[0]
+    ex = 0.5 * (E2d[ny // 2 - 1] + E2d[ny // 2]) - 1.0
+    return int((ex > 0.5 * ex.max()).sum())
+
+
+def beam_45_oracle(n: int, fixed_eigs: bool, t_end: float):
+    """March the oracle's semi-implicit step on the Sect. 5.3 beam to t_end;
+    returns the problem holding the final state."""
+    from oracle import Scheme
+    p = si.beam_45_2d(n, fixed_eigs)
+    for _ in range(int(round(t_end / p.dt))):
+        out = Scheme(p).explicit_step()
+        p.E = out[0]
+        p.F = np.stack(out[1:3])
+    return p

@@ -473,3 +473,23 @@ def test_velocity_sources_rotate_with_the_state():
     np.testing.assert_allclose(out2[0], out1[0], rtol=1e-14)
     np.testing.assert_allclose(out2[1], -out1[2], rtol=1e-13)
     np.testing.assert_allclose(out2[2], out1[1], rtol=1e-13)
+
+
+def test_beam_widths_sect53():
+    # Sect. 5.3: the 128^2 beam at 45 degrees enters over 8 cells; at mid-height it
+    # is about 24 cells wide with computed eigenvalues and about 30 with fixed +-c.
+    # Width here is the FWHM of the horizontal cut (a reading: the paper gives no
+    # definition); the oracle gives 22 and 27. The ordering and the ratio are the
+    # method's; each width is held to 15 % of the paper's value.
+    import json, os
+    from tests.m1_cases import beam_45_oracle, midheight_fwhm
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    w = gold["beam_width_cells"]
+    p = si.beam_45_2d(128)
+    assert int(((p.boundary[(0, 0)][0]) > 1.0).sum()) == w["inflow"]
+    wc = midheight_fwhm(beam_45_oracle(128, False, 4.0).E)
+    wf = midheight_fwhm(beam_45_oracle(128, True, 4.0).E)
+    assert wc < wf
+    assert abs(wc - w["computed_eigs_mid"]) <= 0.15 * w["computed_eigs_mid"], wc
+    assert abs(wf - w["fixed_eigs_mid"]) <= 0.15 * w["fixed_eigs_mid"], wf
+    assert 1.1 <= wf / wc <= 1.4
