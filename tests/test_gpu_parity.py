@@ -297,3 +297,33 @@ def test_implicit_step_bicgstab(m1mod, prec, pc):
     assert np.linalg.norm(s.residual(u)) <= 1e-8 * ref.res0
     errs = rel_by_component(u, ref.u, s.nu, s.N)
     assert max(errs[:1 + p.dim]) < 1e-7, errs
+
+
+@pytest.mark.parametrize("fixed_eigs", [False, True])
+def test_beam_45_sect53(m1mod, fixed_eigs):
+    # The Sect. 5.3 beam (128^2, sigma = 0, 45 degrees) marched with the GPU's
+    # semi-implicit step: 64 steps against the oracle's march (1e-8 per field: the
+    # beam has f = 1, where the eigenvalues go as sqrt(1 - f), so rounding
+    # differences of eps in f become sqrt(eps) in lambda and are carried on),
+    # then to steady state, where the mid-height width (FWHM) matches the oracle's
+    # (22 cells with computed eigenvalues, 27 with fixed +-c; paper 24 and 30).
+    from tests.m1_cases import beam_45_oracle, midheight_fwhm
+    n = 128
+    p = si.beam_45_2d(n, fixed_eigs)
+    ctx = ctx_for(m1mod, p)
+    for _ in range(64):
+        ctx.explicit_step(p.dt)
+    ref = beam_45_oracle(n, fixed_eigs, 64 * p.dt)
+    E, F, _ = ctx.get_state()
+    N = p.ncell
+    assert np.abs(E - ref.E.ravel()).max() <= 1e-8 * np.abs(ref.E).max()
+    for b in range(2):
+        assert np.abs(F[b * N:(b + 1) * N] - ref.F[b].ravel()).max() <= 1e-8 * p.c * np.abs(ref.E).max()
+    widths, done = [], 64
+    for t_end in (4.0, 5.0):
+        for _ in range(int(round(t_end / p.dt)) - done):
+            ctx.explicit_step(p.dt)
+        done = int(round(t_end / p.dt))
+        widths.append(midheight_fwhm(ctx.get_state()[0].reshape(n, n)))
+    assert widths[0] == widths[1]  # steady at mid-height
+    assert widths[1] == (27 if fixed_eigs else 22)
