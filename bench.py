@@ -46,6 +46,8 @@ def args_():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--precond", default="mg", choices=["mg", "bj"],
                     help="preconditioner of the headline path (the plain FP64 path uses point-block Jacobi)")
+    ap.add_argument("--newton", default="full", choices=["full", "backtrack"],
+                    help="full Newton steps, or Armijo backtracking (halving theta up to 6 times)")
     ap.add_argument("--plain-steps", type=int, default=1, help="timed plain-FP64 steps beside the headline")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps run after the timed region with per-kernel-class event timers")
@@ -146,7 +148,7 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_oracle_sample(n, dtf, steps=1):
+def cpu_oracle_sample(n, dtf, steps=1, line_search=False):
     """The oracle as it stands on a bounded sample: full implicit steps of the
     same recipe on an n x n grid (numpy, one host core for the stencil work)."""
     from oracle import Scheme, newton_solve
@@ -154,7 +156,7 @@ def cpu_oracle_sample(n, dtf, steps=1):
     t0 = time.perf_counter()
     conv = True
     for _ in range(steps):
-        r = newton_solve(Scheme(p), rtol=1e-8)
+        r = newton_solve(Scheme(p), rtol=1e-8, line_search=line_search)
         conv = conv and r.converged
     dt = time.perf_counter() - t0
     return {"value": p.ncell * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -167,10 +169,11 @@ def run_reference(a):
     if rank != 0:
         return
     n = a.cpu_sample_n
+    ls = a.newton == "backtrack"
     for _ in range(a.warmup):
-        cpu_oracle_sample(n, a.dt_factor)
+        cpu_oracle_sample(n, a.dt_factor, line_search=ls)
     t0 = time.perf_counter()
-    res = cpu_oracle_sample(n, a.dt_factor, steps=a.steps)
+    res = cpu_oracle_sample(n, a.dt_factor, steps=a.steps, line_search=ls)
     el = time.perf_counter() - t0
     v = res["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
@@ -216,7 +219,10 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     prec = PREC_MIXED if a.precision == "mixed" else PREC_FP64
     use_mg = a.precond == "mg" and prec == PREC_MIXED
-    opts = default_opts(advance=0, precision=prec, precond=PRECOND_MG if use_mg else PRECOND_BJ)
+    ls = int(a.newton == "backtrack")
+    opts = default_opts(advance=0, precision=prec, precond=PRECOND_MG if use_mg else PRECOND_BJ, line_search=ls)
+    # the plain FP64 arm keeps the library defaults (point-block Jacobi, Armijo backtracking): with
+    # full Newton steps its less exact point-block Jacobi solves do not converge in 30 Newton steps
     opts_plain = default_opts(advance=0, precision=PREC_FP64)
 
     def timed_steps(o, k, label):
@@ -260,7 +266,8 @@ def main():
              "ms_per_step": statistics.mean(ms_plain) if ms_plain else None,
              "converged": all(i.converged for i in infos_plain),
              "newton_iters": [i.newton_iters for i in infos_plain],
-             "gmres_iters": [i.gmres_iters for i in infos_plain]}
+             "gmres_iters": [i.gmres_iters for i in infos_plain],
+             "config": "FP64 GMRES(30), point-block Jacobi, Armijo backtracking"}
 
     # roofline of the dominant kernel class over the profiled step(s)
     peak, peak_src = measured_peaks()
@@ -304,7 +311,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = cpu_oracle_sample(a.cpu_sample_n, a.dt_factor)
+        cpu = cpu_oracle_sample(a.cpu_sample_n, a.dt_factor, line_search=a.newton == "backtrack")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -316,7 +323,9 @@ def main():
                            else "FP64 GMRES(30)",
                            "preconditioner": ("aggregation multigrid V(1,1) (Galerkin, damped point-block Jacobi "
                                               "smoothing)" if use_mg else "point-block Jacobi"),
-                           "newton_rtol": 1e-8, "gmres_forcing": 1e-4, "wave_speeds": "frozen at time n",
+                           "newton_rtol": 1e-8, "newton": ("full steps" if a.newton == "full"
+                                                            else "Armijo backtracking"),
+                           "gmres_forcing": 1e-4, "wave_speeds": "frozen at time n",
                            "l2": "256 MiB buffer written between timed steps; basis traffic exceeds L2",
                            "parallelism": f"replicas x{world}"},
                 "converged": converged,
