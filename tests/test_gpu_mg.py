@@ -62,7 +62,8 @@ def test_stencil_levels_match_oracle(m1mod, shape):
         assert _row_rel(got, A) < 2e-5, (lvl, _row_rel(got, A))
 
 
-@pytest.mark.parametrize("shape", [(24, 20), (80, 72), (67, 45)])
+# 2 to 6 levels; (280, 264) runs four tiled coarse levels (140 x 132 down to 18 x 17)
+@pytest.mark.parametrize("shape", [(24, 20), (80, 72), (67, 45), (280, 264)])
 def test_cycle_matches_oracle(m1mod, shape):
     nx, ny = shape
     p = si.beam_lognormal_2d(nx, ny, dt_factor=10.0)
