@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 METRIC = "implicit M1 cell-steps/s at 1e-8 rel. residual: mixed+learned vs plain FP64"
 UNIT = "cell-steps/s"
 L2_FLUSH_BYTES = 256 << 20
+MG_CYCLE_DRAM_BYTES_1024 = 439.2e6
 
 
 def args_():
@@ -289,6 +290,12 @@ def main():
         roof["achieved"] = bytes_map[dom] / (kms[dom] / kcount[dom] / 1e3) / 1e9
     if roof["achieved"] is not None:
         roof["frac"] = roof["achieved"] / peak
+    # DRAM bytes (read + write) of one multigrid cycle on the 1024^2 beam, summed over its 13 launches
+    # from one ncu capture (profiles/multigrid_beam_lognormal_1024_dt10.md); only for that workload
+    if dom == "pc_apply" and use_mg and a.n == 1024 and a.dt_factor == 10.0:
+        roof["traffic"] = MG_CYCLE_DRAM_BYTES_1024
+        roof["traffic_unit"] = "bytes per cycle (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+        roof["algorithmic_bytes"] = bytes_map["pc_apply"]
 
     # end to end through the C ABI with host buffers (H2D inputs, D2H result)
     e2e = None
