@@ -49,6 +49,8 @@ def args_():
                     help="preconditioner of the headline path (the plain FP64 path uses point-block Jacobi)")
     ap.add_argument("--newton", default="full", choices=["full", "backtrack"],
                     help="full Newton steps, or Armijo backtracking (halving theta up to 6 times)")
+    ap.add_argument("--pc-rebuild", type=int, default=1,
+                    help="rebuild the multigrid hierarchy on every k-th Newton step (1: every step)")
     ap.add_argument("--plain-steps", type=int, default=1, help="timed plain-FP64 steps beside the headline")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps run after the timed region with per-kernel-class event timers")
@@ -221,7 +223,8 @@ def main():
     prec = PREC_MIXED if a.precision == "mixed" else PREC_FP64
     use_mg = a.precond == "mg" and prec == PREC_MIXED
     ls = int(a.newton == "backtrack")
-    opts = default_opts(advance=0, precision=prec, precond=PRECOND_MG if use_mg else PRECOND_BJ, line_search=ls)
+    opts = default_opts(advance=0, precision=prec, precond=PRECOND_MG if use_mg else PRECOND_BJ, line_search=ls,
+                        pc_rebuild=a.pc_rebuild)
     # the plain FP64 arm keeps the library defaults (point-block Jacobi, Armijo backtracking): with
     # full Newton steps its less exact point-block Jacobi solves do not converge in 30 Newton steps
     opts_plain = default_opts(advance=0, precision=PREC_FP64)

@@ -92,6 +92,9 @@ typedef struct {
     int advance;          /* 1: on success U^n <- U^{n+1}; 0: keep U^n (result in m1_get_solution) */
     int refine_max;       /* mixed precision: max FP64 refinement sweeps per Newton step (4) */
     int krylov;           /* an m1_krylov value, default M1_KRYLOV_GMRES; the learned preconditioner needs GMRES */
+    int pc_rebuild;       /* M1_PRECOND_MG: rebuild the hierarchy on Newton steps 0, k, 2k, ... of each implicit
+                             step (1, the default: every Newton step; values < 1 act as 1); in between, the
+                             cycle keeps its smoothers and coarse operators and applies the current J on level 0 */
 } m1_solver_opts;
 
 #define M1_HIST 64  /* length of the per-Newton-iteration histories */

@@ -1006,6 +1006,7 @@ void m1_default_opts(m1_solver_opts* o) {
     o->advance = 1;
     o->refine_max = 4;
     o->krylov = M1_KRYLOV_GMRES;
+    o->pc_rebuild = 1;
 }
 
 m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out) {
@@ -1436,9 +1437,10 @@ m1_status m1_diag_blocks(m1_ctx* ctx, double dt, const double* U, double* blocks
     return sync(ctx);
 }
 
+// newton_iter: the Newton step within an implicit step (-1 outside one: always rebuild)
 static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const double* b, double* x,
-                              const m1_solver_opts* o, int* iters, int* refinements, double* bnorm, double* res,
-                              bool* conv) {
+                              const m1_solver_opts* o, int newton_iter, int* iters, int* refinements, double* bnorm,
+                              double* res, bool* conv) {
     const bool learned = o->precond == M1_PRECOND_LEARNED;
     const bool use_mg = o->precond == M1_PRECOND_MG;
     const bool pre = o->precond == M1_PRECOND_BJ || learned || use_mg;
@@ -1476,7 +1478,8 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
             count(ctx, 2);
             ctx->st.precond_builds++;
         }
-        if (use_mg) CKS(build_mg(ctx, g32));
+        const int every = std::max(1, o->pc_rebuild);
+        if (use_mg && (newton_iter < 0 || newton_iter % every == 0)) CKS(build_mg(ctx, g32));
         Ops32 ops32{ctx, g32, ctx->U32, pre};
         ops32.learned = learned;
         ops32.mg = use_mg;
@@ -1514,7 +1517,7 @@ m1_status m1_gmres_solve(m1_ctx* ctx, double dt, const double* U, const double* 
     int it = 0, ref = 0;
     double bn = 0, rs = 0;
     bool conv = false;
-    CKS(linear_solve(ctx, dt, ctx->U, ctx->Rt, ctx->delta, &o, &it, &ref, &bn, &rs, &conv));
+    CKS(linear_solve(ctx, dt, ctx->U, ctx->Rt, ctx->delta, &o, -1, &it, &ref, &bn, &rs, &conv));
     // true residual of the returned x in FP64
     launch_jv_f64(dev64(ctx, dt), ctx->U, ctx->delta, ctx->w, ctx->s);
     launch_axpby_f64(1.0, ctx->Rt, -1.0, ctx->w, ctx->rhs, ctx->n, ctx->s);
@@ -1565,7 +1568,8 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
         int it = 0, ref = 0;
         double bn, rs;
         bool conv;
-        m1_status ls = linear_solve(ctx, dt, ctx->U, ctx->Rt, ctx->delta, &o, &it, &ref, &bn, &rs, &conv);
+        m1_status ls =
+            linear_solve(ctx, dt, ctx->U, ctx->Rt, ctx->delta, &o, inf.newton_iters, &it, &ref, &bn, &rs, &conv);
         inf.gmres_iters += it;
         inf.refinements += ref;
         if (ls != M1_OK) {

@@ -32,9 +32,11 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_default_opts(lib):
-    from paper_2011_13926_gb300 import default_opts
+    from paper_2011_13926_gb300 import default_opts, m1
     o = default_opts()
     assert o.newton_rtol == 1e-8 and o.restart == 30 and o.gmres_rtol == 1e-4 and o.precond == 1
+    # the last fields of the struct: a layout mismatch with include/m1.h would garble them
+    assert o.krylov == m1.KRYLOV_GMRES and o.pc_rebuild == 1 and o.line_search == 1 and o.refine_max == 4
 
 
 @pytest.mark.parametrize("field,value", [("dim", 0), ("dim", 4), ("n", (0, 1, 1)), ("n", (4, 2, 1)),

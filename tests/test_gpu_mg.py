@@ -141,3 +141,23 @@ def test_multigrid_rejects_unsupported(m1mod):
     o = m1mod.default_opts(precision=m1mod.PREC_FP64, precond=m1mod.PRECOND_MG, advance=0)
     st, info = ctx2.implicit_step(p2.dt, o, raise_on_fail=False)
     assert st == m1mod.M1_ERR_ARG
+
+
+def test_implicit_step_with_lagged_multigrid(m1mod):
+    # the hierarchy rebuilt on every third Newton step only: the cycle applies the
+    # current J on level 0 with older smoothers and coarse operators; the step
+    # still meets the FP64 bar
+    p = si.beam_lognormal_2d(64, 48, dt_factor=10.0)
+    s = Scheme(p)
+    ref = newton_solve(s, rtol=1e-10, gmres_rtol=1e-8)
+    ctx = _ctx(m1mod, p)
+    opts = m1mod.default_opts(newton_rtol=1e-10, gmres_rtol=1e-8, advance=0, precision=m1mod.PREC_MIXED,
+                              precond=m1mod.PRECOND_MG, pc_rebuild=3)
+    st, info = ctx.implicit_step(p.dt, opts)
+    assert info.converged
+    u = ctx.get_solution()
+    assert np.linalg.norm(s.residual(u)) <= 1e-8 * ref.res0
+    N = s.N
+    for k in range(1 + p.dim):
+        a, b = u[k * N:(k + 1) * N], ref.u[k * N:(k + 1) * N]
+        assert np.abs(a - b).max() <= 1e-7 * max(np.abs(b).max(), 1e-300)
