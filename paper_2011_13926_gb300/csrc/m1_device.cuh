@@ -84,6 +84,12 @@ template <> struct Tiny<float> {
     static __device__ __forceinline__ float den() { return 1e-30f; }
 };
 
+// 1 / x for a positive wave-speed difference: IEEE division in FP64; in FP32 the
+// hardware reciprocal (__fdividef, within 2 ulp), ample for the FP32 operator
+template <class R> __device__ __forceinline__ R recip_den(R x);
+template <> __device__ __forceinline__ double recip_den<double>(double x) { return 1.0 / x; }
+template <> __device__ __forceinline__ float recip_den<float>(float x) { return __fdividef(1.0f, x); }
+
 // ---------------------------------------------------------------- grid data
 enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2, BC_DIRICHLET = 3 };
 

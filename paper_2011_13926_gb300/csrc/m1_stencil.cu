@@ -241,6 +241,9 @@ __global__ void __launch_bounds__(kTX* kTY)
     const int coord[3] = {ix, iy, 0};
     R sig_self = R(0), sig_nb[2][2], lpf[2][2], lmf[2][2], alf[2][2];
     if (valid) {
+        // the cell's faces: x-faces ix -+ 1/2 at fx, fx + 1 (nx + 1 per row); y-faces
+        // iy -+ 1/2 at fy, fy + nx
+        const long long fx = (long long)iy * (nx + 1) + ix, fy = idx;
         sig_self = g.sig_f[idx];
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(kTX* kTY)
                 else if (periodic)
                     sn = g.sig_f[idx + (side ? -(long long)(g.n[a] - 1) : (long long)(g.n[a] - 1)) * g.stride[a]];
                 sig_nb[a][side] = sn;
-                const long long fidx = face_index(g.n, coord, a, coord[a] + side);
+                const long long fidx = a == 0 ? fx + side : fy + (side ? nx : 0);
                 if (g.fixed_eigs) {
                     lpf[a][side] = g.c;
                     lmf[a][side] = -g.c;
@@ -392,7 +395,7 @@ __global__ void __launch_bounds__(kTX* kTY)
                 const bool boundary = !inside && !periodic;
                 const R lp = lpf[a][side], lm = lmf[a][side];
                 const R den = lp - lm;
-                const R inv = den >= Tiny<R>::den() ? R(1) / den : R(0);
+                const R inv = den >= Tiny<R>::den() ? recip_den<R>(den) : R(0);
                 const R pm = lp * lm * inv;
                 const S FaL = a == 0 ? Lc.Fx : Lc.Fy, FaR = a == 0 ? Rc.Fx : Rc.Fy;
                 const S Fs = (lp * FaL - lm * FaR) * inv + pm * (Rc.E - Lc.E);
