@@ -59,7 +59,13 @@ typedef enum { M1_PREC_FP64 = 0, M1_PREC_MIXED = 1 } m1_precision;
  * paper's BiCGStab (Sect. 3.3.1), right-preconditioned, the recurrence scalars on
  * the device; gmres_max and gmres_rtol bound either. */
 typedef enum { M1_KRYLOV_GMRES = 0, M1_KRYLOV_BICGSTAB = 1 } m1_krylov;
-typedef enum { M1_PRECOND_NONE = 0, M1_PRECOND_BJ = 1, M1_PRECOND_LEARNED = 2, M1_PRECOND_MG = 3 } m1_precond;
+typedef enum {
+    M1_PRECOND_NONE = 0,
+    M1_PRECOND_BJ = 1,
+    M1_PRECOND_LEARNED = 2,
+    M1_PRECOND_MG = 3,
+    M1_PRECOND_LINE = 4
+} m1_precond;
 
 /* Grid and discretisation flags (one context per grid). */
 typedef struct {
@@ -86,7 +92,9 @@ typedef struct {
     double gmres_rtol;    /* 1e-4: forcing term ||J d + R|| <= rtol ||R|| */
     int precision;        /* m1_precision: FP64, or FP32 inner FGMRES under FP64 refinement */
     int precond;          /* m1_precond; M1_PRECOND_LEARNED needs M1_PREC_MIXED and m1_set_preconditioner;
-                             M1_PRECOND_MG needs M1_PREC_MIXED, dim 2 and frozen or fixed wave speeds
+                             M1_PRECOND_LINE (the block-tridiagonal part of J, solved exactly along the
+                             line: J itself on a non-periodic 1D grid) needs dim 1, M1_PREC_FP64 and >= 3
+                             cells; M1_PRECOND_MG needs M1_PREC_MIXED, dim 2 and frozen or fixed wave speeds
                              (see m1_mg_apply) */
     int line_search;      /* 1: halve theta up to 6 times until the Armijo decrease holds */
     int advance;          /* 1: on success U^n <- U^{n+1}; 0: keep U^n (result in m1_get_solution) */

@@ -12,5 +12,5 @@ itself: the whole implicit step at scale (no closed form exists; the pins cover
 each ingredient).
 """
 from .m1 import Closure, Scheme, eigenvalues  # noqa: F401
-from .solvers import (block_jacobi, dense_jacobian, dense_solve, gmres,  # noqa: F401
+from .solvers import (block_jacobi, block_tridiagonal_part, dense_jacobian, dense_solve, gmres,  # noqa: F401
                       newton_solve)

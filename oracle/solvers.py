@@ -203,6 +203,13 @@ def newton_solve(scheme: Scheme, rtol: float = 1e-8, newton_max: int = 30,
     return NewtonResult(u, rn <= rtol * r0, its, git, r0, rn, hist)
 
 
+def block_tridiagonal_part(J: np.ndarray, nu: int, N: int) -> np.ndarray:
+    """The couplings of a 1D dense Jacobian (unknowns [k N + i]) between cells i and j
+    with |i - j| <= 1, no periodic wrap: the matrix the line preconditioner solves."""
+    i = np.arange(nu * N) % N
+    return np.where(np.abs(i[:, None] - i[None, :]) <= 1, J, 0.0)
+
+
 def dense_jacobian(scheme: Scheme, u: np.ndarray) -> np.ndarray:
     """J assembled column by column as J e_k (tiny grids only)."""
     n = u.size

@@ -83,6 +83,7 @@ struct m1_ctx {
     MgHierarchy mg;
     bool mg_alloc = false;
     double* mg_inv64 = nullptr;  // FP64 scratch of the block inverses of every level
+    double *line_B = nullptr, *line_M = nullptr, *line_Dinv = nullptr;  // line preconditioner (1D)
     double* bs_part = nullptr;   // BiCGStab: dot-product partials
     double* bs_sc = nullptr;     // BiCGStab: recurrence scalars
     Dev<float> mg_g32{};         // the step's FP32 descriptor the level-0 J v uses
@@ -479,6 +480,20 @@ void mg_apply(m1_ctx* ctx, const float* in, float* out) {
     count(ctx, mg_launches_per_cycle(ctx->mg, op.down0 != nullptr));
 }
 
+// the line preconditioner at U (1D, FP64)
+m1_status build_line(m1_ctx* ctx, const Dev<double>& g, const double* U) {
+    const size_t nu2 = (size_t)ctx->nu * ctx->nu;
+    CKS(dalloc(ctx, &ctx->line_B, 3 * nu2 * ctx->N));
+    CKS(dalloc(ctx, &ctx->line_M, nu2 * ctx->N));
+    CKS(dalloc(ctx, &ctx->line_Dinv, nu2 * ctx->N));
+    TK t(ctx, M1_K_PC_BUILD);
+    CK(cudaMemsetAsync(ctx->singular, 0, sizeof(int), ctx->s));
+    launch_line_build(g, U, ctx->line_B, ctx->line_M, ctx->line_Dinv, ctx->singular, ctx->s);
+    count(ctx, 2);
+    ctx->st.precond_builds++;
+    return M1_OK;
+}
+
 m1_status build_precond(m1_ctx* ctx, const Dev<double>& g, const double* U) {
     TK t(ctx, M1_K_PC_BUILD);
     launch_diag_f64(g, U, ctx->blocks, ctx->s);
@@ -499,6 +514,7 @@ struct Ops64 {
     const double* U;
     bool precond;
     const double* pj = nullptr;  // dP/dU at U: J v as a linear stencil, else by dual numbers
+    bool line = false;           // M^-1: the block-tridiagonal line solve instead of point-block Jacobi
     bool fused() const { return false; }
     void AM(const double*, double*) {}
     void A(const double* in, double* out) {
@@ -512,7 +528,9 @@ struct Ops64 {
     }
     void M(const double* in, double* out) {
         TK t(ctx, M1_K_PC_APPLY);
-        if (precond) {
+        if (line) {
+            launch_line_solve(ctx->nu, ctx->N, ctx->line_B, ctx->line_M, ctx->line_Dinv, in, out, ctx->s);
+        } else if (precond) {
             launch_bj_apply_f64(ctx->nu, ctx->N, ctx->binv, in, out, ctx->s);
         } else {
             cudaMemcpyAsync(out, in, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s);
@@ -1143,7 +1161,8 @@ m1_status m1_destroy(m1_ctx* ctx) {
             if (q) cudaFree(q);
         if (l > 0 && ctx->mg.Dinv[l]) cudaFree(ctx->mg.Dinv[l]);
     }
-    for (void* q : {(void*)ctx->mg.w0, (void*)ctx->mg.probe, (void*)ctx->mg_inv64})
+    for (void* q : {(void*)ctx->mg.w0, (void*)ctx->mg.probe, (void*)ctx->mg_inv64, (void*)ctx->line_B,
+                    (void*)ctx->line_M, (void*)ctx->line_Dinv})
         if (q) cudaFree(q);
     for (int a = 0; a < 3; ++a) {
         void* fp[] = {ctx->f64.alpha[a], ctx->f64.lam_p[a], ctx->f64.lam_m[a],
@@ -1443,7 +1462,10 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
                               double* res, bool* conv) {
     const bool learned = o->precond == M1_PRECOND_LEARNED;
     const bool use_mg = o->precond == M1_PRECOND_MG;
-    const bool pre = o->precond == M1_PRECOND_BJ || learned || use_mg;
+    const bool line = o->precond == M1_PRECOND_LINE;
+    const bool pre = o->precond == M1_PRECOND_BJ || learned || use_mg || line;
+    if (line && (ctx->dim != 1 || o->precision != M1_PREC_FP64 || ctx->N < 3))
+        return fail(ctx, M1_ERR_ARG, "M1_PRECOND_LINE needs dim 1, M1_PREC_FP64 and >= 3 cells");
     if (o->restart < 1 || o->restart > kMaxRestart)
         return fail(ctx, M1_ERR_ARG, "restart must be in [1, 30]");
     if (o->krylov != M1_KRYLOV_GMRES && o->krylov != M1_KRYLOV_BICGSTAB)
@@ -1489,7 +1511,12 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
     }
     CKS(pressure_jacobian64(ctx, g, Ud, &lin));
     if (lin) ops.pj = ctx->pj64;
-    if (pre) CKS(build_precond(ctx, g, Ud));
+    if (line) {
+        CKS(build_line(ctx, g, Ud));
+        ops.line = true;
+    } else if (pre) {
+        CKS(build_precond(ctx, g, Ud));
+    }
     if (o->krylov == M1_KRYLOV_BICGSTAB) {
         double bn;
         CKS(norm_f64(ctx, b, &bn));

@@ -119,6 +119,11 @@ void launch_diag_f32(const Dev<float>& g, const float* U, float* blocks, cudaStr
 void launch_block_inverse_f32(int nu, long long N, const float* blocks, double* binv64, float* binv32,
                               int* singular, cudaStream_t s);
 void launch_bj_apply_f64(int nu, long long N, const double* binv, const double* r, double* z, cudaStream_t s);
+// block-tridiagonal line preconditioner (1D, FP64): blocks 3 n_u^2 N, factors M and D'^-1 n_u^2 N each
+void launch_line_build(const Dev<double>& g, const double* U, double* blocks, double* Mf, double* Dinv,
+                       int* singular, cudaStream_t s);
+void launch_line_solve(int nu, long long N, const double* blocks, const double* Mf, const double* Dinv,
+                       const double* r, double* z, cudaStream_t s);
 void launch_bj_apply_f32(int nu, long long N, const float* binv, const float* r, float* z, cudaStream_t s);
 // semi-implicit step: hyperbolic update + exchange -> Unew (E, T) and Fstar
 void launch_explicit_hyp(const Dev<double>& g, double* Unew, double* Fstar, cudaStream_t s);

@@ -23,7 +23,7 @@ STATUS_NAMES = ["M1_OK", "M1_ERR_ARG", "M1_ERR_CUDA", "M1_ERR_NOMEM", "M1_ERR_NO
 BC = {"outflow": 0, "periodic": 1, "reflect": 2, "dirichlet": 3}
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
-PRECOND_NONE, PRECOND_BJ, PRECOND_LEARNED, PRECOND_MG = 0, 1, 2, 3
+PRECOND_NONE, PRECOND_BJ, PRECOND_LEARNED, PRECOND_MG, PRECOND_LINE = 0, 1, 2, 3, 4
 KRYLOV_GMRES, KRYLOV_BICGSTAB = 0, 1
 
 EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "m1_set_state", "m1_get_state",

@@ -99,3 +99,21 @@ def beam_45_oracle(n: int, fixed_eigs: bool, t_end: float):
         p.E = out[0]
         p.F = np.stack(out[1:3])
     return p
+
+
+def line_case_1d(periodic: bool, gas: bool, n: int = 12, seed: int = 61):
+    """A 1D state away from equilibrium for the line preconditioner (Dirichlet / outflow
+    or periodic, radiation only or with gas), dt = 50 dt_CFL."""
+    rng = np.random.default_rng(seed)
+    bc = [("periodic", "periodic")] if periodic else [("dirichlet", "outflow")]
+    p = si.make_problem(1, (n,), bc=bc, gas=gas, dt_factor=50)
+    p.E = rng.uniform(0.5, 2.0, p.shape)
+    p.F = 0.6 * rng.uniform(-1, 1, (1,) + p.shape) * p.E
+    p.sigma_a = 10.0 ** rng.uniform(-1, 2, p.shape)
+    p.sigma_f = 10.0 ** rng.uniform(-1, 2, p.shape)
+    if gas:
+        p.T = rng.uniform(0.7, 1.3, p.shape)
+        p.rho_cv = rng.uniform(0.5, 2.0, p.shape)
+    if not periodic:
+        p.boundary[(0, 0)] = (np.array(1.5), np.array([0.5]), np.array(1))
+    return p

@@ -327,3 +327,37 @@ def test_beam_45_sect53(m1mod, fixed_eigs):
         widths.append(midheight_fwhm(ctx.get_state()[0].reshape(n, n)))
     assert widths[0] == widths[1]  # steady at mid-height
     assert widths[1] == (27 if fixed_eigs else 22)
+
+
+@pytest.mark.parametrize("periodic,gas,n", [(False, False, 12), (False, True, 12), (True, False, 12),
+                                            (False, False, 300)])
+def test_line_preconditioner_matches_dense_lu(m1mod, periodic, gas, n):
+    # M1_PRECOND_LINE: on a non-periodic 1D grid the preconditioner is J itself, and
+    # GMRES takes one step (two at most: the convergence test runs one step behind)
+    from tests.m1_cases import line_case_1d
+    p = line_case_1d(periodic, gas, n=n)
+    s = Scheme(p)
+    u = perturbed_state(p, 64)
+    b = np.random.default_rng(65).standard_normal(u.size)
+    x_lu = dense_solve(s, u, b)
+    ctx = ctx_for(m1mod, p)
+    opts = m1mod.default_opts(gmres_rtol=1e-13, gmres_max=300, precond=m1mod.PRECOND_LINE)
+    x, info = ctx.gmres_solve(p.dt, b, U=u, opts=opts)
+    assert info.converged
+    assert np.linalg.norm(x - x_lu) <= 1e-10 * np.linalg.norm(x_lu)
+    if not periodic:
+        assert info.iters <= 2, info.iters
+
+
+def test_line_preconditioner_rejects_unsupported(m1mod):
+    from tests.m1_cases import line_case_1d
+    p1 = line_case_1d(False, False)
+    ctx = ctx_for(m1mod, p1)
+    o = m1mod.default_opts(precision=m1mod.PREC_MIXED, precond=m1mod.PRECOND_LINE, advance=0)
+    st, info = ctx.implicit_step(p1.dt, o, raise_on_fail=False)
+    assert st == m1mod.M1_ERR_ARG
+    p2 = si.beam_lognormal_2d(24, 20, dt_factor=10.0)
+    ctx2 = ctx_for(m1mod, p2)
+    o = m1mod.default_opts(precision=m1mod.PREC_FP64, precond=m1mod.PRECOND_LINE, advance=0)
+    st, info = ctx2.implicit_step(p2.dt, o, raise_on_fail=False)
+    assert st == m1mod.M1_ERR_ARG

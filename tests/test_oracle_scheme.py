@@ -493,3 +493,35 @@ def test_beam_widths_sect53():
     assert abs(wc - w["computed_eigs_mid"]) <= 0.15 * w["computed_eigs_mid"], wc
     assert abs(wf - w["fixed_eigs_mid"]) <= 0.15 * w["fixed_eigs_mid"], wf
     assert 1.1 <= wf / wc <= 1.4
+
+
+@pytest.mark.parametrize("gas", [False, True])
+def test_1d_jacobian_is_block_tridiagonal(gas):
+    # the scheme couples a cell to its two neighbours only (HLL faces, WB face
+    # averages, ghosts through the edge cells): on a non-periodic 1D grid the
+    # line preconditioner's matrix is J itself, and GMRES with it takes one step
+    from oracle import block_tridiagonal_part
+    from tests.m1_cases import line_case_1d
+    p = line_case_1d(False, gas)
+    s = Scheme(p)
+    u = s.pack(s.Un)
+    J = dense_jacobian(s, u)
+    T = block_tridiagonal_part(J, s.nu, s.N)
+    assert np.array_equal(T, J)
+    b = np.random.default_rng(63).standard_normal(u.size)
+    res = gmres(lambda v: s.jv(u, v), b, lambda r: np.linalg.solve(T, r), rtol=1e-12, restart=30, maxiter=10)
+    assert res.converged and res.iters == 1
+
+
+def test_periodic_1d_jacobian_differs_by_the_wrap_corners():
+    from oracle import block_tridiagonal_part
+    from tests.m1_cases import line_case_1d
+    p = line_case_1d(True, False)
+    s = Scheme(p)
+    u = s.pack(s.Un)
+    J = dense_jacobian(s, u)
+    D = J - block_tridiagonal_part(J, s.nu, s.N)
+    i = np.arange(s.nu * s.N) % s.N
+    corner = ((i[:, None] == 0) & (i[None, :] == s.N - 1)) | ((i[:, None] == s.N - 1) & (i[None, :] == 0))
+    assert np.all(D[~corner] == 0.0)
+    assert np.abs(D[corner]).max() > 0.0
