@@ -2,13 +2,15 @@
 """Benchmark: implicit grey M1 step throughput (cell-steps/s at 1e-8 relative
 residual) on the 2D radiation-only beam in a lognormal opacity field,
 1024 x 1024 cells, periodic in y / outflow in x, dt = 10 explicit CFL steps
-(the configuration's smallest implicit step; at 50 and 100 the point-block
-Jacobi GMRES(30) inner solves stagnate on this workload).
+(the configuration's smallest implicit step; at 50 dt_CFL the Newton iterates
+leave the realizable set and do not converge, at 100 backtracking converges in
+46 Newton steps).
 
-One step = one backward-Euler M1 step (time-n face data, Newton with the FP64
-residual judge, (F)GMRES(30) with block Jacobi, line search) from the same
-seeded initial state, inputs resident in HBM. The headline path is the FP32
-inner solver under FP64 refinement; the plain FP64 path is measured beside it.
+One step = one backward-Euler M1 step from the same seeded initial state
+(time-n face data, Newton with full steps tested on the FP64 residual, FP32
+GMRES(30) with the multigrid preconditioner under FP64 refinement), inputs
+resident in HBM. The plain FP64 path (point-block Jacobi GMRES(30), Armijo
+backtracking) is measured beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
