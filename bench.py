@@ -166,7 +166,8 @@ def cpu_oracle_sample(n, dtf, steps=1, line_search=False):
     dt = time.perf_counter() - t0
     return {"value": p.ncell * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} implicit step(s) of the same recipe at {n}x{n} (numpy FP64 oracle, "
-                      f"block-Jacobi GMRES(30)+MGS, 1e-8), converged={conv}, {dt:.1f}s"}
+                      f"block-Jacobi GMRES(30)+MGS, {'Armijo backtracking' if line_search else 'full Newton steps'}, "
+                      f"1e-8), converged={conv}, {dt:.1f}s"}
 
 
 def run_reference(a):
