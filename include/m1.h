@@ -96,7 +96,8 @@ typedef struct {
                              line: J itself on a non-periodic 1D grid) needs dim 1, M1_PREC_FP64 and >= 3
                              cells; M1_PRECOND_MG needs M1_PREC_MIXED, dim 2 and frozen or fixed wave speeds
                              (see m1_mg_apply) */
-    int line_search;      /* 1: halve theta up to 6 times until the Armijo decrease holds */
+    int line_search;      /* 1 (default): halve theta up to 6 times until the Armijo decrease holds; 0: full
+                             Newton steps (theta = 1) */
     int advance;          /* 1: on success U^n <- U^{n+1}; 0: keep U^n (result in m1_get_solution) */
     int refine_max;       /* mixed precision: max FP64 refinement sweeps per Newton step (4) */
     int krylov;           /* an m1_krylov value, default M1_KRYLOV_GMRES; the learned preconditioner needs GMRES */
