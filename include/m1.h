@@ -355,9 +355,18 @@ m1_status m1_batch_destroy(m1_batch* b);
 /* Problem k's opacities, time-n state (E: N, F: 2N) and frozen emission (NULL = 0). */
 m1_status m1_batch_set_problem(m1_batch* b, int k, const double* sigma_a, const double* sigma_f, const double* E,
                                const double* F, const double* B, m1_mem mem);
-/* Time each class's persistent launch with CTAs of 128, 256 and 512 threads and
- * keep the fastest (chosen[c] receives it; may be NULL). */
+/* Time each class on the single-grid path and with persistent CTAs of 128, 256
+ * and 512 threads (a size more than 3x slower than the best so far ends the
+ * class's search) and keep the fastest: chosen[c] receives the CTA size, or 0
+ * for the single-grid path (may be NULL). */
 m1_status m1_batch_tune(m1_batch* b, const double* dts, const m1_solver_opts* opts, int* chosen);
+/* Run class c with persistent CTAs of `threads` (128, 256 or 512), or, with
+ * threads = 0, through single-grid contexts one problem after another on a side
+ * stream while the persistent classes run (the default for classes of more than
+ * 128 x 128 cells: one SM per problem is slow there). The single-grid path uses
+ * FP32 inner GMRES under FP64 refinement with the caller's multigrid, else
+ * point-block Jacobi preconditioner. */
+m1_status m1_batch_set_class(m1_batch* b, int c, int threads);
 /* One implicit step of every problem (dts[k]); info[k] per problem (may be
  * NULL); *elapsed_ms = device time of the graph launch (may be NULL). The
  * solutions are read with m1_batch_get_solution; the time-n states are kept. */

@@ -10,6 +10,11 @@
 // nothing to time out. Problems are grouped by size class; each class has its
 // own persistent launch with a CTA size picked by m1_batch_tune, and the
 // launches of all classes run concurrently from one captured CUDA graph.
+// A class can instead run through single-grid contexts, one problem after
+// another on a side stream while the graph runs: one SM per problem is slow
+// for large grids (a 256^2 problem takes seconds on one SM and milliseconds on
+// all of them). Classes above kGridPathCells cells start on that path, and
+// m1_batch_tune times both paths per class.
 //
 // Scope: 2D radiation-only grids (n_u = 3) with periodic, outflow or reflecting
 // boundaries, frozen (time-n) or fixed wave speeds.
@@ -29,6 +34,7 @@ namespace {
 
 constexpr int kM = kMaxRestart;  // GMRES(m) basis bound
 constexpr int kNU = 3;
+constexpr long long kGridPathCells = 128 * 128;  // larger classes start on the single-grid path
 
 struct Prob {
     Dev<double> g64;
@@ -417,7 +423,11 @@ struct m1_batch {
     int* dorder = nullptr;              // problems ordered by class
     std::vector<int> cls_offset;
     int* dqueue = nullptr;              // one counter per class
-    std::vector<int> bs;                // CTA size per class
+    std::vector<int> bs;                // CTA size per class (persistent path)
+    std::vector<char> on_grid;          // per class: 1 = the single-grid path
+    std::vector<m1_ctx*> gctx;          // per problem: its single-grid context (created on first use)
+    std::vector<m1_batch_problem_info> ginfo;  // per problem: the single-grid path's result
+    cudaStream_t gs = nullptr;          // stream of the single-grid contexts
     std::vector<int> grid;              // persistent CTAs per class
     std::vector<Work*> dworks;          // per class: grid Work slots
     m1_batch_problem_info* dinfo = nullptr;
@@ -633,9 +643,13 @@ m1_status m1_batch_create(int nprob, const m1_grid_desc* descs, void* stream, m1
     for (int q = 0; q < c; ++q) {
         const long long N = B->hp[B->members[q][0]].N;
         B->bs[q] = N <= 16384 ? 256 : 512;
+        B->on_grid.push_back(N > kGridPathCells ? 1 : 0);
         B->grid[q] = std::max(1, std::min((int)B->members[q].size(), nsm));
         if (alloc_works(B, q) != M1_OK) return cleanup(M1_ERR_NOMEM);
     }
+    B->gctx.assign(nprob, nullptr);
+    B->ginfo.assign(nprob, m1_batch_problem_info{});
+    if (cudaStreamCreateWithFlags(&B->gs, cudaStreamNonBlocking) != cudaSuccess) return cleanup(M1_ERR_CUDA);
     B->side.resize(c);
     B->ev.resize(c + 1);
     for (int q = 0; q < c; ++q) cudaStreamCreateWithFlags(&B->side[q], cudaStreamNonBlocking);
@@ -649,7 +663,10 @@ m1_status m1_batch_create(int nprob, const m1_grid_desc* descs, void* stream, m1
 
 m1_status m1_batch_destroy(m1_batch* B) {
     if (!B) return M1_OK;
-    cudaStreamSynchronize(B->s);
+    if (B->s) cudaStreamSynchronize(B->s);
+    for (m1_ctx* x : B->gctx)
+        if (x) m1_destroy(x);
+    if (B->gs) cudaStreamDestroy(B->gs);
     if (B->exec) cudaGraphExecDestroy(B->exec);
     for (auto s : B->side) cudaStreamDestroy(s);
     for (auto e : B->ev) cudaEventDestroy(e);
@@ -676,8 +693,12 @@ m1_status m1_batch_set_problem(m1_batch* B, int k, const double* sigma_a, const 
 }
 
 static m1_status run(m1_batch* B, const Opts& o, bool use_graph) {
+    bool any = false;
+    for (int c = 0; c < B->ncls; ++c) any = any || !B->on_grid[c];
+    if (!any) return M1_OK;
     if (!use_graph) {
-        for (int c = 0; c < B->ncls; ++c) launch_class(B, c, o, B->s);
+        for (int c = 0; c < B->ncls; ++c)
+            if (!B->on_grid[c]) launch_class(B, c, o, B->s);
         return cudaGetLastError() == cudaSuccess ? M1_OK : bfail(B, M1_ERR_CUDA, "launch failed");
     }
     const bool same = B->have_graph && memcmp(&B->graph_opts, &o, sizeof(Opts)) == 0;
@@ -691,6 +712,7 @@ static m1_status run(m1_batch* B, const Opts& o, bool use_graph) {
         if (e0 != cudaSuccess) return bfail(B, M1_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e0));
         cudaEventRecord(B->ev[B->ncls], B->s);
         for (int c = 0; c < B->ncls; ++c) {
+            if (B->on_grid[c]) continue;
             cudaStreamWaitEvent(B->side[c], B->ev[B->ncls], 0);
             launch_class(B, c, o, B->side[c]);
             cudaEventRecord(B->ev[c], B->side[c]);
@@ -709,6 +731,47 @@ static m1_status run(m1_batch* B, const Opts& o, bool use_graph) {
         B->have_graph = true;
     }
     return cudaGraphLaunch(B->exec, B->s) == cudaSuccess ? M1_OK : bfail(B, M1_ERR_CUDA, "graph launch failed");
+}
+
+// problem k through its single-grid context on B->gs: the batch's time-n data
+// (device) in, one implicit step (FP32 inner GMRES under FP64 refinement, the
+// caller's multigrid or else point-block Jacobi), the solution into P.U
+static m1_status grid_solve(m1_batch* B, int k, const m1_solver_opts* so) {
+    Prob& P = B->hp[k];
+    if (!B->gctx[k] && m1_init_grid(&B->descs[k], (void*)B->gs, &B->gctx[k]) != M1_OK)
+        return bfail(B, M1_ERR_NOMEM, "single-grid context");
+    m1_ctx* x = B->gctx[k];
+    const Dev<double>& g = P.g64;
+    m1_status st = m1_set_opacity(x, g.sig_a, g.sig_f, M1_MEM_DEVICE);
+    if (st == M1_OK) st = m1_set_state(x, g.Un, g.Un + P.N, nullptr, nullptr, M1_MEM_DEVICE);
+    if (st == M1_OK) st = m1_set_emission(x, g.B, M1_MEM_DEVICE);
+    if (st != M1_OK) return bfail(B, st, m1_last_error(x));
+    m1_solver_opts o;
+    m1_default_opts(&o);
+    if (so) o = *so;
+    o.advance = 0;
+    o.precision = M1_PREC_MIXED;
+    if (o.precond != M1_PRECOND_MG) o.precond = M1_PRECOND_BJ;
+    o.krylov = M1_KRYLOV_GMRES;
+    m1_step_info info{};
+    st = m1_implicit_step(x, P.dt, &o, &info);
+    m1_batch_problem_info& bi = B->ginfo[k];
+    bi.converged = info.converged;
+    bi.newton_iters = info.newton_iters;
+    bi.gmres_iters = info.gmres_iters;
+    bi.res0 = info.res0;
+    bi.res = info.res;
+    if (st != M1_OK && st != M1_ERR_NOT_CONVERGED) return bfail(B, st, m1_last_error(x));
+    if (st == M1_ERR_NOT_CONVERGED) return M1_OK;  // reported through info, as on the persistent path
+    return m1_get_solution(x, P.U, M1_MEM_DEVICE) == M1_OK ? M1_OK : bfail(B, M1_ERR_CUDA, m1_last_error(x));
+}
+
+static m1_status grid_class(m1_batch* B, int c, const m1_solver_opts* so) {
+    for (int k : B->members[c]) {
+        const m1_status st = grid_solve(B, k, so);
+        if (st != M1_OK) return st;
+    }
+    return M1_OK;
 }
 
 static Opts to_opts(const m1_solver_opts* so) {
@@ -743,17 +806,30 @@ m1_status m1_batch_implicit_step(m1_batch* B, const double* dts, const m1_solver
     cudaEventCreate(&e1);
     cudaEventRecord(e0, B->s);
     m1_status st = run(B, to_opts(so), true);
+    // the single-grid classes on their own stream, concurrently with the graph
+    cudaStreamWaitEvent(B->gs, e0, 0);
+    for (int c = 0; c < B->ncls && st == M1_OK; ++c)
+        if (B->on_grid[c]) st = grid_class(B, c, so);
+    cudaEvent_t eg;
+    cudaEventCreateWithFlags(&eg, cudaEventDisableTiming);
+    cudaEventRecord(eg, B->gs);
+    cudaStreamWaitEvent(B->s, eg, 0);
     cudaEventRecord(e1, B->s);
     if (cudaStreamSynchronize(B->s) != cudaSuccess) st = bfail(B, M1_ERR_CUDA, "batched solve failed");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(eg);
     if (elapsed_ms) *elapsed_ms = ms;
     if (st != M1_OK) return st;
-    if (info &&
-        cudaMemcpy(info, B->dinfo, sizeof(m1_batch_problem_info) * B->nprob, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return bfail(B, M1_ERR_CUDA, "copy failed");
+    if (info) {
+        if (cudaMemcpy(info, B->dinfo, sizeof(m1_batch_problem_info) * B->nprob, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return bfail(B, M1_ERR_CUDA, "copy failed");
+        for (int k = 0; k < B->nprob; ++k)
+            if (B->on_grid[B->cls[k]]) info[k] = B->ginfo[k];
+    }
     return M1_OK;
 }
 
@@ -783,6 +859,19 @@ m1_status m1_batch_tune(m1_batch* B, const double* dts, const m1_solver_opts* so
     for (int c = 0; c < B->ncls; ++c) {
         float best = 1e30f;
         int bbest = B->bs[c];
+        bool grid_best = false;
+        {  // the single-grid path
+            cudaEventRecord(e0, B->gs);
+            const m1_status st = grid_class(B, c, so);
+            cudaEventRecord(e1, B->gs);
+            if (st != M1_OK || cudaStreamSynchronize(B->gs) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st != M1_OK ? st : bfail(B, M1_ERR_CUDA, "tuning run failed");
+            }
+            cudaEventElapsedTime(&best, e0, e1);
+            grid_best = true;
+        }
         for (int bs : cand) {
             B->bs[c] = bs;
             cudaEventRecord(e0, B->s);
@@ -798,14 +887,28 @@ m1_status m1_batch_tune(m1_batch* B, const double* dts, const m1_solver_opts* so
             if (ms < best) {
                 best = ms;
                 bbest = bs;
+                grid_best = false;
+            } else if (ms > 3.f * best) {
+                break;  // far behind the best: the other CTA sizes will not close the gap
             }
         }
         B->bs[c] = bbest;
-        if (chosen) chosen[c] = bbest;
+        B->on_grid[c] = grid_best ? 1 : 0;
+        if (chosen) chosen[c] = grid_best ? 0 : bbest;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     B->have_graph = false;  // re-capture with the chosen sizes
+    return M1_OK;
+}
+
+m1_status m1_batch_set_class(m1_batch* B, int c, int threads) {
+    if (!B || c < 0 || c >= B->ncls) return M1_ERR_ARG;
+    if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
+        return bfail(B, M1_ERR_ARG, "threads must be 0, 128, 256 or 512");
+    B->on_grid[c] = threads == 0 ? 1 : 0;
+    if (threads) B->bs[c] = threads;
+    B->have_graph = false;
     return M1_OK;
 }
 

@@ -33,7 +33,8 @@ EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "
             "m1_nn_destroy", "m1_nn_set_params", "m1_nn_get_params", "m1_nn_forward", "m1_nn_loss_grad",
             "m1_nn_train", "m1_nn_last_error", "m1_nn_make_pair", "m1_set_preconditioner", "m1_set_velocity",
             "m1_advect", "m1_batch_create", "m1_batch_destroy", "m1_batch_set_problem", "m1_batch_tune",
-            "m1_batch_implicit_step", "m1_batch_get_solution", "m1_batch_num_classes", "m1_batch_last_error"]
+            "m1_batch_implicit_step", "m1_batch_get_solution", "m1_batch_num_classes", "m1_batch_last_error",
+            "m1_batch_set_class"]
 
 
 class GridDesc(C.Structure):
@@ -177,6 +178,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_batch_implicit_step": (I, [P, P, C.POINTER(SolverOpts), P, C.POINTER(D)]),
         "m1_batch_get_solution": (I, [P, I, P, I]),
         "m1_batch_num_classes": (I, [P]),
+        "m1_batch_set_class": (I, [P, I, I]),
         "m1_batch_last_error": (C.c_char_p, [P]),
         "m1_advect": (I, [P, D]),
         "m1_velocity_sources": (I, [P, D]),
@@ -615,6 +617,10 @@ class Batch:
 
     def num_classes(self) -> int:
         return int(self.lib.m1_batch_num_classes(self.h))
+
+    def set_class(self, c: int, threads: int):
+        """Class c on persistent CTAs of `threads` (128, 256, 512), or 0: the single-grid path."""
+        self._call("m1_batch_set_class", int(c), int(threads))
 
     def tune(self, dts, opts=None):
         d = np.ascontiguousarray(dts, dtype=np.float64)
