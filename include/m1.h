@@ -340,7 +340,10 @@ m1_status m1_set_preconditioner(m1_ctx* ctx, m1_nn* nn);
  * persistent launch per size class, all classes replayed from one CUDA graph.
  * Each CTA takes problems from a device work queue and runs a whole
  * backward-Euler step (Newton, FP32 GMRES under FP64 refinement, point-block
- * Jacobi, line search) with CTA-wide barriers only.
+ * Jacobi, line search) with CTA-wide barriers only. Classes of more than
+ * 128 x 128 cells (or any class, see m1_batch_set_class and m1_batch_tune) run
+ * instead through single-grid contexts, one problem after another on a side
+ * stream, concurrently with the graph.
  * ------------------------------------------------------------------------- */
 typedef struct m1_batch m1_batch;
 
