@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(Dev<double> g, const doub
 
 // ------------------------------------------------------------------ J v
 template <class R, int DIM, bool GAS>
-__global__ void __launch_bounds__(kThreads) k_jv(Dev<R> g, const R* __restrict__ U, const R* __restrict__ v,
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 1) k_jv(Dev<R> g, const R* __restrict__ U, const R* __restrict__ v,
                                                  R* __restrict__ Jv) {
     constexpr int NU = 1 + DIM + (GAS ? 1 : 0);
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
