@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 METRIC = "implicit M1 cell-steps/s at 1e-8 rel. residual: mixed+learned vs plain FP64"
 UNIT = "cell-steps/s"
 L2_FLUSH_BYTES = 256 << 20
-MG_CYCLE_DRAM_BYTES_1024 = 439.2e6
+MG_CYCLE_DRAM_BYTES_1024 = 439.6e6
 
 
 def args_():
