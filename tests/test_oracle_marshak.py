@@ -7,7 +7,9 @@ that the Marshak wave of Sect. 5.1 is measured against (CPU only).
   left face (the right face is closed);
 * one very long step reaches the uniform steady state T = T_b;
 * the Marshak problem and its step schedule as the paper states them (400 cells,
-  sigma dx = 25, 300 K / 1000 K).
+  sigma dx = 25, 300 K / 1000 K);
+* the oracle's M1 scheme on a coarse Marshak wave: the asymptotic-preserving alpha
+  within 3 % of the diffusion reference, plain HLL off by more than 50 % (Sect. 5.1).
 """
 import numpy as np
 import pytest
@@ -61,3 +63,27 @@ def test_marshak_problem_as_stated():
     dts = si.marshak_schedule()
     assert sum(dts) == pytest.approx(3000.0, rel=1e-12)
     assert max(dts) == 10.0 and dts[0] == 0.01
+
+
+def test_marshak_oracle_ap_against_hll_sect51():
+    # Sect. 5.1 on a coarse grid with the paper's sigma dx = 25 (64 cells, t_end = 480 so that
+    # the front crosses about half the domain): the asymptotic-preserving alpha follows the
+    # diffusion limit (relative L2 error of T about 1 %; paper 1.1 % at 400 cells), plain HLL
+    # does not (about 81 %; paper 84 %)
+    from oracle import Scheme, newton_solve
+    dts = si.marshak_schedule(t_end=480.0)
+    p0 = si.marshak_1d(64)
+    ref = diffusion_reference(p0.T, 1.0, p0.sigma_a, float(p0.rho_cv[0]), p0.dx[0], dts)
+    err = {}
+    for ap in (True, False):
+        p = si.marshak_1d(64, ap_correction=ap)
+        for dt in dts:
+            p.dt = dt
+            s = Scheme(p)
+            r = newton_solve(s, rtol=1e-6, gmres_rtol=1e-4, line_search=False)
+            assert r.converged
+            N = s.N
+            p.E, p.F, p.T = r.u[:N].copy(), r.u[N:2 * N].reshape(1, N).copy(), r.u[2 * N:].copy()
+        err[ap] = np.linalg.norm(p.T - ref.T) / np.linalg.norm(ref.T)
+    assert err[True] <= 0.03, err
+    assert err[False] >= 0.5, err
