@@ -254,6 +254,7 @@ class Context:
         self.nu = 1 + desc.dim + (1 if desc.gas_coupling else 0)
 
     def close(self):
+        """m1_destroy: free the context's device memory."""
         if getattr(self, "h", None):
             self.lib.m1_destroy(self.h)
             self.h = None
@@ -274,15 +275,18 @@ class Context:
         return getattr(self.lib, name)(self.h, *args)
 
     def last_error(self) -> str:
+        """m1_last_error: the message of the last failed call."""
         return self.lib.m1_last_error(self.h).decode()
 
     # ---------------------------------------------------------------- inputs
     def set_opacity(self, sigma_a, sigma_f=None):
+        """m1_set_opacity: sigma_a (exchange) and sigma_f (flux, alpha; None: sigma_a), N values each."""
         pa, ma, ka = _ptr(sigma_a)
         pf, mf, kf = _ptr(sigma_f)
         self._call("m1_set_opacity", pa, pf, _check_mem(ma, mf if pf else None))
 
     def set_state(self, E, F, T=None, rho_cv=None):
+        """m1_set_state: the time-n state E (N), F (dim x N), and with gas coupling T and rho c_v (N each)."""
         pe, me, ke = _ptr(E)
         pF, mF, kF = _ptr(F)
         pt, mt, kt = _ptr(T)
@@ -291,16 +295,19 @@ class Context:
         self._call("m1_set_state", pe, pF, pt, pr, mem)
 
     def set_boundary(self, axis, side, E, F, mask=None):
+        """m1_set_boundary: Dirichlet ghost data (E, F) of one face and its mask (1: given, 0: zero-gradient)."""
         pe, me, ke = _ptr(E)
         pF, mF, kF = _ptr(F)
         pm, mm, km = _ptr(mask, dtype=np.uint8)
         self._call("m1_set_boundary", axis, side, pe, pF, pm, _check_mem(me, mF, mm if pm else None))
 
     def set_emission(self, B):
+        """m1_set_emission: the frozen emission B = a_r T_g^4 of the radiation-only model (N values)."""
         p, m, k = _ptr(B)
         self._call("m1_set_emission", p, m)
 
     def set_source(self, S):
+        """m1_set_source: the point-source term S added to the energy equation (N values)."""
         p, m, k = _ptr(S)
         self._call("m1_set_source", p, m)
 
@@ -322,6 +329,7 @@ class Context:
         return out
 
     def get_solution(self, out=None):
+        """m1_get_solution: the last implicit step's U^{n+1} as [E, F_0.., (T)] (n_u N values)."""
         if out is None:
             out = np.empty(self.nu * self.N)
         p, m, k = _ptr(out)
@@ -330,9 +338,11 @@ class Context:
 
     # ---------------------------------------------------------------- steps
     def explicit_step(self, dt: float):
+        """m1_explicit_step: one semi-implicit step of size dt (Sect. 3.1); advances the state."""
         self._call("m1_explicit_step", C.c_double(dt))
 
     def implicit_step(self, dt: float, opts: Optional[SolverOpts] = None, raise_on_fail: bool = True):
+        """m1_implicit_step: one backward-Euler step by Newton + Krylov; returns (status, StepInfo)."""
         info = StepInfo()
         o = opts if opts is not None else default_opts()
         st = self.lib.m1_implicit_step(self.h, C.c_double(dt), C.byref(o), C.byref(info))
@@ -341,6 +351,7 @@ class Context:
         return st, info
 
     def residual(self, dt: float, U, out=None):
+        """m1_residual: the FP64 backward-Euler residual R(U) for step dt (time-n data from the state)."""
         pu, mu, ku = _ptr(U)
         if out is None:
             out = np.empty(self.nu * self.N) if mu == MEM_HOST else None
@@ -349,6 +360,7 @@ class Context:
         return out
 
     def jv(self, dt: float, U, v, out=None, precision: int = PREC_FP64):
+        """m1_jv: J(U) v of the residual, in FP64 or with the mixed path's FP32 operator."""
         pu, mu, ku = _ptr(U)
         pv, mv, kv = _ptr(v)
         if out is None:
@@ -358,6 +370,7 @@ class Context:
         return out
 
     def diag_blocks(self, dt: float, U, out=None):
+        """m1_diag_blocks: the point blocks dR_i/dU_i of J(U), n_u^2 N values component-major."""
         pu, mu, ku = _ptr(U)
         if out is None:
             out = np.empty(self.nu * self.nu * self.N)
@@ -376,6 +389,7 @@ class Context:
         return out
 
     def mg_levels(self) -> int:
+        """Number of levels of the multigrid hierarchy last built."""
         n = C.c_int(0)
         self._call("m1_mg_blocks", 0, C.byref(n), None, MEM_HOST)
         return n.value
@@ -389,6 +403,7 @@ class Context:
 
     def gmres_solve(self, dt: float, b, U=None, out=None, opts: Optional[SolverOpts] = None,
                     raise_on_fail: bool = True):
+        """m1_gmres_solve: solve J(U) x = b with the solver options; returns (x, SolveInfo)."""
         pu, mu, ku = _ptr(U)
         pb, mb, kb = _ptr(b)
         if out is None:
@@ -403,11 +418,13 @@ class Context:
         return out, info
 
     def set_velocity(self, ux, uy=None, uz=None):
+        """m1_set_velocity: prescribed face velocities of the gas, one array per axis."""
         ps = [_ptr(u) for u in (ux, uy, uz)]
         self._call("m1_set_velocity", ps[0][0], ps[1][0], ps[2][0],
                    _check_mem(*[q[1] for q in ps if q[0] is not None]))
 
     def advect(self, dt: float):
+        """m1_advect: explicit upwind transport of rho c_v T by the prescribed velocities over dt."""
         self._call("m1_advect", C.c_double(dt))
 
     def velocity_sources(self, dt: float):
@@ -415,6 +432,7 @@ class Context:
         self._call("m1_velocity_sources", C.c_double(dt))
 
     def set_preconditioner(self, net):
+        """m1_set_preconditioner: attach a trained U-Net (Net) as the learned preconditioner."""
         self._call("m1_set_preconditioner", net.h if net is not None else None)
         self._net = net  # keep the network alive while attached
 
@@ -433,9 +451,11 @@ class Context:
         return x, t
 
     def profile(self, enable: bool = True):
+        """m1_profile: switch the per-kernel-class event timers on or off."""
         self._call("m1_profile", int(bool(enable)))
 
     def stats(self) -> dict:
+        """m1_stats: counters, kernel times per class and algorithmic bytes as a dict."""
         s = Stats()
         self._call("m1_stats", C.byref(s))
         return s.as_dict()
@@ -600,6 +620,7 @@ class Batch:
                        Bm.ctypes.data if Bm is not None else None, MEM_HOST)
 
     def close(self):
+        """m1_batch_destroy."""
         if getattr(self, "h", None):
             self.lib.m1_batch_destroy(self.h)
             self.h = None
@@ -616,6 +637,7 @@ class Batch:
             raise M1Error(st, self.lib.m1_batch_last_error(self.h).decode())
 
     def num_classes(self) -> int:
+        """m1_batch_num_classes: the number of size classes (distinct cell counts)."""
         return int(self.lib.m1_batch_num_classes(self.h))
 
     def set_class(self, c: int, threads: int):
@@ -623,6 +645,7 @@ class Batch:
         self._call("m1_batch_set_class", int(c), int(threads))
 
     def tune(self, dts, opts=None):
+        """m1_batch_tune: per class the fastest of the single-grid path (0) and CTA sizes 128/256/512."""
         d = np.ascontiguousarray(dts, dtype=np.float64)
         chosen = np.zeros(self.num_classes(), dtype=np.int32)
         o = opts if opts is not None else default_opts()
@@ -630,6 +653,7 @@ class Batch:
         return chosen
 
     def implicit_step(self, dts, opts=None):
+        """m1_batch_implicit_step: one step of every problem; returns (per-problem info, elapsed ms)."""
         d = np.ascontiguousarray(dts, dtype=np.float64)
         info = (BatchProblemInfo * len(self.problems))()
         ms = C.c_double()
@@ -638,6 +662,7 @@ class Batch:
         return [{k: getattr(i, k) for k, _ in i._fields_} for i in info], ms.value
 
     def get_solution(self, k: int):
+        """m1_batch_get_solution: problem k's U^{n+1} (3 N values)."""
         p = self.problems[k]
         out = np.empty(p.n_u * p.ncell)
         self._call("m1_batch_get_solution", int(k), out.ctypes.data, MEM_HOST)
