@@ -66,3 +66,32 @@ def test_null_arguments(lib):
     assert lib.m1_init_grid(None, None, None) == m1.M1_ERR_ARG
     assert lib.m1_destroy(None) == m1.M1_OK
     assert lib.m1_last_error(None) == b"null context"
+
+
+def _c_struct_fields(header: str, name: str):
+    """Field names, in order, of `typedef struct { ... } name;` in a C header: in each
+    comma-separated declarator the last identifier once array brackets are removed."""
+    import re
+    src = re.sub(r"/\*.*?\*/", "", header, flags=re.S)
+    m = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + re.escape(name) + r"\s*;", src)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        for d in decl.split(","):
+            d = re.sub(r"\[[^\]]*\]", "", d).strip()
+            if d:
+                fields.append(re.findall(r"[A-Za-z_]\w*", d)[-1])
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("m1_grid_desc", "GridDesc"), ("m1_solver_opts", "SolverOpts"),
+                                          ("m1_step_info", "StepInfo"), ("m1_solve_info", "SolveInfo"),
+                                          ("m1_stats_t", "Stats"), ("m1_batch_problem_info", "BatchProblemInfo"),
+                                          ("m1_train_opts", "TrainOpts"), ("m1_train_info", "TrainInfo"),
+                                          ("m1_device_fields", "DeviceFields")])
+def test_ctypes_structs_mirror_the_header(cname, pyname):
+    # the binding's ctypes structures must list the C structs' fields in the same order
+    import os
+    from paper_2011_13926_gb300 import m1
+    header = open(os.path.join(os.path.dirname(__file__), "..", "include", "m1.h")).read()
+    assert [f for f, _ in getattr(m1, pyname)._fields_] == _c_struct_fields(header, cname)
