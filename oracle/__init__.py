@@ -7,9 +7,11 @@ import it; the library never does, and the two share no code. Inputs come from
 ``seeded_inputs`` (data only).
 
 Pinned by tests/test_oracle_*.py against closed forms, limits, invariants,
-brute force and the values the paper prints. Parity unpinned beyond the oracle
-itself: the whole implicit step at scale (no closed form exists; the pins cover
-each ingredient).
+brute force and the values the paper prints. The whole implicit step has no
+closed form; it is pinned through its ingredients and in its diffusive limit
+(one thick step against Eq. discreteDiffusionEqua; the Marshak wave of Sect. 5.1
+against the diffusion reference of oracle/diffusion.py, AP 1.1 % and HLL 81 %
+where the paper prints 1.1 % and 84 %).
 """
 from .m1 import Closure, Scheme, eigenvalues  # noqa: F401
 from .solvers import (block_jacobi, block_tridiagonal_part, dense_jacobian, dense_solve, gmres,  # noqa: F401
