@@ -397,9 +397,11 @@ const char* m1_batch_last_error(const m1_batch* b);
  *   - N = n[0]*n[1]*n[2] above M1_NOALLOC_MAX_CELLS is rejected with
  *     M1_ERR_ARG before anything is launched.
  *   - The call allocates nothing (no cudaMalloc, cudaFree or allocating
- *     library routine). Its first call on a device looks up the array's device
- *     address (cudaGetSymbolAddress) with that device current; make that first
- *     call before any stream capture.
+ *     library routine). Its first call in each CUDA context (the device's
+ *     primary context, made current by the call) looks up the array's device
+ *     address (cudaGetSymbolAddress) and caches it under the context's unique
+ *     id; make that first call before any stream capture. After a device reset
+ *     the next call runs in a new context and looks the address up again.
  *   - Every call shares the one array, which keeps the last call's contents:
  *     the call clears what must start at zero, but calls that overlap on the
  *     GPU (different streams, or different host threads on one device) race.

@@ -6,11 +6,16 @@
 // file-scope __device__ array sized for M1_NOALLOC_MAX_CELLS cells. The same
 // kernels as the context path run on it, so the results are the same.
 //
-// The array's device address is looked up once per device with
-// cudaGetSymbolAddress (the device current at the first call); host code never
-// passes the array's host-side name to a kernel. Calls share the array: every
+// The array's device address is looked up with cudaGetSymbolAddress once per
+// CUDA context, at the first call made while that context is current, and
+// cached under the context's unique id (cuCtxGetId; ids are never reused within
+// a process). A device reset or a re-created primary context therefore gets a
+// fresh lookup instead of a stale address. Host code never passes the array's
+// host-side name to a kernel. Calls share the array: every
 // entry is written before it is read within a call, nothing accumulates across
 // calls, and calls that overlap on the GPU race.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "../../include/m1.h"
@@ -31,21 +36,58 @@ static __device__ __align__(256) double m1_noalloc_scratch[kScratchDoubles];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
+// (context id, device address) pairs; a full table overwrites its oldest entry
+constexpr int kCacheSlots = 64;
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void* addr;
+};
+ScratchSlot g_slots[kCacheSlots] = {};
+int g_next_slot = 0;
 std::mutex g_scratch_mu;
 
-m1_status scratch_address(double** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return M1_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return M1_ERR_ARG;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, m1_noalloc_scratch) != cudaSuccess || !p) return M1_ERR_CUDA;
-        g_scratch_addr[dev] = p;
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// the unique id of the CUDA context current on this thread (the runtime makes
+// the device's primary context current first)
+m1_status current_context_id(unsigned long long* id) {
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return M1_ERR_CUDA;
+        get_current = reinterpret_cast<PfnCtxGetCurrent>(f1);
+        get_id = reinterpret_cast<PfnCtxGetId>(f2);
     }
-    *out = static_cast<double*>(g_scratch_addr[dev]);
+    // cudaSetDevice makes the device's primary context current on this thread
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) return M1_ERR_CUDA;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return M1_ERR_CUDA;
+    return get_id(ctx, id) == CUDA_SUCCESS ? M1_OK : M1_ERR_CUDA;
+}
+
+m1_status scratch_address(double** out) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    unsigned long long id = 0;
+    const m1_status st = current_context_id(&id);
+    if (st != M1_OK) return st;
+    for (const ScratchSlot& e : g_slots)
+        if (e.addr && e.ctx_id == id) {
+            *out = static_cast<double*>(e.addr);
+            return M1_OK;
+        }
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, m1_noalloc_scratch) != cudaSuccess || !p) return M1_ERR_CUDA;
+    g_slots[g_next_slot] = ScratchSlot{id, p};
+    g_next_slot = (g_next_slot + 1) % kCacheSlots;
+    *out = static_cast<double*>(p);
     return M1_OK;
 }
 
