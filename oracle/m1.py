@@ -108,9 +108,18 @@ def eigenvalues(cl: Closure, a: int, c: float):
 
 
 class Scheme:
-    """The discretisation of one Problem (seeded_inputs.Problem)."""
+    """The discretisation of one Problem (seeded_inputs.Problem).
 
-    def __init__(self, prob):
+    ``fallback`` (grid-shaped, nonzero = flagged) selects, cell by cell, the
+    admissible fallback that Sect. 3.1.3 names for states where the AP + WB
+    scheme gives f > 1: a flagged cell takes the centred flux source of
+    Eq. (wb_naive), and every face of a flagged cell takes alpha = 1 and the
+    wave speeds -c, +c (HLL with the largest speeds the M1 system allows). With
+    every cell flagged this is the HLL scheme with fixed speeds and the centred
+    source, whose backward-Euler update keeps |F| <= cE when sigma_f >= sigma_a
+    (the paper's single sigma). Needs wave speeds frozen at time n or fixed."""
+
+    def __init__(self, prob, fallback=None):
         self.p = prob
         self.d = prob.dim
         self.c = prob.c
@@ -119,9 +128,27 @@ class Scheme:
         self.shape = prob.shape
         self.N = prob.ncell
         self.nu = prob.n_u
+        self.fallback = None
+        if fallback is not None and np.any(fallback):
+            if prob.implicit_eigs and not prob.fixed_eigs:
+                raise ValueError("the fallback needs wave speeds frozen at time n or fixed")
+            self.fallback = np.asarray(fallback).reshape(self.shape) != 0
         self.Un = self.unpack(prob.state_vector())
         self.lam_n = [self._speeds_at(self.Un, a) for a in range(self.d)]
         self.alpha = [self._alpha_axis(a) for a in range(self.d)]
+        if self.fallback is not None:
+            for a in range(self.d):
+                m = self._fallback_faces(a)
+                lp, lm = self.lam_n[a]
+                self.lam_n[a] = (np.where(m, self.c, lp), np.where(m, -self.c, lm))
+                self.alpha[a] = np.where(m, 1.0, self.alpha[a])
+
+    def _fallback_faces(self, a: int):
+        """Faces along axis a with a flagged cell on either side (a boundary face
+        follows its one cell; a periodic face both of its cells)."""
+        flag = self.pad_sigma(self.fallback.astype(float), a)
+        fL, fR = self.LR(flag, a)
+        return (fL > 0) | (fR > 0)
 
     # ------------------------------------------------------------------ layout
     def ax(self, a: int) -> int:
@@ -293,12 +320,15 @@ class Scheme:
         return Phi
 
     def flux_source(self, U, b: int):
-        """{sigma F_b}_i: Eq. (wb_smart) (well-balanced) or Eq. (wb_naive)."""
+        """{sigma F_b}_i: Eq. (wb_smart) (well-balanced) or Eq. (wb_naive); flagged
+        fallback cells take Eq. (wb_naive)."""
+        naive = self.p.sigma_f * U[1 + b]
         if self.p.well_balanced:
             Phi = self.wb_faces(U, b)
             lo, hi = self.LR(Phi, b)
-            return 0.5 * (hi + lo)
-        return self.p.sigma_f * U[1 + b]
+            wb = 0.5 * (hi + lo)
+            return wb if self.fallback is None else where(self.fallback, naive, wb)
+        return naive
 
     def emission(self, U):
         """a_r T^4 (gas coupled) or the frozen emission field B."""
@@ -522,3 +552,11 @@ class Scheme:
         U = self.unpack(u)
         F2 = sum(np.asarray(U[1 + b]) ** 2 for b in range(self.d))
         return int(np.count_nonzero(np.sqrt(F2) > self.c * U[0]))
+
+    def inadmissible(self, u) -> np.ndarray:
+        """Grid-shaped mask of the cells outside the admissible set: E <= 0 or
+        |F| > c E (Sect. 2.2: f = |F| / (cE) must not exceed 1)."""
+        U = self.unpack(u)
+        F2 = sum(np.asarray(U[1 + b]) ** 2 for b in range(self.d))
+        E = np.asarray(U[0])
+        return ~(E > 0.0) | (np.sqrt(F2) > self.c * E)

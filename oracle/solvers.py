@@ -160,35 +160,107 @@ class NewtonResult:
     res0: float
     res: float
     history: List[float] = field(default_factory=list)
+    fallback: Optional[np.ndarray] = None  # grid-shaped mask of the flagged cells (realizability=True)
+    fallback_rounds: int = 0               # times the flagged set grew
+
+
+def admissible_theta(scheme: Scheme, u: np.ndarray, delta: np.ndarray, flagged: np.ndarray) -> np.ndarray:
+    """Per-cell step factors for the fallback cells: theta_i = 1 when U_i + delta_i is
+    admissible (E > 0, |F| <= cE), else 0.9 times the first of 1/2, 1/4, ... (at most
+    40 halvings) that is; 1 in every unflagged cell. The admissible set is convex, so
+    the admissible part of the segment from an admissible U_i is an interval."""
+    N, d, c = scheme.N, scheme.d, scheme.c
+    E, dE = u[:N], delta[:N]
+    F, dF = u[N:(1 + d) * N].reshape(d, N), delta[N:(1 + d) * N].reshape(d, N)
+    m = np.asarray(flagged).ravel()
+    th = np.ones(N)
+    for _ in range(40):
+        Et = E + th * dE
+        Ft = F + th * dF
+        ok = (Et > 0.0) & (np.sqrt((Ft * Ft).sum(0)) <= c * Et)
+        bad = m & ~ok
+        if not bad.any():
+            break
+        th = np.where(bad, 0.5 * th, th)
+    return np.where(m & (th < 1.0), 0.9 * th, th)
 
 
 def newton_solve(scheme: Scheme, rtol: float = 1e-8, newton_max: int = 30,
                  gmres_rtol: float = 1e-4, restart: int = 30, gmres_max: int = 3000,
-                 precond: str = "bj", line_search: bool = True) -> NewtonResult:
+                 precond: str = "bj", line_search: bool = True, dense: bool = False,
+                 realizability: bool = False, check_every: int = 5) -> NewtonResult:
     """Backward-Euler step by Newton-Raphson (Sect. 3.3.1) from U^n.
 
     Converged when ||R(U^k)||_2 <= rtol ||R(U^n)||_2 (2-norm over all unknowns).
-    Each Newton step solves J delta = -R to gmres_rtol; the step is damped by
+    Each Newton step solves J delta = -R to gmres_rtol (``dense``: exactly, by
+    LU of the assembled Jacobian; tiny grids only); the step is damped by
     halving theta (up to 6 times) until ||R|| decreases by the Armijo factor
     (1 - 1e-4 theta); the last trial is taken if none does.
+
+    ``realizability``: the library's a posteriori admissibility fallback (Sect.
+    3.1.3 leaves f > 1 possible with the AP + WB scheme and names the centred
+    source as a remedy; the fallback scheme is described with Scheme). Checks
+    run when the iterate has converged and after every ``check_every`` Newton
+    steps without convergence (0: only at convergence). A check flags the cells
+    with E <= 0 or |F| > cE that are not flagged yet; when there are none and
+    Newton has not converged, it flags instead the unflagged cells whose largest
+    residual component is at least a tenth of the largest one (Newton stalls on
+    the AP + WB system where the fallback one converges). Flagging resets the
+    newly flagged cells of the iterate to U^n (admissible), rebuilds the scheme
+    with the grown set and re-takes ||R(U^n)|| as the reference. In flagged
+    cells every Newton update is scaled per cell so that they stay admissible
+    (admissible_theta), before the line search. Newton steps of all rounds count
+    against newton_max. Converged: the last scheme's residual meets rtol at a
+    check that flags nothing.
     """
-    u = scheme.pack(scheme.Un)
+    p = scheme.p
+    mask = None
+    if realizability:
+        mask = np.zeros(scheme.shape, dtype=bool) if scheme.fallback is None else scheme.fallback.copy()
+    un = scheme.pack(scheme.Un)
+    u = un.copy()
     R = scheme.residual(u)
     r0 = np.linalg.norm(R)
     hist = [r0]
     rn = r0
     its = 0
     git = 0
+    rounds = 0
+    since = 0
     N, nu = scheme.N, scheme.nu
-    while rn > rtol * r0 and its < newton_max:
-        if precond == "bj":
-            Minv = block_jacobi(scheme.diag_blocks(u), N, nu)
+    while True:
+        due = rn <= rtol * r0 or (check_every > 0 and since >= check_every)
+        if realizability and due:
+            since = 0
+            new = scheme.inadmissible(u) & ~mask
+            if not new.any() and rn > rtol * r0:
+                Rc = np.abs(R.reshape(nu, N)).max(axis=0).reshape(scheme.shape)
+                new = (Rc >= 0.1 * Rc.max()) & ~mask
+            if new.any():
+                mask |= new
+                rounds += 1
+                u = np.where(np.tile(new.ravel(), nu), un, u)
+                scheme = Scheme(p, mask)
+                r0 = np.linalg.norm(scheme.residual(un))
+                R = scheme.residual(u)
+                rn = np.linalg.norm(R)
+                hist.append(rn)
+                continue
+        if rn <= rtol * r0 or its >= newton_max:
+            break
+        if dense:
+            delta = dense_solve(scheme, u, -R)
         else:
-            Minv = lambda r: r  # noqa: E731
-        res = gmres(lambda v: scheme.jv(u, v), -R, Minv, rtol=gmres_rtol, restart=restart,
-                    maxiter=gmres_max)
-        git += res.iters
-        delta = res.x
+            if precond == "bj":
+                Minv = block_jacobi(scheme.diag_blocks(u), N, nu)
+            else:
+                Minv = lambda r: r  # noqa: E731
+            res = gmres(lambda v: scheme.jv(u, v), -R, Minv, rtol=gmres_rtol, restart=restart,
+                        maxiter=gmres_max)
+            git += res.iters
+            delta = res.x
+        if realizability and mask.any():
+            delta = delta * np.tile(admissible_theta(scheme, u, delta, mask), nu)
         theta = 1.0
         for _ in range(7):
             ut = u + theta * delta
@@ -199,8 +271,13 @@ def newton_solve(scheme: Scheme, rtol: float = 1e-8, newton_max: int = 30,
             theta *= 0.5
         u, R, rn = ut, Rt, rt
         its += 1
+        since += 1
         hist.append(rn)
-    return NewtonResult(u, rn <= rtol * r0, its, git, r0, rn, hist)
+    out = NewtonResult(u, bool(rn <= rtol * r0), its, git, r0, rn, hist)
+    if realizability:
+        out.fallback = mask
+        out.fallback_rounds = rounds
+    return out
 
 
 def block_tridiagonal_part(J: np.ndarray, nu: int, N: int) -> np.ndarray:

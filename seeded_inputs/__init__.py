@@ -317,6 +317,56 @@ def marshak_schedule(t_end: float = 3000.0, dt0: float = 0.01, dt_max: float = 1
     return dts
 
 
+def diffusion_gaussian_1d(n: int, sigma: float = 1000.0, width: float = 0.05, floor: float = 1e-6,
+                          ap_correction: bool = True) -> Problem:
+    """1D Gaussian pulse in a thick, purely scattering medium (the diffusive limit of
+    Sect. 2.3): [0, 1], outflow, sigma_a = 0, sigma_f = ``sigma`` everywhere,
+    E = floor + exp(-(x - 1/2)^2 / (2 width^2)), F = 0, wave speeds frozen at time n.
+    ``dt`` is left at 1; the caller sets it."""
+    p = make_problem(1, (n,), bc=[("outflow", "outflow")], dt=1.0, ap_correction=ap_correction,
+                     name=f"diffusion_gaussian_1d_{n}")
+    x = p.centers(0)
+    p.E = floor + np.exp(-((x - 0.5) ** 2) / (2 * width * width))
+    p.F = np.zeros((1, n))
+    p.sigma_a = np.zeros(p.shape)
+    p.sigma_f = np.full(p.shape, float(sigma))
+    p.B = np.zeros(p.shape)
+    p.implicit_eigs = False
+    return p
+
+
+def opacity_jump_1d(n: int = 100, sigma_dx: float = 100.0, well_balanced: bool = True) -> Problem:
+    """The opacity-jump run of Sect. 5.2 in code units (c = a_r = 1, domain [0, 1]).
+
+    sigma_f dx = ``sigma_dx`` for x < 1/2 and 0 beyond (sigma = 1e4 at n = 100, as in the
+    paper), sigma_a = 0 (the gas is in equilibrium with the radiation, so the exchange
+    vanishes in the steady state), E = 1 (300 K scaled), F = 0. The left side is a
+    Dirichlet ghost at 1000 K (E = (10/3)^4, F = 0), the right side outflow. Wave speeds
+    frozen at time n; ``dt`` is left at dx / c."""
+    p = make_problem(1, (n,), bc=[("dirichlet", "outflow")], well_balanced=well_balanced,
+                     name=f"opacity_jump_1d_{n}_{'wb' if well_balanced else 'centred'}")
+    x = p.centers(0)
+    p.sigma_a = np.zeros(p.shape)
+    p.sigma_f = np.where(x < 0.5, sigma_dx / p.dx[0], 0.0)
+    p.E = np.ones(p.shape)
+    p.F = np.zeros((1, n))
+    p.B = np.zeros(p.shape)
+    p.boundary[(0, 0)] = (np.array((1000.0 / 300.0) ** 4), np.array([0.0]), np.array(1, np.uint8))
+    p.implicit_eigs = False
+    p.dt = p.dx[0] / p.c
+    return p
+
+
+def opacity_jump_schedule(dt0: float = 0.01, growth: float = 1.8, dt_max: float = 4000.0,
+                          steps: int = 24) -> List[float]:
+    """Time steps of the opacity-jump run: from dx / c, growing by ``growth`` up to dt_max."""
+    dts, d = [], dt0
+    for _ in range(steps):
+        dts.append(d)
+        d = min(d * growth, dt_max)
+    return dts
+
+
 def gaussian_lognormal_2d(n: int, seed: int, span=(1e-2, 1e3), dt_factor: float = 50.0,
                           ell: Optional[float] = None, center=None) -> Problem:
     """2D radiation-only problem with a Gaussian E pulse in a lognormal opacity
