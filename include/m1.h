@@ -104,6 +104,21 @@ typedef struct {
     int pc_rebuild;       /* M1_PRECOND_MG: rebuild the hierarchy on Newton steps 0, k, 2k, ... of each implicit
                              step (1, the default: every Newton step; values < 1 act as 1); in between, the
                              cycle keeps its smoothers and coarse operators and applies the current J on level 0 */
+    int realizability;    /* 0 (default): the result may leave the admissible set (E > 0, |F| <= cE); its
+                             violations are counted. 1: the a posteriori admissibility fallback (Sect. 3.1.3
+                             names the centred source as the remedy for f > 1). Checks run when Newton has
+                             converged and after every check_every Newton steps without convergence. A check
+                             flags the unflagged cells with E <= 0 or |F| > cE; if there are none and Newton has
+                             not converged, the unflagged cells whose largest residual component is at least a
+                             tenth of the largest one. A flagged cell takes the centred flux source
+                             (Eq. wb_naive); its faces take alpha = 1 and the speeds -c, +c. The iterate of a
+                             flagged inadmissible cell is reset to U^n, ||R(U^n)|| of the new scheme becomes the
+                             reference, and every later Newton
+                             update of a flagged cell is scaled so that the cell stays admissible. Newton steps
+                             of all rounds count against newton_max. Needs frozen (implicit_eigs = 0) or fixed
+                             wave speeds. */
+    int check_every;      /* realizability = 1: Newton steps between checks before convergence (5; 0: only at
+                             convergence) */
 } m1_solver_opts;
 
 #define M1_HIST 64  /* length of the per-Newton-iteration histories */
@@ -113,7 +128,7 @@ typedef struct {
     int newton_iters;
     int gmres_iters;      /* total Arnoldi iterations over all linear solves */
     int refinements;      /* FP64 refinement sweeps (mixed precision) */
-    double res0, res;     /* ||R(U^n)||_2 and the final ||R||_2 */
+    double res0, res;     /* ||R(U^n)||_2 (of the last scheme when the fallback flagged cells) and the final ||R||_2 */
     long long realizability_violations; /* cells with |F| > c E in the result (Sect. 3.1.3) */
     double time_ms;       /* wall time of the step measured on the stream */
     /* per Newton iteration k < min(newton_iters, M1_HIST): ||R|| after the
@@ -121,6 +136,8 @@ typedef struct {
     double res_hist[M1_HIST];
     int gmres_hist[M1_HIST];
     double theta_hist[M1_HIST];
+    long long fallback_cells;  /* realizability = 1: cells flagged in this step (m1_get_fallback) */
+    int fallback_rounds;       /* realizability = 1: checks that flagged cells */
 } m1_step_info;
 
 typedef struct {
@@ -228,6 +245,11 @@ m1_status m1_explicit_step(m1_ctx* ctx, double dt);
  * restarted (F)GMRES (Sect. 3.3). On failure returns M1_ERR_NOT_CONVERGED
  * (or M1_ERR_NONFINITE) and leaves the state unchanged; info is filled either way. */
 m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m1_step_info* info);
+
+/* The cells the admissibility fallback flagged in the last m1_implicit_step
+ * (realizability = 1): N bytes, 1 = flagged (centred source, alpha = 1 and
+ * speeds -c, +c on its faces), 0 otherwise; all 0 after a step without it. */
+m1_status m1_get_fallback(const m1_ctx* ctx, unsigned char* mask, m1_mem mem);
 
 /* R(U) of the backward-Euler step of size dt from the context's time-n state
  * (the scheme of Sect. 3.1.1). U, R: n_u*N doubles. */

@@ -205,8 +205,8 @@ def newton_solve(scheme: Scheme, rtol: float = 1e-8, newton_max: int = 30,
     with E <= 0 or |F| > cE that are not flagged yet; when there are none and
     Newton has not converged, it flags instead the unflagged cells whose largest
     residual component is at least a tenth of the largest one (Newton stalls on
-    the AP + WB system where the fallback one converges). Flagging resets the
-    newly flagged cells of the iterate to U^n (admissible), rebuilds the scheme
+    the AP + WB system where the fallback one converges). Flagging resets newly
+    flagged inadmissible cells of the iterate to U^n (admissible), rebuilds the scheme
     with the grown set and re-takes ||R(U^n)|| as the reference. In flagged
     cells every Newton update is scaled per cell so that they stay admissible
     (admissible_theta), before the line search. Newton steps of all rounds count
@@ -233,13 +233,15 @@ def newton_solve(scheme: Scheme, rtol: float = 1e-8, newton_max: int = 30,
         if realizability and due:
             since = 0
             new = scheme.inadmissible(u) & ~mask
-            if not new.any() and rn > rtol * r0:
+            reset = new.any()
+            if not reset and rn > rtol * r0:
                 Rc = np.abs(R.reshape(nu, N)).max(axis=0).reshape(scheme.shape)
                 new = (Rc >= 0.1 * Rc.max()) & ~mask
             if new.any():
                 mask |= new
                 rounds += 1
-                u = np.where(np.tile(new.ravel(), nu), un, u)
+                if reset:
+                    u = np.where(np.tile(new.ravel(), nu), un, u)
                 scheme = Scheme(p, mask)
                 r0 = np.linalg.norm(scheme.residual(un))
                 R = scheme.residual(u)

@@ -100,6 +100,10 @@ struct m1_ctx {
     double* scal_base = nullptr;
     int* singular = nullptr;
     unsigned long long* viol = nullptr;
+    unsigned char* fb = nullptr;          // admissibility fallback: flagged cells of the current step
+    unsigned long long* fbw = nullptr;    // [0] cells flagged by a check, [1] bit pattern of max |R|
+    bool fb_on = false;                   // some cell is flagged: the kernels read fb
+    long long fb_cells = 0;
     double* hpin = nullptr;      // pinned host scalars (mapped)
     double* hpin_dev = nullptr;  // their device address, or null when mapping is unavailable
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -223,6 +227,7 @@ void fill_dev_common(const m1_ctx* ctx, Dev<R>& g) {
     g.fixed_eigs = ctx->d.fixed_eigs;
     g.wb_boundary = ctx->d.wb_boundary;
     g.implicit_eigs = ctx->d.implicit_eigs;
+    g.fb = ctx->fb_on ? ctx->fb : nullptr;
 }
 
 Dev<double> dev64(const m1_ctx* ctx, double dt) {
@@ -335,6 +340,9 @@ m1_status ensure_work(m1_ctx* ctx) {
     CKS(dalloc(ctx, &ctx->blocks, (size_t)nu * nu * N));
     CKS(dalloc(ctx, &ctx->binv, (size_t)nu * nu * N));
     CKS(dalloc(ctx, &ctx->binv32, (size_t)nu * nu * N));
+    CKS(dalloc(ctx, &ctx->fb, (size_t)N));
+    CKS(dalloc(ctx, &ctx->fbw, 2));
+    CK(cudaMemsetAsync(ctx->fb, 0, (size_t)N, ctx->s));
     ctx->work_ok = true;
     return M1_OK;
 }
@@ -1025,6 +1033,8 @@ void m1_default_opts(m1_solver_opts* o) {
     o->refine_max = 4;
     o->krylov = M1_KRYLOV_GMRES;
     o->pc_rebuild = 1;
+    o->realizability = 0;
+    o->check_every = 5;
 }
 
 m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out) {
@@ -1153,7 +1163,8 @@ m1_status m1_destroy(m1_ctx* ctx) {
                     ctx->delta, ctx->rhs, ctx->w, ctx->z, ctx->tmp, ctx->V, ctx->xacc, ctx->blocks, ctx->binv,
                     ctx->binv32, ctx->V32, ctx->w32, ctx->z32, ctx->U32, ctx->tmp32, ctx->Fstar, ctx->linework,
                     ctx->partials, ctx->scal_base, ctx->singular, ctx->viol, ctx->ar_partials,
-                    ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32, ctx->bs_part, ctx->bs_sc};
+                    ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32, ctx->bs_part, ctx->bs_sc,
+                    ctx->fb, ctx->fbw};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int l = 0; l < kMgMaxLevels; ++l) {
@@ -1562,6 +1573,55 @@ m1_status m1_gmres_solve(m1_ctx* ctx, double dt, const double* U, const double* 
     return conv ? M1_OK : fail(ctx, M1_ERR_NOT_CONVERGED, "GMRES did not converge");
 }
 
+// One check of the admissibility fallback at the iterate ctx->U (residual in
+// ctx->R): flag the unflagged inadmissible cells (E <= 0 or |F| > cE), or, when
+// there are none and Newton has not converged, the unflagged cells whose
+// largest residual component is at least a tenth of the largest one; newly
+// flagged inadmissible cells of U are reset to U^n. When cells were flagged, the faces of
+// flagged cells get alpha = 1 and the speeds -c, +c (FP64 and FP32 copies).
+static m1_status fallback_check(m1_ctx* ctx, double dt, bool converged, long long* flagged) {
+    cudaStream_t s = ctx->s;
+    const long long N = ctx->N;
+    unsigned long long cnt = 0;
+    CK(cudaMemsetAsync(ctx->fbw, 0, 2 * sizeof(unsigned long long), s));
+    launch_fallback_flag(0, ctx->nu, ctx->dim, N, ctx->d.c, 0.0, ctx->U, ctx->R, ctx->Un, ctx->fb, ctx->fbw, s);
+    count(ctx, 1);
+    CK(cudaMemcpyAsync(ctx->hpin, ctx->fbw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CKS(sync(ctx));
+    memcpy(&cnt, ctx->hpin, sizeof(cnt));
+    if (cnt == 0 && !converged) {
+        launch_residual_absmax(ctx->nu, N, ctx->R, ctx->fbw + 1, s);
+        count(ctx, 1);
+        CK(cudaMemcpyAsync(ctx->hpin, ctx->fbw + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CKS(sync(ctx));
+        unsigned long long bits = 0;
+        memcpy(&bits, ctx->hpin, sizeof(bits));
+        double rmax = 0.0;
+        memcpy(&rmax, &bits, sizeof(rmax));
+        if (rmax > 0.0) {
+            launch_fallback_flag(1, ctx->nu, ctx->dim, N, ctx->d.c, 0.1 * rmax, ctx->U, ctx->R, ctx->Un, ctx->fb,
+                                 ctx->fbw, s);
+            count(ctx, 1);
+            CK(cudaMemcpyAsync(ctx->hpin, ctx->fbw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            CKS(sync(ctx));
+            memcpy(&cnt, ctx->hpin, sizeof(cnt));
+        }
+    }
+    *flagged = (long long)cnt;
+    if (cnt > 0) {
+        ctx->fb_on = true;
+        TK t(ctx, M1_K_VECTOR);
+        launch_fallback_faces(dev64(ctx, dt), ctx->fb, ctx->f64.lam_p, ctx->f64.lam_m, ctx->f64.alpha, s);
+        for (int a = 0; a < ctx->dim; ++a) {
+            launch_f64_to_f32(ctx->f64.alpha[a], ctx->f32.alpha[a], ctx->nfaces[a], s);
+            launch_f64_to_f32(ctx->f64.lam_p[a], ctx->f32.lam_p[a], ctx->nfaces[a], s);
+            launch_f64_to_f32(ctx->f64.lam_m[a], ctx->f32.lam_m[a], ctx->nfaces[a], s);
+        }
+        count(ctx, 4 * ctx->dim);
+    }
+    return M1_OK;
+}
+
 m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m1_step_info* info) {
     if (!ctx) return M1_ERR_ARG;
     if (!(dt > 0.0)) return fail(ctx, M1_ERR_ARG, "dt must be positive");
@@ -1569,10 +1629,17 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
     m1_default_opts(&o);
     if (opts) o = *opts;
     if (o.restart < 1 || o.restart > kMaxRestart) return fail(ctx, M1_ERR_ARG, "restart must be in [1, 30]");
+    const bool fbk = o.realizability != 0;
+    if (fbk && ctx->d.implicit_eigs && !ctx->d.fixed_eigs)
+        return fail(ctx, M1_ERR_ARG, "realizability = 1 needs frozen (implicit_eigs = 0) or fixed wave speeds");
     CKS(prepare(ctx));
     CKS(ensure_work(ctx));
     m1_step_info inf{};
     cudaStream_t s = ctx->s;
+    // a fresh flagged set per step
+    ctx->fb_on = false;
+    ctx->fb_cells = 0;
+    CK(cudaMemsetAsync(ctx->fb, 0, (size_t)ctx->N, s));
     CK(cudaEventRecord(ctx->ev0, s));
     // alpha and the time-n wave speeds are the first stage of every step
     CKS(refresh(ctx));
@@ -1588,7 +1655,27 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
     }
     rn = r0;
     m1_status result = M1_OK;
-    while (rn > o.newton_rtol * r0 && inf.newton_iters < o.newton_max) {
+    int since = 0;  // Newton steps since the last admissibility check
+    while (true) {
+        const bool done = rn <= o.newton_rtol * r0;
+        if (fbk && (done || (o.check_every > 0 && since >= o.check_every))) {
+            since = 0;
+            long long nf = 0;
+            CKS(fallback_check(ctx, dt, done, &nf));
+            if (nf > 0) {
+                ctx->fb_cells += nf;
+                inf.fallback_rounds++;
+                g = dev64(ctx, dt);
+                CKS(residual_norm(ctx, g, ctx->Un, ctx->Rt, &r0));  // the reference of the grown scheme
+                CKS(residual_norm(ctx, g, ctx->U, ctx->R, &rn));
+                if (!(r0 == r0) || isinf(r0) || !(rn == rn) || isinf(rn)) {
+                    result = fail(ctx, M1_ERR_NONFINITE, "non-finite residual after flagging");
+                    break;
+                }
+                continue;
+            }
+        }
+        if (done || inf.newton_iters >= o.newton_max) break;
         // delta solves J delta = -R
         launch_axpby_f64(-1.0, ctx->R, 0.0, ctx->R, ctx->Rt, n, s);
         count(ctx, 1);
@@ -1602,6 +1689,10 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
         if (ls != M1_OK) {
             result = ls;
             break;
+        }
+        if (ctx->fb_on) {  // flagged cells stay admissible
+            launch_admissible_theta(ctx->nu, ctx->dim, ctx->N, ctx->d.c, ctx->U, ctx->delta, ctx->fb, s);
+            count(ctx, 1);
         }
         double theta = 1.0, rt = 0.0;
         for (int ls_it = 0; ls_it < 7; ++ls_it) {
@@ -1620,14 +1711,21 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
             inf.theta_hist[inf.newton_iters] = theta;
         }
         inf.newton_iters++;
+        since++;
         ctx->st.newton_iters++;
         if (!(rn == rn) || isinf(rn)) {
             result = fail(ctx, M1_ERR_NONFINITE, "non-finite residual in Newton");
             break;
         }
     }
+    inf.res0 = r0;
     inf.res = rn;
     inf.converged = (result == M1_OK) && rn <= o.newton_rtol * r0;
+    inf.fallback_cells = ctx->fb_cells;
+    if (ctx->fb_on) {  // the face arrays carry the fallback: recompute them before the next use
+        ctx->fb_on = false;
+        ctx->dirty = true;
+    }
     CK(cudaMemsetAsync(ctx->viol, 0, sizeof(unsigned long long), s));
     launch_realizability(ctx->U, ctx->dim, ctx->N, ctx->d.c, ctx->viol, s);
     count(ctx, 1);
@@ -1651,6 +1749,20 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
     if (result != M1_OK) return result;
     if (!inf.converged) return fail(ctx, M1_ERR_NOT_CONVERGED, "Newton did not converge");
     return M1_OK;
+}
+
+m1_status m1_get_fallback(const m1_ctx* cctx, unsigned char* mask, m1_mem mem) {
+    m1_ctx* ctx = const_cast<m1_ctx*>(cctx);
+    if (!ctx || !mask) return M1_ERR_ARG;
+    if (!ctx->fb) {
+        if (mem == M1_MEM_DEVICE)
+            CK(cudaMemsetAsync(mask, 0, (size_t)ctx->N, ctx->s));
+        else
+            memset(mask, 0, (size_t)ctx->N);
+        return sync(ctx);
+    }
+    CKS(copy_out(ctx, mask, ctx->fb, (size_t)ctx->N, mem));
+    return sync(ctx);
 }
 
 m1_status m1_set_preconditioner(m1_ctx* ctx, m1_nn* nn) {

@@ -119,6 +119,10 @@ struct Dev {
     const R* bF[3][2];  // dim * M
     const unsigned char* bmask[3][2];
     long long bM[3];    // cells per face of axis a
+    // admissibility fallback (implicit step): nonzero = the cell takes the
+    // centred flux source of Eq. (wb_naive); its faces carry alpha = 1 and
+    // speeds -c, +c in the face arrays. Null: no cell is flagged.
+    const unsigned char* fb;
 };
 
 __device__ __forceinline__ long long face_index(const int* n, const int* coord, int a, int fa) {
@@ -315,6 +319,7 @@ __device__ __forceinline__ void cell_residual(const Dev<R>& g, const L& ld, long
     const Cl<S, DIM> ks = closure(self, g.c);
     const R sig_self = g.sig_f[idx];
     const R dt = g.dt;
+    const bool wbc = g.wb && !(g.fb && g.fb[idx]);  // well-balanced source in this cell
     S RE = self.E - g.Un[idx];
     S RF[DIM];
 #pragma unroll
@@ -360,7 +365,7 @@ __device__ __forceinline__ void cell_residual(const Dev<R>& g, const L& ld, long
             RE = RE + (w * g.alpha[a][fidx]) * Fs;
 #pragma unroll
             for (int b = 0; b < DIM; ++b) RF[b] = RF[b] + w * Ps[b];
-            if (g.wb) {
+            if (wbc) {
                 if (boundary && g.wb_boundary) {
                     // Eq. (boundaryCondition): sigma F at the face = -c (P_R - P_L) / dx
                     phi[a] = phi[a] - g.c * g.inv_dx[a] * (pressure(kR, a, a) - pressure(kL, a, a));
@@ -373,7 +378,7 @@ __device__ __forceinline__ void cell_residual(const Dev<R>& g, const L& ld, long
     const R cdt = g.c * dt;
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
-        S src = g.wb ? R(0.5) * phi[b] : sig_self * self.F[b];
+        S src = wbc ? R(0.5) * phi[b] : sig_self * self.F[b];
         RF[b] = RF[b] + cdt * src;
     }
     S emis;

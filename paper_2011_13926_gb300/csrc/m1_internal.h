@@ -178,6 +178,20 @@ void launch_scale_f64_to_f32(const double* x, const double* nrm2, float* y, long
 // back substitution y = H^-1 g on the rotated k x k triangle
 void launch_backsolve(const double* H, const double* g, int k, double* y, cudaStream_t s);
 // count cells with |F| > c E and non-finite entries
+// ----------------------------------------------------------------- admissibility fallback (m1_fallback.cu)
+// faces of flagged cells: lambda+- = +-c, alpha = 1 (the FP64 time-n face arrays)
+void launch_fallback_faces(const Dev<double>& g, const unsigned char* fb, double* const lam_p[3],
+                           double* const lam_m[3], double* const alpha[3], cudaStream_t s);
+// flag unflagged cells by rule 0 (E <= 0 or |F| > cE in U; their U is reset to U^n) or rule 1
+// (max_k |R_k| >= thresh; U kept), count += cells flagged
+void launch_fallback_flag(int rule, int nu, int dim, long long N, double c, double thresh, double* U,
+                          const double* R, const double* Un, unsigned char* fb, unsigned long long* count,
+                          cudaStream_t s);
+// *out = bit pattern of max |R| over all n_u N entries (atomicMax on a zeroed word)
+void launch_residual_absmax(int nu, long long N, const double* R, unsigned long long* out, cudaStream_t s);
+// per flagged cell: delta *= theta_i so that U + delta stays admissible
+void launch_admissible_theta(int nu, int dim, long long N, double c, const double* U, double* delta,
+                             const unsigned char* fb, cudaStream_t s);
 void launch_realizability(const double* U, int dim, long long N, double c, unsigned long long* count,
                           cudaStream_t s);
 

@@ -112,7 +112,7 @@ struct MgFace {
 };
 
 __device__ __forceinline__ void mg_lin_out(const Dev<float>& g, const float (*st)[6], const MgFace* fc,
-                                           float sig_self, float sig_a, float* out) {
+                                           float sig_self, float sig_a, bool wbc, float* out) {
     const float dt = g.dt, c = g.c, c2 = g.c * g.c;
     float RE = st[0][0], RFx = st[0][1], RFy = st[0][2];
     float phi[2] = {0.f, 0.f};
@@ -139,7 +139,7 @@ __device__ __forceinline__ void mg_lin_out(const Dev<float>& g, const float (*st
             RE = RE + (w * f.al) * Fs;
             RFx = RFx + w * Psx;
             RFy = RFy + w * Psy;
-            if (g.wb) {
+            if (wbc) {
                 if (f.boundary && g.wb_boundary) {
                     const float PR = a == 0 ? Rr[3] : Rr[5], PL = a == 0 ? L[3] : L[5];
                     phi[a] = phi[a] - c * g.inv_dx[a] * (PR - PL);
@@ -150,7 +150,7 @@ __device__ __forceinline__ void mg_lin_out(const Dev<float>& g, const float (*st
         }
     }
     const float cdt = c * dt;
-    if (g.wb) {
+    if (wbc) {
         RFx = RFx + cdt * (0.5f * phi[0]);
         RFy = RFy + cdt * (0.5f * phi[1]);
     } else {
@@ -175,6 +175,7 @@ __global__ void k_mg_assemble2d(Dev<float> g, const float* __restrict__ U, const
         const int ix = (int)(i % nx), iy = (int)(i / nx);
         const int coord[3] = {ix, iy, 0};
         const float sig_self = g.sig_f[i], sig_a = g.sig_a[i];
+        const bool wbc = g.wb && !(g.fb && g.fb[i]);
         MgFace fc[4];
         long long nbi[4];
         bool any_boundary = false;
@@ -257,7 +258,7 @@ __global__ void k_mg_assemble2d(Dev<float> g, const float* __restrict__ U, const
 #pragma unroll
                                 for (int k = 0; k < 6; ++k) st[1 + p][k] = gd[p][c][k];
                     }
-                    mg_lin_out(g, st, fc, sig_self, sig_a, out);
+                    mg_lin_out(g, st, fc, sig_self, sig_a, wbc, out);
                 }
 #pragma unroll
                 for (int r = 0; r < 3; ++r) A[((long long)(s * 3 + r) * 3 + c) * N + i] = out[r];

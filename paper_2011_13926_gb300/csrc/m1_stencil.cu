@@ -240,7 +240,9 @@ __global__ void __launch_bounds__(kTX* kTY)
     const long long idx = valid ? (long long)iy * nx + ix : 0;
     const int coord[3] = {ix, iy, 0};
     R sig_self = R(0), sig_nb[2][2], lpf[2][2], lmf[2][2], alf[2][2];
+    bool wbc = g.wb;  // well-balanced source in this cell (the fallback takes the centred one)
     if (valid) {
+        if (g.fb) wbc = wbc && !g.fb[idx];
         // the cell's faces: x-faces ix -+ 1/2 at fx, fx + 1 (nx + 1 per row); y-faces
         // iy -+ 1/2 at fy, fy + nx
         const long long fx = (long long)iy * (nx + 1) + ix, fy = idx;
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(kTX* kTY)
                 RE = RE + (w * alf[a][side]) * Fs;
                 RFx = RFx + w * Psx;
                 RFy = RFy + w * Psy;
-                if (g.wb) {
+                if (wbc) {
                     if (boundary && g.wb_boundary) {
                         const S PR = a == 0 ? Rc.Pxx : Rc.Pyy, PL = a == 0 ? Lc.Pxx : Lc.Pyy;
                         phi[a] = phi[a] - c * g.inv_dx[a] * (PR - PL);
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(kTX* kTY)
             }
         }
         const R cdt = c * dt;
-        if (g.wb) {
+        if (wbc) {
             RFx = RFx + cdt * (R(0.5) * phi[0]);
             RFy = RFy + cdt * (R(0.5) * phi[1]);
         } else {

@@ -49,7 +49,8 @@ class SolverOpts(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("restart", C.c_int),
                 ("gmres_max", C.c_int), ("gmres_rtol", C.c_double), ("precision", C.c_int),
                 ("precond", C.c_int), ("line_search", C.c_int), ("advance", C.c_int),
-                ("refine_max", C.c_int), ("krylov", C.c_int), ("pc_rebuild", C.c_int)]
+                ("refine_max", C.c_int), ("krylov", C.c_int), ("pc_rebuild", C.c_int),
+                ("realizability", C.c_int), ("check_every", C.c_int)]
 
 
 M1_HIST = 64
@@ -61,10 +62,13 @@ class StepInfo(C.Structure):
                 ("refinements", C.c_int), ("res0", C.c_double), ("res", C.c_double),
                 ("realizability_violations", C.c_longlong), ("time_ms", C.c_double),
                 ("res_hist", C.c_double * M1_HIST), ("gmres_hist", C.c_int * M1_HIST),
-                ("theta_hist", C.c_double * M1_HIST)]
+                ("theta_hist", C.c_double * M1_HIST), ("fallback_cells", C.c_longlong),
+                ("fallback_rounds", C.c_int)]
 
     def as_dict(self, history: bool = False):
         out = {k: getattr(self, k) for k, _ in self._fields_[:8]}
+        out["fallback_cells"] = self.fallback_cells
+        out["fallback_rounds"] = self.fallback_rounds
         if history:
             k = min(self.newton_iters, M1_HIST)
             out["res_hist"] = list(self.res_hist[:k])
@@ -150,6 +154,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_explicit_step": (I, [P, D]),
         "m1_implicit_step": (I, [P, D, C.POINTER(SolverOpts), C.POINTER(StepInfo)]),
         "m1_residual": (I, [P, D, P, P, I]),
+        "m1_get_fallback": (I, [P, P, I]),
         "m1_jv": (I, [P, D, P, P, P, I, I]),
         "m1_diag_blocks": (I, [P, D, P, P, I]),
         "m1_mg_apply": (I, [P, D, P, P, P, I]),
@@ -349,6 +354,15 @@ class Context:
         if st != M1_OK and raise_on_fail:
             raise M1Error(st, self.last_error())
         return st, info
+
+    def get_fallback(self, out=None):
+        """m1_get_fallback: the cells the admissibility fallback flagged in the last implicit step
+        (N bytes, x fastest; 1 = flagged)."""
+        if out is None:
+            out = np.empty(self.N, dtype=np.uint8)
+        p, m, k = _ptr(out, dtype=np.uint8)
+        self._call("m1_get_fallback", p, m)
+        return out
 
     def residual(self, dt: float, U, out=None):
         """m1_residual: the FP64 backward-Euler residual R(U) for step dt (time-n data from the state)."""
