@@ -81,7 +81,7 @@ def test_beam_small_fallback_parity(m1mod, factor, path):
 
 
 def test_two_slab_200_steps_at_50(m1mod):
-    """configs[0]'s 200 backward-Euler steps at 50 dt_CFL (FP64 GMRES(30), line preconditioner)."""
+    """The two-slab workload's 200 backward-Euler steps at 50 dt_CFL (FP64 GMRES(30), line preconditioner)."""
     p = si.two_slab_1d(512, dt_factor=50.0)
     ctx = _ctx(m1mod, p)
     opts = m1mod.default_opts(realizability=1, precond=m1mod.PRECOND_LINE, newton_max=60)
