@@ -43,6 +43,11 @@ def args_():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="beam", choices=["beam", "learned"],
+                    help="beam: the 1024^2 beam (headline); learned: the learned preconditioner on 512^2 "
+                         "lognormal Gaussian-pulse systems at 50 dt_CFL (training, then held-out solves)")
+    ap.add_argument("--train-rounds", type=int, default=8)
+    ap.add_argument("--train-pairs", type=int, default=512, help="pairs per training round (learned workload)")
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--dt-factor", type=float, default=50.0)
     ap.add_argument("--other-dts", default="10,100",
@@ -278,11 +283,110 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- learned workload
+def run_learned(a):
+    """Train the network on 512^2 problems (seeds 1000+), then time one implicit step of
+    held-out problems (seeds 1100, 1101) with mixed precision + the learned preconditioner
+    (FGMRES(30)) beside mixed point-block Jacobi, mixed multigrid and plain FP64
+    point-block Jacobi; errors are the oracle's residual of each GPU state."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import seeded_inputs as si
+    from oracle import Scheme, unet
+    from paper_2011_13926_gb300 import learned, m1
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream().cuda_stream
+    n = 512
+
+    def prob(seed):
+        return si.gaussian_lognormal_2d(n, seed, dt_factor=a.dt_factor if a.dt_factor else 50.0)
+
+    res = learned.train(prob, range(1000, 1100), n=n, rounds=a.train_rounds, pairs_per_round=a.train_pairs,
+                        epochs=4, lr=1e-3, lr_final=1e-4, krylov_steps=10, init=unet.init_params(0))
+    paths = {"mixed_learned": dict(precision=m1.PREC_MIXED, precond=learned.PRECOND_LEARNED),
+             "mixed_bj": dict(precision=m1.PREC_MIXED, precond=m1.PRECOND_BJ),
+             "mixed_mg": dict(precision=m1.PREC_MIXED, precond=3),
+             "plain_fp64_bj": dict(precision=m1.PREC_FP64, precond=m1.PRECOND_BJ)}
+    out = {k: {"ms": [], "newton_iters": [], "gmres_iters": [], "converged": [], "oracle_residual_ratio": []}
+           for k in paths}
+    infer = m1.Net(n, n, 1, s)
+    infer.set_params(res["params"])
+    launches0 = 0
+    for seed in (1100, 1101):
+        p = prob(seed)
+        sch = Scheme(p)
+        r0 = np.linalg.norm(sch.residual(p.state_vector()))
+        for name, kw in paths.items():
+            ctx = m1.context_from_problem(p, stream=s, device=True)
+            if name == "mixed_learned":
+                ctx.set_preconditioner(infer)
+            opts = m1.default_opts(advance=0, **kw)
+            for _ in range(max(1, a.warmup)):
+                ctx.implicit_step(p.dt, opts, raise_on_fail=False)
+            st0 = ctx.stats()
+            for _ in range(a.steps):
+                st, info = ctx.implicit_step(p.dt, opts, raise_on_fail=False)
+                out[name]["ms"].append(info.time_ms)
+                out[name]["newton_iters"].append(info.newton_iters)
+                out[name]["gmres_iters"].append(info.gmres_iters)
+                out[name]["converged"].append(bool(info.converged))
+            if name == "mixed_learned":
+                launches0 += ctx.stats()["kernel_launches"] - st0["kernel_launches"]
+            u = ctx.get_solution()
+            out[name]["oracle_residual_ratio"].append(float(np.linalg.norm(sch.residual(u)) / r0))
+            ctx.close()
+    for v in out.values():
+        v["value"] = n * n * len(v["ms"]) / (sum(v["ms"]) / 1e3) if v["ms"] else None
+    # the network on the tensor cores: one forward pass at 512^2 (BF16), CUDA events
+    x = torch.randn(n * n * 7, device="cuda", dtype=torch.float32)
+    for _ in range(3):
+        infer.forward(x, bf16=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    reps = 20
+    for _ in range(reps):
+        infer.forward(x, bf16=True)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / reps
+    flops = learned.forward_flops(n, n)
+    peak = None
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
+    v = out["mixed_learned"]["value"]
+    plain = out["plain_fp64_bj"]["value"]
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": statistics.mean(out["mixed_learned"]["ms"]), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64", "data": "synthetic",
+            "config": {"workload": f"gaussian_lognormal_2d {n}x{n}: radiation-only grey M1, periodic, lognormal "
+                                   f"sigma (ell=n/32, sigma*dx in [1e-2,1e3]), Gaussian pulse, dt=50 dt_CFL; "
+                                   f"held-out seeds 1100-1101, training seeds 1000+",
+                       "path": "FP32 inner FGMRES(30) + FP64 refinement, learned correction on odd Arnoldi steps"},
+            "training": {"pairs": res["pairs"], "seconds": res["seconds"], "first_loss": res["first_loss"],
+                         "final_loss": res["final_loss"], "rounds": a.train_rounds},
+            "paths": out, "speedup_vs_plain_fp64": v / plain if v and plain else None,
+            "roofline": {"bound": "tensor", "kernel_class": "network forward (tensor-core convolutions)",
+                         "achieved": flops / (fwd_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (fwd_ms / 1e3) / 1e12 / peak, "traffic": None,
+                         "flops_per_forward": flops, "forward_ms": fwd_ms,
+                         "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops)"},
+            "gpu_launches": launches0}
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU path
 def main():
     a = args_()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "learned":
+        return run_learned(a)
     import numpy as np
     import torch
 

@@ -303,17 +303,21 @@ m1_status m1_profile(m1_ctx* ctx, int enable);
 /* ---------------------------------------------------------------------------
  * Learned preconditioner (not in the paper; the library's own addition).
  *
- * A 3-level 2D U-Net (63,443 parameters; 3x3 convolutions 4-16-16 | 16-32-32 |
+ * A 3-level 2D U-Net (63,875 parameters; 3x3 convolutions 7-16-16 | 16-32-32 |
  * 32-32-32 | 64-32-16 | 32-16-3, ReLU, 2x2 average pooling, nearest 2x
  * upsampling with skip concatenation) maps a Krylov vector v of a 2D
- * radiation-only grid (channels E, F_x, F_y, scaled by s = ||v|| / sqrt(n)) and
- * the normalised log opacity (log10(sigma_f dx) - 0.5) / 2.5 to a correction.
- * As the right preconditioner of flexible GMRES it applies
- *     z = J_bj^-1 v + s * N(v / s, log sigma),
+ * radiation-only grid (channels E, F_x, F_y, scaled by s = ||v|| / sqrt(n)),
+ * the normalised log opacity (log10(sigma_f dx) - 0.5) / 2.5, and the state U
+ * at which the Jacobian is taken (F_x / (cE), F_y / (cE) clipped to [-1, 1], and
+ * (log10 E + 3) / 3, E floored at 1e-30) to a correction. As the right
+ * preconditioner of flexible GMRES it applies
+ *     z = J_bj^-1 v + s * N(v / s, log sigma, U),
  * the point-block Jacobi result plus the learned correction. Weights are FP32
- * masters with a BF16 copy; the forward pass uses the BF16 weights, FP32
- * accumulation, BF16 activations in inference and FP32 activations in training.
- * Tensors are NHWC float arrays: inputs B*H*W*4, outputs/targets B*H*W*3.
+ * masters with a BF16 copy; the convolutions multiply BF16 weights and BF16
+ * activations on the tensor cores with FP32 accumulation (activations stored in
+ * BF16 in inference, FP32 in training), or, after m1_nn_set_tensor_cores(nn, 0),
+ * FP32 activations on the CUDA cores (the precise path of the gradient checks).
+ * Tensors are NHWC float arrays: inputs B*H*W*7, outputs/targets B*H*W*3.
  * ------------------------------------------------------------------------- */
 typedef struct m1_nn m1_nn;
 
@@ -338,17 +342,21 @@ m1_status m1_nn_set_params(m1_nn* nn, const float* theta, m1_mem mem);
 m1_status m1_nn_get_params(const m1_nn* nn, float* theta, m1_mem mem);
 /* y = N(x) for one batch; bf16 = 1 stores activations in BF16 (inference path). */
 m1_status m1_nn_forward(m1_nn* nn, const float* x, float* y, int bf16, m1_mem mem);
-/* Loss (1/B) sum_b ||N(x_b) - t_b||^2 / ||t_b||^2 and its gradient (FP32 activations). */
+/* Loss (1/B) sum_b ||N(x_b) - t_b||^2 / (H W 3) (mean squared error per output element)
+ * and its gradient. */
 m1_status m1_nn_loss_grad(m1_nn* nn, const float* x, const float* t, double* loss, float* grad, m1_mem mem);
 /* Adam on npairs (x, t) pairs held as consecutive images; batches of the network's size. */
 m1_status m1_nn_train(m1_nn* nn, const float* X, const float* T, int npairs, const m1_train_opts* opts,
                       m1_train_info* info, m1_mem mem);
+/* 1 (default): convolutions on the tensor cores (BF16 operands, FP32 accumulation);
+ * 0: FP32 activations and products on the CUDA cores. Applies to every later call. */
+m1_status m1_nn_set_tensor_cores(m1_nn* nn, int on);
 const char* m1_nn_last_error(const m1_nn* nn);
 
 /* One training pair from the context's own Jacobian (2D, radiation only):
- * r = J(U) e (U NULL = the time-n state), s = ||r|| / sqrt(n), x = [r / s, log sigma]
- * (NHWC, 4 channels), t = (e - J_bj(U)^-1 r) / s (NHWC, 3 channels): the part of
- * the exact inverse that point-block Jacobi misses. */
+ * r = J(U) e (U NULL = the time-n state), s = ||r|| / sqrt(n), x = [r / s, log sigma,
+ * the state channels of U] (NHWC, 7 channels), t = (e - J_bj(U)^-1 r) / s (NHWC,
+ * 3 channels): the part of the exact inverse that point-block Jacobi misses. */
 m1_status m1_nn_make_pair(m1_ctx* ctx, double dt, const double* U, const double* e, float* x, float* t,
                           m1_mem mem);
 

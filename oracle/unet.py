@@ -2,8 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-A 3-level 2D U-Net mapping 4 input channels (the three components of a
-residual vector, scaled, and the normalised log opacity) to 3 output channels.
+A 3-level 2D U-Net mapping 7 input channels (the three components of a
+residual vector, scaled, the normalised log opacity, and the state at which
+the Jacobian is taken: the reduced flux F / (cE) in two channels and the
+normalised log energy; input_planes) to 3 output channels.
 All convolutions are 3x3, stride 1, zero padding 1, weights laid out
 W[ky, kx, ci, co] with bias b[co]; ReLU after every convolution but the last;
 2x2 average pooling down; nearest-neighbour 2x upsampling followed by channel
@@ -12,7 +14,8 @@ concatenation [upsampled, skip]. Arrays are NHWC (batch, y, x, channel).
 The paper has no learned preconditioner; this network and its training are
 the library's own design. The oracle gives the forward pass and the exact
 backward pass of the loss
-    L = (1/B) sum_b ||y_b - t_b||^2 / max(||t_b||^2, tiny)
+    L = (1/B) sum_b ||y_b - t_b||^2 / (H W 3)
+(the mean squared error per output element)
 by plain loops over layers (numpy einsum for each 3x3 tap). Pinned by central
 finite differences (tests/test_oracle_unet.py).
 """
@@ -24,8 +27,9 @@ import numpy as np
 
 # (name, cin, cout, relu) in execution order; "pool"/"up" markers separate levels
 C1, C2, C3 = 16, 32, 32
+CIN = 7
 LAYERS: List[Tuple[str, int, int, bool]] = [
-    ("e1a", 4, C1, True), ("e1b", C1, C1, True),
+    ("e1a", CIN, C1, True), ("e1b", C1, C1, True),
     ("e2a", C1, C2, True), ("e2b", C2, C2, True),
     ("e3a", C2, C3, True), ("e3b", C3, C3, True),
     ("d2a", C3 + C2, C2, True), ("d2b", C2, C1, True),
@@ -69,6 +73,17 @@ def init_params(seed: int = 0) -> np.ndarray:
         p[name + ".w"] = rng.standard_normal((3, 3, ci, co)) * std
         p[name + ".b"] = np.zeros(co)
     return flatten(p)
+
+
+def input_planes(E, Fx, Fy, sigma_f, dx, c):
+    """The four input channels that do not depend on the Krylov vector, from the
+    linearisation state: (log10(sigma_f dx) - 0.5) / 2.5, F_x / (cE) and F_y / (cE)
+    with E floored at 1e-30 and clipped to [-1, 1], and (log10 E + 3) / 3."""
+    E = np.maximum(np.asarray(E, dtype=np.float64), 1e-30)
+    logsig = (np.log10(np.maximum(np.asarray(sigma_f, dtype=np.float64) * dx, 1e-30)) - 0.5) / 2.5
+    fx = np.clip(np.asarray(Fx, dtype=np.float64) / (c * E), -1.0, 1.0)
+    fy = np.clip(np.asarray(Fy, dtype=np.float64) / (c * E), -1.0, 1.0)
+    return np.stack([logsig, fx, fy, (np.log10(E) + 3.0) / 3.0], axis=-1)
 
 
 # ------------------------------------------------------------------ layers
@@ -140,9 +155,8 @@ def forward(theta: np.ndarray, x: np.ndarray, keep: bool = False):
 
 def loss(theta, x, t):
     y = forward(theta, x)
-    num = ((y - t) ** 2).sum(axis=(1, 2, 3))
-    den = np.maximum((t ** 2).sum(axis=(1, 2, 3)), 1e-30)
-    return float((num / den).mean())
+    per = float(np.prod(t.shape[1:]))
+    return float((((y - t) ** 2).sum(axis=(1, 2, 3)) / per).mean())
 
 
 def grad(theta: np.ndarray, x: np.ndarray, t: np.ndarray):
@@ -150,9 +164,9 @@ def grad(theta: np.ndarray, x: np.ndarray, t: np.ndarray):
     p = unflatten(theta)
     y, cache = forward(theta, x, keep=True)
     B = x.shape[0]
-    den = np.maximum((t ** 2).sum(axis=(1, 2, 3)), 1e-30)
-    L = float((((y - t) ** 2).sum(axis=(1, 2, 3)) / den).mean())
-    gy = 2.0 * (y - t) / den[:, None, None, None] / B
+    per = float(np.prod(t.shape[1:]))
+    L = float((((y - t) ** 2).sum(axis=(1, 2, 3)) / per).mean())
+    gy = 2.0 * (y - t) / per / B
     g = {}
     relu = dict((l[0], l[3]) for l in LAYERS)
 

@@ -76,6 +76,8 @@ struct m1_ctx {
     double *Fstar = nullptr, *linework = nullptr;
     m1_nn* nn = nullptr;        // learned preconditioner (not owned)
     float* logsig = nullptr;    // its opacity channel
+    float* nn_static = nullptr; // its four input planes that are fixed within a linear solve (k_nn_static)
+    float* nn_null = nullptr;   // its output for a zero residual at the same iterate (3N, subtracted)
     float* Z32 = nullptr;       // flexible-GMRES basis of preconditioned vectors
     double* pj64 = nullptr;     // dP/dU at the Newton iterate (2D frozen wave speeds), FP64
     float* pj32 = nullptr;      // the same in FP32
@@ -521,6 +523,7 @@ struct Ops64 {
     Dev<double> g;
     const double* U;
     bool precond;
+    int step = 0;                // Arnoldi step of the next M application (unused: M is fixed)
     const double* pj = nullptr;  // dP/dU at U: J v as a linear stencil, else by dual numbers
     bool line = false;           // M^-1: the block-tridiagonal line solve instead of point-block Jacobi
     bool fused() const { return false; }
@@ -552,6 +555,7 @@ struct Ops32 {
     const float* U;
     bool precond;
     bool learned = false;
+    int step = 0;               // Arnoldi step of the next M application (the learned correction: odd steps)
     const float* pj = nullptr;  // dP/dU at U in FP32: J v as a linear stencil, else by dual numbers
     bool mg = false;            // M^-1: one multigrid cycle instead of point-block Jacobi
     // J M^-1 v in one stencil (point-block Jacobi applied while staging)
@@ -583,8 +587,12 @@ struct Ops32 {
             cudaMemcpyAsync(out, in, sizeof(float) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s);
         }
         count(ctx, 1);
-        if (learned) {  // + s N(v / s): the Krylov vectors have unit norm, s = 1 / sqrt(n)
-            nn_apply_add(ctx->nn, in, ctx->N, ctx->logsig, (float)(1.0 / sqrt((double)ctx->n)), out, ctx->s);
+        // + s (N(v / s) - N(0)) on odd Arnoldi steps: the Krylov vectors have unit norm,
+        // s = 1 / sqrt(n); even steps keep the plain point-block Jacobi direction in the
+        // flexible basis, so the learned directions can only add to it
+        if (learned && (step & 1)) {
+            nn_apply_add(ctx->nn, in, ctx->N, ctx->nn_static, ctx->nn_null, (float)(1.0 / sqrt((double)ctx->n)), out,
+                         ctx->s);
             count(ctx, 24);
         }
     }
@@ -672,6 +680,7 @@ m1_status gmres_cycle(m1_ctx* ctx, Ops& ops, T* V, T* w, T* z, const T* r0, doub
                 ops.AM(Vj, w);  // J M^-1 V_j, M^-1 V_j never stored
             } else {
                 T* zj = Z ? Z + (long long)j * ld : z;  // flexible GMRES keeps every preconditioned vector
+                ops.step = j;
                 ops.M(Vj, zj);
                 ops.A(zj, w);
             }
@@ -1163,7 +1172,7 @@ m1_status m1_destroy(m1_ctx* ctx) {
                     ctx->delta, ctx->rhs, ctx->w, ctx->z, ctx->tmp, ctx->V, ctx->xacc, ctx->blocks, ctx->binv,
                     ctx->binv32, ctx->V32, ctx->w32, ctx->z32, ctx->U32, ctx->tmp32, ctx->Fstar, ctx->linework,
                     ctx->partials, ctx->scal_base, ctx->singular, ctx->viol, ctx->ar_partials,
-                    ctx->ar_reorth, ctx->logsig, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32, ctx->bs_part, ctx->bs_sc,
+                    ctx->ar_reorth, ctx->logsig, ctx->nn_static, ctx->nn_null, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32, ctx->bs_part, ctx->bs_sc,
                     ctx->fb, ctx->fbw};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -1515,6 +1524,13 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
         if (use_mg && (newton_iter < 0 || newton_iter % every == 0)) CKS(build_mg(ctx, g32));
         Ops32 ops32{ctx, g32, ctx->U32, pre};
         ops32.learned = learned;
+        if (learned) {  // the network's opacity and state planes at this Newton iterate, and its zero response
+            launch_nn_static_f32(ctx->U32, ctx->N, ctx->d.c, ctx->logsig, ctx->nn_static, ctx->s);
+            CK(cudaMemsetAsync(ctx->tmp32, 0, sizeof(float) * ctx->n, ctx->s));
+            if (nn_null_response(ctx->nn, ctx->tmp32, ctx->N, ctx->nn_static, ctx->nn_null, ctx->s) != M1_OK)
+                return fail(ctx, M1_ERR_CUDA, "learned preconditioner: null response failed");
+            count(ctx, 23);
+        }
         ops32.mg = use_mg;
         if (lin) ops32.pj = ctx->pj32;
         return gmres_mixed(ctx, ops, ops32, b, x, o->gmres_rtol, o->restart, o->gmres_max, o->refine_max, iters,
@@ -1776,6 +1792,8 @@ m1_status m1_set_preconditioner(m1_ctx* ctx, m1_nn* nn) {
     if (nn_height(nn) != ctx->d.n[1] || nn_width(nn) != ctx->d.n[0])
         return fail(ctx, M1_ERR_ARG, "network size differs from the grid (build it for n[1] x n[0], batch 1)");
     CKS(dalloc(ctx, &ctx->logsig, ctx->N));
+    CKS(dalloc(ctx, &ctx->nn_static, 4 * ctx->N));
+    CKS(dalloc(ctx, &ctx->nn_null, 3 * ctx->N));
     ctx->nn = nn;
     ctx->dirty = true;
     return M1_OK;
@@ -1786,6 +1804,7 @@ m1_status m1_nn_make_pair(m1_ctx* ctx, double dt, const double* U, const double*
     if (!ctx || !e || !x || !t) return M1_ERR_ARG;
     if (ctx->dim != 2 || ctx->d.gas_coupling) return fail(ctx, M1_ERR_ARG, "pairs are 2D radiation-only");
     CKS(dalloc(ctx, &ctx->logsig, ctx->N));
+    CKS(dalloc(ctx, &ctx->nn_static, 4 * ctx->N));
     CKS(prepare(ctx));
     CKS(ensure_work(ctx));
     launch_logsig(ctx->sig_f, ctx->N, (ctx->d.hi[0] - ctx->d.lo[0]) / ctx->d.n[0], ctx->logsig, ctx->s);
@@ -1809,15 +1828,16 @@ m1_status m1_nn_make_pair(m1_ctx* ctx, double dt, const double* U, const double*
         xd = x;
         td = t;
     } else {
-        CKS(dalloc(ctx, &ctx->pair_x, 4 * ctx->N));
+        CKS(dalloc(ctx, &ctx->pair_x, 7 * ctx->N));
         CKS(dalloc(ctx, &ctx->pair_t, 3 * ctx->N));
         xd = ctx->pair_x;
         td = ctx->pair_t;
     }
-    launch_pack_pair(ctx->w, ctx->tmp, ctx->N, ctx->logsig, scale, xd, td, ctx->s);
-    count(ctx, 1);
+    launch_nn_static_f64(ctx->U, ctx->N, ctx->d.c, ctx->logsig, ctx->nn_static, ctx->s);
+    launch_pack_pair(ctx->w, ctx->tmp, ctx->N, ctx->nn_static, scale, xd, td, ctx->s);
+    count(ctx, 2);
     if (mem != M1_MEM_DEVICE) {
-        CK(cudaMemcpyAsync(x, xd, sizeof(float) * 4 * ctx->N, cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaMemcpyAsync(x, xd, sizeof(float) * 7 * ctx->N, cudaMemcpyDeviceToHost, ctx->s));
         CK(cudaMemcpyAsync(t, td, sizeof(float) * 3 * ctx->N, cudaMemcpyDeviceToHost, ctx->s));
     }
     return sync(ctx);

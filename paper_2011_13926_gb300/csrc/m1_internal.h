@@ -196,12 +196,18 @@ void launch_realizability(const double* U, int dim, long long N, double c, unsig
                           cudaStream_t s);
 
 // ----------------------------------------------------------------- learned preconditioner (m1_unet.cu)
-m1_status nn_apply_add(m1_nn* nn, const float* v, long long N, const float* logsig, float scale, float* z,
-                       cudaStream_t s);
+// z += scale (N([v / scale, stat]) - y0): stat = the four planes of k_nn_static at the Newton
+// iterate, y0 = nn_null_response at the same iterate (zero3: 3N zero floats)
+m1_status nn_apply_add(m1_nn* nn, const float* v, long long N, const float* stat, const float* y0, float scale,
+                       float* z, cudaStream_t s);
+m1_status nn_null_response(m1_nn* nn, const float* zero3, long long N, const float* stat, float* y0, cudaStream_t s);
 int nn_height(const m1_nn* nn);
 int nn_width(const m1_nn* nn);
 void launch_logsig(const double* sig, long long N, double dx, float* out, cudaStream_t s);
-void launch_pack_pair(const double* r, const double* tt, long long N, const float* logsig, double scale, float* x,
+// the network's opacity and state planes (logsig, f_x, f_y, normalised log E) from U
+void launch_nn_static_f64(const double* U, long long N, double c, const float* logsig, float* stat, cudaStream_t s);
+void launch_nn_static_f32(const float* U, long long N, double c, const float* logsig, float* stat, cudaStream_t s);
+void launch_pack_pair(const double* r, const double* tt, long long N, const float* stat, double scale, float* x,
                       float* t, cudaStream_t s);
 
 }  // namespace m1

@@ -1,20 +1,32 @@
 // m1_unet.cu — the learned preconditioner network: a 3-level 2D U-Net
-// (63,443 parameters), its forward and backward kernels, loss, Adam, and the
+// (63,875 parameters), its forward and backward kernels, loss, Adam, and the
 // packing between Krylov vectors and network tensors.
 //
+// Inputs (7 channels): the Krylov vector (E, F_x, F_y) scaled by s, the
+// normalised log opacity, and the linearisation state of the Jacobian: the
+// reduced flux f = F / (cE) (two channels, clamped to [-1, 1]) and the
+// normalised log energy (log10 E + 3) / 3.
+//
 // Layers (all 3x3 convolutions, stride 1, zero padding, weights W[ky][kx][ci][co]):
-//   e1a 4->16, e1b 16->16 | pool | e2a 16->32, e2b 32->32 | pool |
+//   e1a 7->16, e1b 16->16 | pool | e2a 16->32, e2b 32->32 | pool |
 //   e3a 32->32, e3b 32->32 | up, cat(e2b) | d2a 64->32, d2b 32->16 | up, cat(e1b) |
 //   d1a 32->16, d1b 16->3 (linear); ReLU after every other convolution.
 // Tensors are NHWC. Activations are stored in FP32 for training and in BF16
 // for inference; weights are FP32 masters with a BF16 copy (the forward pass
 // always uses BF16-rounded weights); every product is accumulated in FP32.
 //
-// The convolution kernel stages a 16x16-pixel tile plus halo of 16 input
-// channels and the matching 9x16x16 weight block in shared memory; each thread
-// owns one output pixel and 16 output channels. The backward data pass is the
-// same kernel on the flipped, transposed weights; the weight gradient is a
-// per-CTA partial sum over pixel tiles reduced in a fixed order.
+// Two convolution kernels:
+//   - k_conv3x3_tc, the default: an implicit GEMM on the tensor cores
+//     (mma.sync m16n8k16, BF16 operands, FP32 accumulation). A CTA stages a
+//     16 x 16-pixel tile plus its halo (activations rounded to BF16) and the
+//     layer's weights in shared memory; each warp multiplies two 16-pixel rows
+//     (M) by all output channels (N), K = 9 taps x input channels, A fragments
+//     by ldmatrix from a padded pixel stride (no bank conflicts).
+//   - k_conv3x3, FP32 on the CUDA cores (FP32 activations and products): the
+//     precise path for gradient checks (m1_nn_set_tensor_cores(nn, 0)).
+// The backward data pass is the same convolution on the flipped, transposed
+// weights; the weight gradient is a per-CTA partial sum over pixel tiles on
+// the CUDA cores, reduced in a fixed order.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -36,8 +48,9 @@ struct LayerSpec {
     bool relu;
 };
 constexpr int kLayers = 10;
+constexpr int kCin0 = 7;  // input channels
 const LayerSpec kSpec[kLayers] = {
-    {"e1a", 4, 16, true},  {"e1b", 16, 16, true}, {"e2a", 16, 32, true}, {"e2b", 32, 32, true},
+    {"e1a", kCin0, 16, true},  {"e1b", 16, 16, true}, {"e2a", 16, 32, true}, {"e2b", 32, 32, true},
     {"e3a", 32, 32, true}, {"e3b", 32, 32, true}, {"d2a", 64, 32, true}, {"d2b", 32, 16, true},
     {"d1a", 32, 16, true}, {"d1b", 16, 3, false},
 };
@@ -116,6 +129,131 @@ __global__ void __launch_bounds__(256) k_conv3x3(const Tin* __restrict__ x, int 
             }
         }
     }
+}
+
+// ------------------------------------------------------------------ tensor-core convolution
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                               unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldmatrix_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
+                                            const void* smem_ptr) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem_ptr));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+// Shared memory of k_conv3x3_tc<CINP, COUTP>: the 18 x 18 halo tile with a pixel
+// stride of CINP + 8 BF16 (16-byte rows for ldmatrix, consecutive pixels 16
+// bytes apart modulo 128: conflict-free), then the weights as [tap][co][ci] with
+// the same ci stride.
+__host__ __device__ constexpr int tc_smem_bytes(int cinp, int coutp) {
+    return (18 * 18 * (cinp + 8) + 9 * coutp * (cinp + 8)) * 2;
+}
+
+// y[b,i,j,co] = bias[co] + sum x[b,i+dy-1,j+dx-1,ci] w[dy][dx][ci][co] with BF16
+// operands and FP32 accumulation; optional ReLU and multiplicative mask (mask > 0).
+// CINP >= cin and COUTP >= cout are the padded GEMM sizes (multiples of 16 and 8).
+// Grid: (ceil(W/16), ceil(H/16), B), 256 threads; warp w owns tile rows 2w, 2w+1.
+template <int CINP, int COUTP, class Tin, class Tout>
+__global__ void __launch_bounds__(256) k_conv3x3_tc(const Tin* __restrict__ x, int cin,
+                                                    const __nv_bfloat16* __restrict__ w16,
+                                                    const float* __restrict__ bias, Tout* __restrict__ y, int cout,
+                                                    int H, int W, int relu, const float* __restrict__ mask) {
+    static_assert(CINP % 16 == 0 && COUTP % 8 == 0, "GEMM tile sizes");
+    constexpr int XS = CINP + 8;
+    constexpr int NT = COUTP / 8;
+    extern __shared__ __align__(16) unsigned char tc_smem[];
+    __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(tc_smem);
+    __nv_bfloat16* ws = xs + 18 * 18 * XS;
+    const int j0 = blockIdx.x * 16, i0 = blockIdx.y * 16, b = blockIdx.z;
+    const long long img = (long long)b * H * W;
+    for (int t = threadIdx.x; t < 18 * 18 * CINP; t += 256) {
+        const int c = t % CINP, px = (t / CINP) % 18, py = t / (CINP * 18);
+        const int gi = i0 + py - 1, gj = j0 + px - 1;
+        float v = 0.f;
+        if (c < cin && gi >= 0 && gi < H && gj >= 0 && gj < W) v = ld(x, (img + (long long)gi * W + gj) * cin + c);
+        xs[(py * 18 + px) * XS + c] = __float2bfloat16(v);
+    }
+    for (int t = threadIdx.x; t < 9 * COUTP * CINP; t += 256) {
+        const int ci = t % CINP, co = (t / CINP) % COUTP, tap = t / (CINP * COUTP);
+        __nv_bfloat16 v = __float2bfloat16(0.f);
+        if (ci < cin && co < cout) v = w16[((long long)tap * cin + ci) * cout + co];
+        ws[(tap * COUTP + co) * XS + ci] = v;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int mi = lane >> 3, rr = lane & 7;  // ldmatrix: this lane's matrix and row
+    const int apx = ((mi & 1) ? 8 : 0) + rr, ach = (mi >> 1) ? 8 : 0;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.f;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+        for (int kc = 0; kc < CINP / 16; ++kc) {
+            unsigned bfr[NT][2];
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                const __nv_bfloat16* wr = ws + (tap * COUTP + n * 8 + g) * XS + kc * 16 + 2 * tq;
+                bfr[n][0] = *reinterpret_cast<const unsigned*>(wr);
+                bfr[n][1] = *reinterpret_cast<const unsigned*>(wr + 8);
+            }
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int row = warp * 2 + m;
+                unsigned a0, a1, a2, a3;
+                ldmatrix_x4(a0, a1, a2, a3, xs + ((row + dy) * 18 + apx + dx) * XS + kc * 16 + ach);
+#pragma unroll
+                for (int n = 0; n < NT; ++n) mma_bf16_16816(acc[m][n], a0, a1, a2, a3, bfr[n][0], bfr[n][1]);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int i = i0 + warp * 2 + m;
+        if (i >= H) continue;
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {  // c0,c1: pixel g; c2,c3: pixel g + 8
+                const int j = j0 + g + 8 * h;
+                if (j >= W) continue;
+                const long long o = (img + (long long)i * W + j) * cout;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int co = n * 8 + 2 * tq + e;
+                    if (co < cout) {
+                        float v = acc[m][n][2 * h + e] + (bias ? bias[co] : 0.f);
+                        if (relu) v = fmaxf(v, 0.f);
+                        if (mask) v = mask[o + co] > 0.f ? v : 0.f;
+                        st(y, o + co, v);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// BF16 flipped weights for the backward data pass on the tensor cores
+__global__ void k_flip_weights16(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wt, int cin,
+                                 int cout) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 9 * cin * cout) return;
+    const int co = t % cout, ci = (t / cout) % cin, tap = t / (cout * cin);
+    wt[((long long)(8 - tap) * cout + co) * cin + ci] = w[t];
 }
 
 // Wt[dy][dx][co][ci] = W[2-dy][2-dx][ci][co]: the backward data pass as a convolution
@@ -292,39 +430,27 @@ __global__ void k_up_cat_bwd(const float* __restrict__ gy, float* __restrict__ g
     }
 }
 
-// per-sample relative squared error and its gradient dy = 2 (y - t) / ||t_b||^2 / B
+// mean squared error per output element, L = (1/B) sum_b ||y_b - t_b||^2 / per
+// (per = H W 3; the pairs' inputs have unit RMS in their residual channels),
+// and its gradient dy = 2 (y - t) / per / B
 __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ t, long long per, int B,
                        float* __restrict__ gy, double* __restrict__ loss) {
-    __shared__ double red[2][8];
+    __shared__ double red[8];
     const int b = blockIdx.x;
-    double num = 0.0, den = 0.0;
+    double num = 0.0;
     for (long long k = threadIdx.x; k < per; k += blockDim.x) {
         const double d = (double)y[b * per + k] - (double)t[b * per + k];
         num += d * d;
-        den += (double)t[b * per + k] * t[b * per + k];
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        num += __shfl_xor_sync(0xffffffffu, num, o);
-        den += __shfl_xor_sync(0xffffffffu, den, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = num;
-        red[1][threadIdx.x >> 5] = den;
-    }
+    for (int o = 16; o > 0; o >>= 1) num += __shfl_xor_sync(0xffffffffu, num, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = num;
     __syncthreads();
-    __shared__ double tot[2];
     if (threadIdx.x == 0) {
-        double a = 0.0, c = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-            a += red[0][q];
-            c += red[1][q];
-        }
-        tot[0] = a;
-        tot[1] = fmax(c, 1e-30);
-        loss[b] = a / tot[1] / B;
+        double a = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += red[q];
+        loss[b] = a / (double)per / B;
     }
-    __syncthreads();
-    const float sc = (float)(2.0 / tot[1] / B);
+    const float sc = (float)(2.0 / (double)per / B);
     for (long long k = threadIdx.x; k < per; k += blockDim.x) gy[b * per + k] = sc * (y[b * per + k] - t[b * per + k]);
 }
 
@@ -353,27 +479,40 @@ __global__ void k_round_bf16(const float* __restrict__ a, float* __restrict__ r,
 }
 
 // network input from a component-major Krylov vector v (E, Fx, Fy; N = H*W
-// each): x = [v / s, logsig] in NHWC, s = scale
+// each): x = [v / s, static] in NHWC (7 channels), s = scale, static the four
+// planes of the opacity and state channels (k_nn_static)
 template <class T>
-__global__ void k_pack_input(const float* __restrict__ v, long long N, const float* __restrict__ logsig, float scale,
+__global__ void k_pack_input(const float* __restrict__ v, long long N, const float* __restrict__ stat, float scale,
                              T* __restrict__ x) {
     const float inv = 1.f / scale;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        st(x, 4 * p + 0, v[p] * inv);
-        st(x, 4 * p + 1, v[N + p] * inv);
-        st(x, 4 * p + 2, v[2 * N + p] * inv);
-        st(x, 4 * p + 3, logsig[p]);
+        st(x, kCin0 * p + 0, v[p] * inv);
+        st(x, kCin0 * p + 1, v[N + p] * inv);
+        st(x, kCin0 * p + 2, v[2 * N + p] * inv);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) st(x, kCin0 * p + 3 + c, stat[c * N + p]);
     }
 }
 
-// z (component-major) += scale * y (NHWC, 3 channels)
+// z (component-major) += scale * (y - y0) (NHWC, 3 channels; y0 may be null)
 template <class T>
-__global__ void k_unpack_add(const T* __restrict__ y, long long N, float scale, float* __restrict__ z) {
+__global__ void k_unpack_add(const T* __restrict__ y, const float* __restrict__ y0, long long N, float scale,
+                             float* __restrict__ z) {
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        z[p] += scale * ld(y, 3 * p + 0);
-        z[N + p] += scale * ld(y, 3 * p + 1);
-        z[2 * N + p] += scale * ld(y, 3 * p + 2);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float v = ld(y, 3 * p + c) - (y0 ? y0[3 * p + c] : 0.f);
+            z[c * N + p] += scale * v;
+        }
     }
+}
+
+// y0 = the network's output (FP32, NHWC) for a zero residual: the part of N
+// that does not depend on the Krylov vector
+template <class T>
+__global__ void k_copy_out(const T* __restrict__ y, long long n, float* __restrict__ y0) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        y0[k] = ld(y, k);
 }
 
 __global__ void k_widen(const __nv_bfloat16* __restrict__ a, float* __restrict__ b, long long n) {
@@ -401,6 +540,8 @@ struct m1_nn {
     float* grad = nullptr;
     float *adam_m = nullptr, *adam_v = nullptr;
     float* wflip = nullptr;        // flipped weights of one layer (backward data pass)
+    __nv_bfloat16* wflip16 = nullptr;  // the same in BF16 (tensor-core backward data pass)
+    int tc = 1;                    // convolutions on the tensor cores (1) or FP32 CUDA cores (0)
     float* dwpart = nullptr;       // per-CTA weight-gradient partials
     long long dwpart_size = 0;
     // activations, FP32 (training) and BF16 (inference); index by layer output + the cat/pool tensors
@@ -424,7 +565,7 @@ enum Slot {
 long long slot_elems(const m1_nn* nn, int sl) {
     const long long f = (long long)nn->B * nn->H * nn->W, h = f / 4, q = f / 16;
     switch (sl) {
-        case S_IN: return f * 4;
+        case S_IN: return f * kCin0;
         case S_E1A: case S_E1B: return f * 16;
         case S_P1: return h * 16;
         case S_E2A: case S_E2B: return h * 32;
@@ -460,14 +601,50 @@ void conv(m1_nn* nn, const Tin* x, int cin, const float* w, const float* b, Tout
     k_conv3x3<Tin, Tout><<<grid, 256, 0, nn->s>>>(x, cin, w, b, y, cout, H, W, relu, mask);
 }
 
+template <int CINP, int COUTP, class Tin, class Tout>
+void conv_tc_launch(m1_nn* nn, const Tin* x, int cin, const __nv_bfloat16* w16, const float* b, Tout* y, int cout,
+                    int H, int W, int relu, const float* mask) {
+    constexpr int bytes = tc_smem_bytes(CINP, COUTP);
+    static bool attr_set = false;  // per instantiation; the attribute is a property of the function
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_conv3x3_tc<CINP, COUTP, Tin, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        attr_set = true;
+    }
+    dim3 grid((W + 15) / 16, (H + 15) / 16, nn->B);
+    k_conv3x3_tc<CINP, COUTP, Tin, Tout><<<grid, 256, bytes, nn->s>>>(x, cin, w16, b, y, cout, H, W, relu, mask);
+}
+
+// the tensor-core convolution with the smallest GEMM tile that holds (cin, cout)
+template <class Tin, class Tout>
+void conv_tc(m1_nn* nn, const Tin* x, int cin, const __nv_bfloat16* w16, const float* b, Tout* y, int cout, int H,
+             int W, int relu, const float* mask) {
+#define TC_CASE(CI, CO)                                                                     \
+    if (cin <= CI && cout <= CO) {                                                         \
+        conv_tc_launch<CI, CO, Tin, Tout>(nn, x, cin, w16, b, y, cout, H, W, relu, mask); \
+        return;                                                                             \
+    }
+    TC_CASE(16, 8)
+    TC_CASE(16, 16)
+    TC_CASE(16, 32)
+    TC_CASE(32, 16)
+    TC_CASE(32, 32)
+    TC_CASE(32, 64)
+    TC_CASE(64, 32)
+#undef TC_CASE
+}
+
 // forward pass; T = float (training, keeps every activation) or bf16 (inference)
 template <class T>
 void forward(m1_nn* nn, T* const* A) {
     const int H = nn->H, W = nn->W, B = nn->B;
     const float* th = nn->theta_r;
     auto L = [&](int l, const T* in, T* out, int H_, int W_) {
-        conv<T, T>(nn, in, kSpec[l].cin, th + nn->woff[l], th + nn->boff[l], out, kSpec[l].cout, H_, W_,
-                   kSpec[l].relu ? 1 : 0, nullptr);
+        if (nn->tc)
+            conv_tc<T, T>(nn, in, kSpec[l].cin, nn->theta16 + nn->woff[l], th + nn->boff[l], out, kSpec[l].cout, H_,
+                          W_, kSpec[l].relu ? 1 : 0, nullptr);
+        else
+            conv<T, T>(nn, in, kSpec[l].cin, th + nn->woff[l], th + nn->boff[l], out, kSpec[l].cout, H_, W_,
+                       kSpec[l].relu ? 1 : 0, nullptr);
     };
     L(0, A[S_IN], A[S_E1A], H, W);
     L(1, A[S_E1A], A[S_E1B], H, W);
@@ -496,8 +673,14 @@ void layer_backward(m1_nn* nn, int l, const float* in, const float* out, float* 
     k_reduce_parts<<<grid_for(nw + co), 256, 0, nn->s>>>(nn->dwpart, nw + co, nw + co, kDwGrid, nn->grad + nn->woff[l]);
     // biases follow the weights of the same layer in the flat vector (boff = woff + nw)
     if (gin) {
-        k_flip_weights<<<(int)((nw + 255) / 256), 256, 0, nn->s>>>(nn->theta_r + nn->woff[l], nn->wflip, ci, co);
-        conv<float, float>(nn, gout, co, nn->wflip, nullptr, gin, ci, H, W, 0, nullptr);
+        if (nn->tc) {
+            k_flip_weights16<<<(int)((nw + 255) / 256), 256, 0, nn->s>>>(nn->theta16 + nn->woff[l], nn->wflip16, ci,
+                                                                          co);
+            conv_tc<float, float>(nn, gout, co, nn->wflip16, nullptr, gin, ci, H, W, 0, nullptr);
+        } else {
+            k_flip_weights<<<(int)((nw + 255) / 256), 256, 0, nn->s>>>(nn->theta_r + nn->woff[l], nn->wflip, ci, co);
+            conv<float, float>(nn, gout, co, nn->wflip, nullptr, gin, ci, H, W, 0, nullptr);
+        }
     }
 }
 
@@ -551,17 +734,34 @@ __global__ void k_logsig(const double* __restrict__ sig, long long N, double dx,
         out[p] = (float)((log10(fmax(sig[p] * dx, 1e-30)) - 0.5) / 2.5);
 }
 
-// training pair from FP64 vectors: x = [r/s, logsig] (4 ch), t = tt/s (3 ch), NHWC
+// The four input planes that do not depend on the Krylov vector, from the
+// linearisation state U (E, F_x, F_y component-major, FP64 or FP32):
+// stat[0] = logsig, stat[1..2] = F / (c max(E, 1e-30)) clamped to [-1, 1],
+// stat[3] = (log10 max(E, 1e-30) + 3) / 3.
+template <class R>
+__global__ void k_nn_static(const R* __restrict__ U, long long N, double c, const float* __restrict__ logsig,
+                            float* __restrict__ stat) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        const double E = fmax((double)U[p], 1e-30);
+        const double inv = 1.0 / (c * E);
+        stat[p] = logsig[p];
+        stat[N + p] = (float)fmin(fmax((double)U[N + p] * inv, -1.0), 1.0);
+        stat[2 * N + p] = (float)fmin(fmax((double)U[2 * N + p] * inv, -1.0), 1.0);
+        stat[3 * N + p] = (float)((log10(E) + 3.0) / 3.0);
+    }
+}
+
+// training pair from FP64 vectors: x = [r/s, static] (7 ch), t = tt/s (3 ch), NHWC
 __global__ void k_pack_pair(const double* __restrict__ r, const double* __restrict__ tt, long long N,
-                            const float* __restrict__ logsig, double scale, float* __restrict__ x,
+                            const float* __restrict__ stat, double scale, float* __restrict__ x,
                             float* __restrict__ t) {
     const double inv = 1.0 / scale;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
         for (int c = 0; c < 3; ++c) {
-            x[4 * p + c] = (float)(r[(long long)c * N + p] * inv);
+            x[kCin0 * p + c] = (float)(r[(long long)c * N + p] * inv);
             t[3 * p + c] = (float)(tt[(long long)c * N + p] * inv);
         }
-        x[4 * p + 3] = logsig[p];
+        for (int c = 0; c < 4; ++c) x[kCin0 * p + 3 + c] = stat[(long long)c * N + p];
     }
 }
 
@@ -569,20 +769,41 @@ namespace m1 {
 void launch_logsig(const double* sig, long long N, double dx, float* out, cudaStream_t s) {
     k_logsig<<<grid_for(N), 256, 0, s>>>(sig, N, dx, out);
 }
-void launch_pack_pair(const double* r, const double* tt, long long N, const float* logsig, double scale, float* x,
+void launch_pack_pair(const double* r, const double* tt, long long N, const float* stat, double scale, float* x,
                       float* t, cudaStream_t s) {
-    k_pack_pair<<<grid_for(N), 256, 0, s>>>(r, tt, N, logsig, scale, x, t);
+    k_pack_pair<<<grid_for(N), 256, 0, s>>>(r, tt, N, stat, scale, x, t);
 }
-// inference inside (F)GMRES: z += scale * N(pack(v / scale)) on the context's stream
-m1_status nn_apply_add(m1_nn* nn, const float* v, long long N, const float* logsig, float scale, float* z,
-                       cudaStream_t s) {
+void launch_nn_static_f64(const double* U, long long N, double c, const float* logsig, float* stat, cudaStream_t s) {
+    k_nn_static<double><<<grid_for(N), 256, 0, s>>>(U, N, c, logsig, stat);
+}
+void launch_nn_static_f32(const float* U, long long N, double c, const float* logsig, float* stat, cudaStream_t s) {
+    k_nn_static<float><<<grid_for(N), 256, 0, s>>>(U, N, c, logsig, stat);
+}
+// inference inside (F)GMRES: z += scale * (N(pack(v / scale, static)) - y0) on the
+// context's stream, y0 from nn_null_response (null: not subtracted)
+m1_status nn_apply_add(m1_nn* nn, const float* v, long long N, const float* stat, const float* y0, float scale,
+                       float* z, cudaStream_t s) {
     if (!nn || (long long)nn->H * nn->W != N || nn->B != 1) return M1_ERR_ARG;
     cudaStream_t keep = nn->s;
     nn->s = s;
     __nv_bfloat16* const* A = nn->act16.data();
-    k_pack_input<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(v, N, logsig, scale, nn->act16[S_IN]);
+    k_pack_input<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(v, N, stat, scale, nn->act16[S_IN]);
     forward<__nv_bfloat16>(nn, A);
-    k_unpack_add<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(nn->act16[S_OUT], N, scale, z);
+    k_unpack_add<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(nn->act16[S_OUT], y0, N, scale, z);
+    nn->s = keep;
+    return cudaGetLastError() == cudaSuccess ? M1_OK : M1_ERR_CUDA;
+}
+// y0 (3N floats, NHWC) = N(pack(0, static)): the network's response to a zero
+// residual at this state, subtracted in every application so that the learned
+// correction of a zero vector is zero (flexible GMRES would otherwise see the
+// same field added to every preconditioned vector)
+m1_status nn_null_response(m1_nn* nn, const float* zero3, long long N, const float* stat, float* y0, cudaStream_t s) {
+    if (!nn || (long long)nn->H * nn->W != N || nn->B != 1) return M1_ERR_ARG;
+    cudaStream_t keep = nn->s;
+    nn->s = s;
+    k_pack_input<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(zero3, N, stat, 1.f, nn->act16[S_IN]);
+    forward<__nv_bfloat16>(nn, nn->act16.data());
+    k_copy_out<__nv_bfloat16><<<grid_for(3 * N), 256, 0, s>>>(nn->act16[S_OUT], 3 * N, y0);
     nn->s = keep;
     return cudaGetLastError() == cudaSuccess ? M1_OK : M1_ERR_CUDA;
 }
@@ -632,6 +853,7 @@ m1_status m1_nn_create(int H, int W, int batch, void* stream, m1_nn** out) {
     NAL(nn->adam_m, off);
     NAL(nn->adam_v, off);
     NAL(nn->wflip, maxw);
+    NAL(nn->wflip16, maxw);
     nn->dwpart_size = (long long)kDwGrid * maxw;
     NAL(nn->dwpart, nn->dwpart_size);
     NAL(nn->loss_dev, batch);
@@ -658,8 +880,8 @@ m1_status m1_nn_create(int H, int W, int batch, void* stream, m1_nn** out) {
 m1_status m1_nn_destroy(m1_nn* nn) {
     if (!nn) return M1_OK;
     cudaStreamSynchronize(nn->s);
-    void* p[] = {nn->theta, nn->theta_r, nn->theta16, nn->grad, nn->adam_m, nn->adam_v, nn->wflip, nn->dwpart,
-                 nn->loss_dev};
+    void* p[] = {nn->theta, nn->theta_r, nn->theta16, nn->grad, nn->adam_m, nn->adam_v, nn->wflip, nn->wflip16,
+                 nn->dwpart, nn->loss_dev};
     for (void* q : p)
         if (q) cudaFree(q);
     for (auto* q : nn->act)
@@ -793,6 +1015,12 @@ m1_status m1_nn_train(m1_nn* nn, const float* X, const float* T, int npairs, con
         info->first_loss = first;
         info->final_loss = last;
     }
+    return M1_OK;
+}
+
+m1_status m1_nn_set_tensor_cores(m1_nn* nn, int on) {
+    if (!nn) return M1_ERR_ARG;
+    nn->tc = on ? 1 : 0;
     return M1_OK;
 }
 

@@ -173,6 +173,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_nn_loss_grad": (I, [P, P, P, C.POINTER(D), P, I]),
         "m1_nn_train": (I, [P, P, P, I, C.POINTER(TrainOpts), C.POINTER(TrainInfo), I]),
         "m1_nn_last_error": (C.c_char_p, [P]),
+        "m1_nn_set_tensor_cores": (I, [P, I]),
         "m1_nn_make_pair": (I, [P, D, P, P, P, P, I]),
         "m1_set_preconditioner": (I, [P, P]),
         "m1_set_velocity": (I, [P, P, P, P, I]),
@@ -257,6 +258,7 @@ class Context:
         self.dim = desc.dim
         self.N = desc.n[0] * desc.n[1] * desc.n[2]
         self.nu = 1 + desc.dim + (1 if desc.gas_coupling else 0)
+        self.shape2d = (desc.n[1], desc.n[0])
 
     def close(self):
         """m1_destroy: free the context's device memory."""
@@ -331,6 +333,15 @@ class Context:
         pF, mF, _ = _ptr(F)
         pt, mt, _ = _ptr(T)
         self._call("m1_get_state", pe, pF, pt, _check_mem(me, mF, mt if pt else None))
+        return out
+
+    def get_state_vector(self, out):
+        """The current state as one unknown vector [E, F_0.., (T)] written into ``out``
+        (a contiguous float64 numpy array or device tensor of n_u N values)."""
+        p, m, k = _ptr(out)
+        N = self.N
+        pT = p + 8 * (1 + self.dim) * N if self.nu == 2 + self.dim else None
+        self._call("m1_get_state", p, p + 8 * N, pT, m)
         return out
 
     def get_solution(self, out=None):
@@ -455,7 +466,7 @@ class Context:
         pe, me, ke = _ptr(e)
         pu, mu, ku = _ptr(U)
         if out is None:
-            x = np.empty(4 * self.N, dtype=np.float32)
+            x = np.empty(7 * self.N, dtype=np.float32)
             t = np.empty(3 * self.N, dtype=np.float32)
         else:
             x, t = out
@@ -569,6 +580,10 @@ class Net:
         st = getattr(self.lib, name)(self.h, *args)
         if st != M1_OK:
             raise M1Error(st, self.lib.m1_nn_last_error(self.h).decode())
+
+    def set_tensor_cores(self, on: bool = True):
+        """m1_nn_set_tensor_cores: BF16 tensor-core convolutions (default) or FP32 CUDA-core ones."""
+        self._call("m1_nn_set_tensor_cores", int(bool(on)))
 
     def set_params(self, theta):
         p, m, k = _ptr(theta, dtype=np.float32)

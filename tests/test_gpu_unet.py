@@ -3,8 +3,12 @@
 flexible GMRES with the trained network (A/B against point-block Jacobi).
 
 Tolerances: the GPU forward pass uses BF16-rounded weights (the oracle is given
-the same rounded weights) and FP32 accumulation: FP32 activations 1e-5
-relative, BF16 activations 3e-2; gradients 1e-4 relative in the 2-norm.
+the same rounded weights) and FP32 accumulation. CUDA-core path (FP32 products):
+FP32 activations 1e-5 relative, BF16 activations 3e-2; gradients 1e-4 relative in
+the 2-norm. Tensor-core path (BF16 operands, FP32 accumulation): every
+convolution input is rounded to BF16 (relative 2^-9 per operand), so outputs
+3e-2 and gradients 5e-2 relative in the 2-norm, on images of several 16 x 16
+tiles with ragged edges.
 """
 import numpy as np
 import pytest
@@ -34,14 +38,15 @@ def m1mod():
     return m1
 
 
-def _net_case(m1, B=2, H=8, W=12, seed=0):
+def _net_case(m1, B=2, H=8, W=12, seed=0, tc=False):
     net = m1.Net(H, W, B)
+    net.set_tensor_cores(tc)
     p = unet.unflatten(unet.init_params(seed))
     p["d1b.w"] = p["d1b.w"] * 1e3  # O(1) outputs for the comparisons
     theta = unet.flatten(p).astype(np.float32)
     net.set_params(theta)
     rng = np.random.default_rng(seed + 1)
-    x = rng.standard_normal((B, H, W, 4)).astype(np.float32)
+    x = rng.standard_normal((B, H, W, unet.CIN)).astype(np.float32)
     t = rng.standard_normal((B, H, W, 3)).astype(np.float32)
     return net, bf16_round(theta).astype(np.float64), x, t
 
@@ -75,22 +80,54 @@ def test_gradient_matches_oracle(m1mod):
         assert np.linalg.norm(a - b) <= 1e-4 * max(np.linalg.norm(b), 1e-12), name
 
 
+@pytest.mark.parametrize("bf16", [False, True])
+def test_forward_tensor_cores_match_oracle(m1mod, bf16):
+    B, H, W = 2, 20, 36  # 2 x 3 tiles of 16 x 16, ragged in both directions
+    net, th, x, _ = _net_case(m1mod, B=B, H=H, W=W, seed=7, tc=True)
+    y = net.forward(x.ravel(), bf16=bf16).reshape(B, H, W, 3)
+    ref = unet.forward(th, bf16_round(x).astype(np.float64))
+    assert np.linalg.norm(y - ref) <= 3e-2 * np.linalg.norm(ref)
+    # the CUDA-core path on the same input agrees to the same tolerance pixel-block by pixel-block
+    net.set_tensor_cores(False)
+    y32 = net.forward(x.ravel(), bf16=bf16).reshape(B, H, W, 3)
+    for i0 in (0, 16):
+        for j0 in (0, 16, 32):
+            a, b = y[:, i0:i0 + 16, j0:j0 + 16], y32[:, i0:i0 + 16, j0:j0 + 16]
+            assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b), (i0, j0)
+
+
+def test_gradient_tensor_cores_match_oracle(m1mod):
+    net, th, x, t = _net_case(m1mod, B=2, H=20, W=36, seed=9, tc=True)
+    L, g = net.loss_grad(x.ravel(), t.ravel())
+    Lr, gr = unet.grad(th, x.astype(np.float64), t.astype(np.float64))
+    assert L == pytest.approx(Lr, rel=3e-2)
+    k = 0
+    for name, shp in unet.param_shapes():
+        m = int(np.prod(shp))
+        a, b = g[k:k + m], gr[k:k + m]
+        k += m
+        assert np.linalg.norm(a - b) <= 5e-2 * max(np.linalg.norm(b), 1e-12), name
+
+
 def test_make_pair_matches_oracle(m1mod):
     p = si.gaussian_lognormal_2d(16, 31, dt_factor=20.0)
     s = Scheme(p)
+    rng = np.random.default_rng(4)
+    N = s.N
     u = p.state_vector()
-    e = np.random.default_rng(4).standard_normal(u.size)
+    u[N:3 * N] = 1.3 * np.tile(u[:N], 2) * rng.uniform(-1.0, 1.0, 2 * N)  # some cells beyond |F| = cE
+    e = rng.standard_normal(u.size)
     ctx = m1mod.context_from_problem(p)
-    x, t = ctx.make_pair(p.dt, e)
+    x, t = ctx.make_pair(p.dt, e, U=u)
     r = s.jv(u, e)
     Minv = block_jacobi(s.diag_blocks(u), s.N, s.nu)
     tt = e - Minv(r)
     scale = np.linalg.norm(r) / np.sqrt(r.size)
     N = s.N
-    xr = np.stack([r[k * N:(k + 1) * N] / scale for k in range(3)]
-                  + [(np.log10(p.sigma_f.ravel() * p.dx[0]) - 0.5) / 2.5], axis=1)
+    planes = unet.input_planes(u[:N], u[N:2 * N], u[2 * N:3 * N], p.sigma_f.ravel(), p.dx[0], p.c)
+    xr = np.concatenate([np.stack([r[k * N:(k + 1) * N] / scale for k in range(3)], axis=1), planes], axis=1)
     tr = np.stack([tt[k * N:(k + 1) * N] / scale for k in range(3)], axis=1)
-    assert np.abs(x.reshape(N, 4) - xr).max() <= 1e-5 * np.abs(xr).max()
+    assert np.abs(x.reshape(N, unet.CIN) - xr).max() <= 1e-5 * np.abs(xr).max()
     assert np.abs(t.reshape(N, 3) - tr).max() <= 1e-5 * np.abs(tr).max()
 
 

@@ -7,7 +7,8 @@ from oracle import unet
 
 
 def test_param_count():
-    assert unet.num_params() == 63443
+    # 9 ci co + co per layer: 7->16, 16->16, 16->32, 32->32, 32->32, 32->32, 64->32, 32->16, 32->16, 16->3
+    assert unet.num_params() == 63875
 
 
 def test_conv_identity_and_shift():
@@ -38,7 +39,7 @@ def test_gradient_matches_central_differences():
     p = unet.unflatten(unet.init_params(3))
     p["d1b.w"] = p["d1b.w"] * 1e3
     theta = unet.flatten(p)
-    x = rng.standard_normal((2, 8, 8, 4))
+    x = rng.standard_normal((2, 8, 8, unet.CIN))
     t = rng.standard_normal((2, 8, 8, 3))
     L, g = unet.grad(theta, x, t)
     assert L == pytest.approx(unet.loss(theta, x, t), rel=1e-14)
