@@ -40,24 +40,45 @@ def source_hash(files) -> str:
     return h.hexdigest()[:16]
 
 
-def read_launches(path):
-    """[(id, kernel, {metric: value in bytes or seconds})] in launch order."""
+def read_launches(path, by_grid=False):
+    """[(id, kernel, {metric: value in bytes or seconds})] in launch order (by_grid: the
+    kernel name carries its grid size, so that launches of one kernel on different
+    grids, e.g. multigrid levels, stay apart)."""
     rows = OrderedDict()
     with open(path, newline="") as f:
         lines = [ln for ln in f if ln.startswith('"')]  # ncu prints its own log lines before the CSV
     for r in csv.DictReader(lines):
         key = r["ID"]
-        ent = rows.setdefault(key, [r["Kernel Name"], {}])
+        label = r["Kernel Name"] + (f" grid {r['Grid Size']}" if by_grid else "")
+        ent = rows.setdefault(key, [label, {}])
         unit = r.get("Metric Unit", "").strip().lower()
         val = float(r["Metric Value"].replace(",", ""))
         ent[1][r["Metric Name"]] = val * _SCALE.get(unit, 1.0)
     return [(k, v[0], v[1]) for k, v in rows.items()]
 
 
-def summarise(launches, select=None, units_regex=None):
+def short_name(name: str) -> str:
+    """Kernel name without its parameter list and return type."""
+    depth, cut = 0, len(name)
+    for i, ch in enumerate(name):  # the first '(' outside template brackets opens the parameter list
+        if ch == "<":
+            depth += 1
+        elif ch == ">":
+            depth -= 1
+        elif ch == "(" and depth == 0:
+            cut = i
+            break
+    out = name[:cut]
+    return out[5:] if out.startswith("void ") else out
+
+
+def summarise(launches, select=None, units_regex=None, short=False, only_selected=False):
     per = OrderedDict()
     total_t = 0.0
     for _, name, m in launches:
+        if short:
+            grid = name[name.rfind(" grid "):] if " grid " in name else ""
+            name = short_name(name[:len(name) - len(grid)] if grid else name) + grid
         t = m.get("gpu__time_duration.sum", 0.0)
         b = m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
         e = per.setdefault(name, [0, 0.0, 0.0])
@@ -66,6 +87,11 @@ def summarise(launches, select=None, units_regex=None):
         e[2] += b
         total_t += t
     has_dram = any("dram__bytes_read.sum" in m for _, _, m in launches)
+    if only_selected and select:
+        sel0 = re.compile(select)
+        per = OrderedDict((k, v) for k, v in per.items() if sel0.search(k))
+        total_t = sum(v[1] for v in per.values())
+        launches = [x for x in launches if sel0.search(short_name(x[1]) if short else x[1])]
     out = ["| kernel | launches | total ms | share | avg us |" + (" DRAM MB |" if has_dram else ""),
            "|---|---|---|---|---|" + ("---|" if has_dram else "")]
     for name, (n, t, b) in sorted(per.items(), key=lambda kv: -kv[1][1]):
@@ -93,8 +119,12 @@ def main():
     ap.add_argument("--select", default=None)
     ap.add_argument("--units-regex", default=None)
     ap.add_argument("--sources", default="")
+    ap.add_argument("--short-names", action="store_true", help="kernel names without parameter lists")
+    ap.add_argument("--by-grid", action="store_true", help="one row per kernel and grid size")
+    ap.add_argument("--only-selected", action="store_true", help="the table lists the --select kernels only")
     a = ap.parse_args()
-    table, traffic, units = summarise(read_launches(a.csv), a.select, a.units_regex)
+    table, traffic, units = summarise(read_launches(a.csv, a.by_grid), a.select, a.units_regex, a.short_names,
+                                      a.only_selected)
     print(table)
     if a.traffic and traffic is not None:
         files = [f.strip() for f in a.sources.split(",") if f.strip()]
