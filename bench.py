@@ -43,9 +43,10 @@ def args_():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="beam", choices=["beam", "learned"],
+    ap.add_argument("--workload", default="beam", choices=["beam", "learned", "gas3d"],
                     help="beam: the 1024^2 beam (headline); learned: the learned preconditioner on 512^2 "
-                         "lognormal Gaussian-pulse systems at 50 dt_CFL (training, then held-out solves)")
+                         "lognormal Gaussian-pulse systems at 50 dt_CFL (training, then held-out solves); "
+                         "gas3d: the 256^3 gas-coupled point source (advection, implicit step, velocity sources)")
     ap.add_argument("--train-rounds", type=int, default=8)
     ap.add_argument("--train-pairs", type=int, default=512, help="pairs per training round (learned workload)")
     ap.add_argument("--n", type=int, default=1024)
@@ -380,6 +381,120 @@ def run_learned(a):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- 3D gas workload
+def bytes_jv32_3d_gas(N):
+    """J v, FP32, 3D with gas (n_u = 5): read v, U, sigma, alpha (3 faces); write J v (76 B per cell)."""
+    return N * W32 * (5 + 5 + 1 + 3 + 5)
+
+
+def run_gas3d(a):
+    """One step of the 256^3 gas workload from the same seeded state per step: the
+    explicit advection of the gas energy, the implicit M1 step (mixed precision,
+    point-block Jacobi GMRES(30)) and the explicit velocity-dependent sources."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import seeded_inputs as si
+    from paper_2011_13926_gb300 import m1
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream().cuda_stream
+    n = a.n if a.n != 1024 else 256
+    dtf = a.dt_factor
+    p = si.gas_point_source_3d(n, dt_factor=dtf)
+    ctx = m1.context_from_problem(p, stream=s, device=True)
+    ux, uy, uz = si.divergence_free_velocity_3d(n, 7)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64).ravel()).cuda()  # noqa: E731
+    ctx.set_velocity(dev(ux), dev(uy), dev(uz))
+    E0, F0, T0, rc = dev(p.E), dev(p.F), dev(p.T), dev(p.rho_cv)
+    N = p.ncell
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(opts):
+        ctx.set_state(E0, F0, T0, rc)
+        ctx.advect(p.dt)
+        st, info = ctx.implicit_step(p.dt, opts, raise_on_fail=False)
+        ctx.velocity_sources(p.dt)
+        return info
+
+    def timed(opts, k):
+        ms, infos = [], []
+        for _ in range(k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = step(opts)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+        return ms, infos
+
+    opts = m1.default_opts(precision=m1.PREC_MIXED, gmres_max=3000)
+    timed(opts, a.warmup)
+    s0 = ctx.stats()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, infos = timed(opts, a.steps)
+    clk = clocks.stop()
+    s1 = ctx.stats()
+    ctx.profile(True)
+    p0 = ctx.stats()
+    msp, _ = timed(opts, 1)
+    p1 = ctx.stats()
+    ctx.profile(False)
+    mplain, iplain = timed(m1.default_opts(precision=m1.PREC_FP64, gmres_max=3000), a.plain_steps)
+    peak, peak_src = measured_peaks()
+    kms = {k: p1["kernel_ms"][k] - p0["kernel_ms"][k] for k in p1["kernel_ms"]}
+    kcount = {k: p1["kernel_count"][k] - p0["kernel_count"][k] for k in p1["kernel_count"]}
+    dom = max(kms, key=kms.get)
+    roof = {"bound": "hbm", "kernel_class": dom, "share_of_step": kms[dom] / sum(msp), "achieved": None,
+            "peak": peak, "unit": "GB/s", "frac": None, "traffic": None, "peak_source": peak_src,
+            "kernel_ms": kms, "kernel_count": kcount}
+    if dom == "ortho":
+        ob = p1.get("ortho_bytes", 0.0) - p0.get("ortho_bytes", 0.0)
+        roof["achieved"] = ob / (kms[dom] / 1e3) / 1e9
+    elif dom == "jv32" and kcount[dom]:
+        roof["achieved"] = bytes_jv32_3d_gas(N) / (kms[dom] / kcount[dom] / 1e3) / 1e9
+        roof["algorithmic_bytes"] = bytes_jv32_3d_gas(N)
+    if roof["achieved"]:
+        roof["frac"] = roof["achieved"] / peak
+    cpu = None
+    if not a.no_cpu_baseline:
+        from oracle import Scheme, newton_solve
+        q = si.gas_point_source_3d(24, dt_factor=dtf)
+        t0 = time.perf_counter()
+        r = newton_solve(Scheme(q), rtol=1e-8)
+        el = time.perf_counter() - t0
+        cpu = {"value": q.ncell / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 implicit step at 24^3 (numpy FP64 oracle, block-Jacobi GMRES(30)+MGS, Armijo "
+                         f"backtracking, 1e-8), converged={r.converged}, {el:.1f}s"}
+    line = {"metric": METRIC, "value": N * len(ms) / (sum(ms) / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"gas_point_source_3d {n}^3: grey M1 + gas energy, lognormal density "
+                                   f"(ell=16), sigma = kappa rho (kappa dx = 1), point source, outflow, dt={dtf:g} "
+                                   f"dt_CFL, divergence-free flow (max |u| = 1e-3 c); advection + implicit step + "
+                                   f"velocity sources", "cells": N,
+                       "path": "FP32 inner GMRES(30) + FP64 refinement, point-block Jacobi, Armijo backtracking",
+                       "l2": "256 MiB buffer written between timed steps; the state alone is 670 MB"},
+            "converged": all(i.converged for i in infos), "newton_iters": [i.newton_iters for i in infos],
+            "gmres_iters": [i.gmres_iters for i in infos],
+            "realizability_violations": [i.realizability_violations for i in infos],
+            "plain_fp64": {"ms_per_step": statistics.mean(mplain) if mplain else None,
+                           "value": N * len(mplain) / (sum(mplain) / 1e3) if mplain else None,
+                           "converged": all(i.converged for i in iplain),
+                           "newton_iters": [i.newton_iters for i in iplain],
+                           "gmres_iters": [i.gmres_iters for i in iplain]},
+            "roofline": roof, "cpu_baseline": cpu,
+            "gpu_launches": s1["kernel_launches"] - s0["kernel_launches"], "clocks": clk}
+    if line["plain_fp64"]["value"]:
+        line["speedup_vs_plain_fp64"] = line["value"] / line["plain_fp64"]["value"]
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 # ----------------------------------------------------------------------------- GPU path
 def main():
     a = args_()
@@ -387,6 +502,8 @@ def main():
         return run_reference(a)
     if a.workload == "learned":
         return run_learned(a)
+    if a.workload == "gas3d":
+        return run_gas3d(a)
     import numpy as np
     import torch
 

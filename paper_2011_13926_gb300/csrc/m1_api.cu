@@ -202,6 +202,14 @@ struct TK {
 
 void count(m1_ctx* ctx, int k) { ctx->st.kernel_launches += k; }
 
+// J v by dual numbers: the 3D tiled kernel where it applies, else the generic path
+void jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s) {
+    if (!launch_jv3d_tiled_f64(g, U, v, Jv, s)) launch_jv_f64(g, U, v, Jv, s);
+}
+void jv_f32(const Dev<float>& g, const float* U, const float* v, float* Jv, cudaStream_t s) {
+    if (!launch_jv3d_tiled_f32(g, U, v, Jv, s)) launch_jv_f32(g, U, v, Jv, s);
+}
+
 template <class R>
 void fill_dev_common(const m1_ctx* ctx, Dev<R>& g) {
     g.dim = ctx->dim;
@@ -533,7 +541,7 @@ struct Ops64 {
         if (pj)
             launch_jv_linear_f64(g, U, pj, in, out, ctx->s);
         else
-            launch_jv_f64(g, U, in, out, ctx->s);
+            jv_f64(g, U, in, out, ctx->s);
         count(ctx, 1);
         ctx->st.jv_calls++;
     }
@@ -571,7 +579,7 @@ struct Ops32 {
         if (pj)
             launch_jv_linear_f32(g, U, pj, in, out, ctx->s);
         else
-            launch_jv_f32(g, U, in, out, ctx->s);
+            jv_f32(g, U, in, out, ctx->s);
         count(ctx, 1);
         ctx->st.jv_calls++;
     }
@@ -1405,7 +1413,7 @@ m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double
         if (lin)
             launch_jv_linear_f32(dev32(ctx, dt), ctx->U32, ctx->pj32, ctx->z32, ctx->w32, ctx->s);
         else
-            launch_jv_f32(dev32(ctx, dt), ctx->U32, ctx->z32, ctx->w32, ctx->s);
+            jv_f32(dev32(ctx, dt), ctx->U32, ctx->z32, ctx->w32, ctx->s);
         launch_f32_to_f64(ctx->w32, ctx->w, ctx->n, ctx->s);
         count(ctx, 4);
     } else {
@@ -1413,7 +1421,7 @@ m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double
         if (lin)
             launch_jv_linear_f64(dev64(ctx, dt), ctx->U, ctx->pj64, ctx->z, ctx->w, ctx->s);
         else
-            launch_jv_f64(dev64(ctx, dt), ctx->U, ctx->z, ctx->w, ctx->s);
+            jv_f64(dev64(ctx, dt), ctx->U, ctx->z, ctx->w, ctx->s);
         count(ctx, 1);
     }
     ctx->st.jv_calls++;
@@ -1573,7 +1581,7 @@ m1_status m1_gmres_solve(m1_ctx* ctx, double dt, const double* U, const double* 
     bool conv = false;
     CKS(linear_solve(ctx, dt, ctx->U, ctx->Rt, ctx->delta, &o, -1, &it, &ref, &bn, &rs, &conv));
     // true residual of the returned x in FP64
-    launch_jv_f64(dev64(ctx, dt), ctx->U, ctx->delta, ctx->w, ctx->s);
+    jv_f64(dev64(ctx, dt), ctx->U, ctx->delta, ctx->w, ctx->s);
     launch_axpby_f64(1.0, ctx->Rt, -1.0, ctx->w, ctx->rhs, ctx->n, ctx->s);
     count(ctx, 2);
     double tr;
@@ -1814,7 +1822,7 @@ m1_status m1_nn_make_pair(m1_ctx* ctx, double dt, const double* U, const double*
         CK(cudaMemcpyAsync(ctx->U, ctx->Un, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s));
     CKS(copy_in(ctx, ctx->delta, e, sizeof(double) * ctx->n, mem));
     Dev<double> g = dev64(ctx, dt);
-    launch_jv_f64(g, ctx->U, ctx->delta, ctx->w, ctx->s);  // r = J e
+    jv_f64(g, ctx->U, ctx->delta, ctx->w, ctx->s);  // r = J e
     CKS(build_precond(ctx, g, ctx->U));
     launch_bj_apply_f64(ctx->nu, ctx->N, ctx->binv, ctx->w, ctx->z, ctx->s);  // J_bj^-1 r
     launch_axpby_f64(1.0, ctx->delta, -1.0, ctx->z, ctx->tmp, ctx->n, ctx->s);  // e - J_bj^-1 r

@@ -32,6 +32,10 @@ void launch_jv_linear_f64(const Dev<double>& g, const double* U, const double* p
                           cudaStream_t s);
 void launch_jv_linear_f32(const Dev<float>& g, const float* U, const float* pj, const float* v, float* Jv,
                           cudaStream_t s);
+// 3D J v tiled in x-y and marching in z (m1_stencil3d.cu): for wave speeds frozen at time n or
+// fixed; false (nothing launched) otherwise
+bool launch_jv3d_tiled_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s);
+bool launch_jv3d_tiled_f32(const Dev<float>& g, const float* U, const float* v, float* Jv, cudaStream_t s);
 // J M^-1 v with the point-block inverse binv (NU x NU row-major planes, FP32)
 // applied to v inside the stencil (M^-1 v is never stored)
 void launch_jv_linear_pre_f32(const Dev<float>& g, const float* U, const float* pj, const float* binv,
