@@ -43,10 +43,11 @@ def args_():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="beam", choices=["beam", "learned", "gas3d"],
+    ap.add_argument("--workload", default="beam", choices=["beam", "learned", "gas3d", "batch"],
                     help="beam: the 1024^2 beam (headline); learned: the learned preconditioner on 512^2 "
                          "lognormal Gaussian-pulse systems at 50 dt_CFL (training, then held-out solves); "
-                         "gas3d: the 256^3 gas-coupled point source (advection, implicit step, velocity sources)")
+                         "gas3d: the 256^3 gas-coupled point source (advection, implicit step, velocity sources); "
+                         "batch: 256 independent 2D problems of 64^2-256^2 cells in one batched step")
     ap.add_argument("--train-rounds", type=int, default=8)
     ap.add_argument("--train-pairs", type=int, default=512, help="pairs per training round (learned workload)")
     ap.add_argument("--n", type=int, default=1024)
@@ -495,6 +496,100 @@ def run_gas3d(a):
     ctx.close()
 
 
+# ----------------------------------------------------------------------------- batched workload
+def run_batch(a):
+    """One batched implicit step of 256 independent problems (sizes uniform from 64^2,
+    96^2, 128^2, 192^2, 256^2, own opacity and pulse, dt log-uniform in [10, 100]
+    dt_CFL): persistent CTA-per-problem classes from one CUDA graph, large classes
+    through single-grid contexts beside it, the split chosen by m1_batch_tune during
+    the warm-up. Plain FP64 point-block Jacobi solves of every problem, one after
+    another, are timed beside it."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import seeded_inputs as si
+    from oracle import Scheme
+    from paper_2011_13926_gb300 import m1
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream().cuda_stream
+    probs = si.batch_problems(256)
+    cells = sum(p.ncell for p in probs)
+    dts = [p.dt for p in probs]
+    B = m1.Batch(probs, s)
+    opts = m1.default_opts()
+    chosen = B.tune(dts, opts)
+    for _ in range(max(1, a.warmup - 1)):
+        B.implicit_step(dts, opts)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, infos = [], []
+    for _ in range(a.steps):
+        info, t = B.implicit_step(dts, opts)
+        ms.append(t)
+        infos.append(info)
+    clk = clocks.stop()
+    last = infos[-1]
+    # parity sample: the first problem of every size class, oracle residual of the GPU state
+    sample, seen = {}, set()
+    for k, p in enumerate(probs):
+        if p.n[0] in seen:
+            continue
+        seen.add(p.n[0])
+        sch = Scheme(p)
+        r0 = np.linalg.norm(sch.residual(p.state_vector()))
+        sample[f"{p.n[0]}^2 (problem {k})"] = float(np.linalg.norm(sch.residual(B.get_solution(k))) / r0)
+    B.close()
+    # plain FP64, problem by problem through single-grid contexts
+    plain_ms, plain_conv = 0.0, True
+    po = m1.default_opts(advance=0, precision=m1.PREC_FP64)
+    for p in probs:
+        ctx = m1.context_from_problem(p, stream=s, device=True)
+        st, inf = ctx.implicit_step(p.dt, po, raise_on_fail=False)
+        plain_ms += inf.time_ms
+        plain_conv = plain_conv and bool(inf.converged)
+        ctx.close()
+    cpu = None
+    if not a.no_cpu_baseline:
+        from oracle import newton_solve
+        q = si.gaussian_lognormal_2d(64, 5000, dt_factor=30.0)
+        t0 = time.perf_counter()
+        r = newton_solve(Scheme(q), rtol=1e-8)
+        el = time.perf_counter() - t0
+        cpu = {"value": q.ncell / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 implicit step of one 64^2 problem of the batch recipe (numpy FP64 oracle, block-Jacobi "
+                         f"GMRES(30)+MGS, 1e-8), converged={r.converged}, {el:.1f}s"}
+    sizes = sorted({p.n[0] for p in probs})
+    line = {"metric": METRIC, "value": cells * len(ms) / (sum(ms) / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "256 independent gaussian_lognormal_2d problems (seeds 5000+k), sizes uniform "
+                                   "from 64^2, 96^2, 128^2, 192^2, 256^2, dt log-uniform in [10, 100] dt_CFL",
+                       "cells": cells, "problems": len(probs),
+                       "path": "persistent CTA-per-problem classes (one CUDA graph) + single-grid contexts for the "
+                               "classes m1_batch_tune sends there; FP32 inner GMRES(30) + FP64 refinement, "
+                               "point-block Jacobi"},
+            "per_class": {f"{n}^2": {"problems": sum(1 for p in probs if p.n[0] == n),
+                                     "path": ("single-grid" if int(chosen[i]) == 0
+                                              else f"persistent, {int(chosen[i])} threads"),
+                                     "newton_iters_mean": float(np.mean([last[k]["newton_iters"] for k, p in
+                                                                         enumerate(probs) if p.n[0] == n])),
+                                     "gmres_iters_mean": float(np.mean([last[k]["gmres_iters"] for k, p in
+                                                                        enumerate(probs) if p.n[0] == n]))}
+                          for i, n in enumerate(sizes)},
+            "converged": all(i["converged"] == 1 for i in last),
+            "oracle_residual_ratio_sample": sample,
+            "plain_fp64": {"ms": plain_ms, "value": cells / (plain_ms / 1e3), "converged": plain_conv,
+                           "config": "FP64 GMRES(30), point-block Jacobi, Armijo backtracking, one problem after "
+                                     "another"},
+            "speedup_vs_plain_fp64": (cells * len(ms) / (sum(ms) / 1e3)) / (cells / (plain_ms / 1e3)),
+            "roofline": None, "roofline_note": "one persistent launch per size class runs whole solves; no "
+                                               "single kernel class dominates",
+            "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU path
 def main():
     a = args_()
@@ -504,6 +599,8 @@ def main():
         return run_learned(a)
     if a.workload == "gas3d":
         return run_gas3d(a)
+    if a.workload == "batch":
+        return run_batch(a)
     import numpy as np
     import torch
 

@@ -214,8 +214,10 @@ struct LoadPre {
     }
 };
 
+// FP32 instantiations are held to 64 registers (four CTAs per SM): they are
+// bound by global-load latency, and occupancy hides it
 template <class S, bool GAS, int MODE>
-__global__ void __launch_bounds__(kTX* kTY)
+__global__ void __launch_bounds__(kTX* kTY, std::is_same<typename RealOf<S>::type, float>::value ? 4 : 1)
     k_stencil2d_tiled(Dev<typename RealOf<S>::type> g, const typename RealOf<S>::type* __restrict__ U,
                       const typename RealOf<S>::type* __restrict__ v, const typename RealOf<S>::type* __restrict__ pj,
                       const typename RealOf<S>::type* __restrict__ binv, typename RealOf<S>::type* __restrict__ out,

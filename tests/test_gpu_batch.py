@@ -81,3 +81,33 @@ def test_batch_single_grid_path_matches_oracle(m1mod, cases):
     _check(B, info, probs, refs)
     with pytest.raises(m1mod.M1Error):
         B.set_class(0, 100)
+
+
+@pytest.mark.parametrize("path", ["persistent", "single_grid"])
+def test_batch_workload_sizes(m1mod, path):
+    """Problems of the batched workload's sizes (64^2, 128^2, 256^2; own opacity, pulse
+    and dt in [10, 100] dt_CFL) through one path for every class. 64^2: the state
+    against the oracle's Newton solve (1e-7); every size: the oracle residual of the
+    GPU state within 1e-8 of ||R(U^n)|| (an oracle Newton solve at 256^2 is out of reach
+    in the test's time)."""
+    probs = [si.gaussian_lognormal_2d(n, 6000 + n, dt_factor=dtf)
+             for n, dtf in ((64, 37.0), (128, 12.0), (256, 85.0))]
+    B = m1mod.Batch(probs)
+    for c in range(B.num_classes()):
+        B.set_class(c, 256 if path == "persistent" else 0)
+    dts = [p.dt for p in probs]
+    info, ms = B.implicit_step(dts, m1mod.default_opts(newton_rtol=1e-10, gmres_rtol=1e-8))
+    for k, p in enumerate(probs):
+        assert info[k]["converged"] == 1, (k, info[k])
+        u = B.get_solution(k)
+        s = Scheme(p)
+        r0 = np.linalg.norm(s.residual(p.state_vector()))
+        assert np.linalg.norm(s.residual(u)) <= 1.05e-8 * r0, k
+        if p.n[0] == 64:
+            ref = newton_solve(s, rtol=1e-10, gmres_rtol=1e-8)
+            N = p.ncell
+            scaleE = np.abs(ref.u[:N]).max()
+            for c in range(3):
+                a, b = u[c * N:(c + 1) * N], ref.u[c * N:(c + 1) * N]
+                scale = np.abs(b).max() if c == 0 else max(np.abs(b).max(), p.c * scaleE)
+                assert np.abs(a - b).max() <= 1e-7 * scale, c
