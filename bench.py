@@ -55,6 +55,8 @@ def args_():
     ap.add_argument("--other-dts", default="10,100",
                     help="dt factors timed beside the headline on the same path (comma list, '' for none)")
     ap.add_argument("--other-steps", type=int, default=2, help="timed steps per other dt")
+    ap.add_argument("--forcing", default="fixed", choices=["fixed", "ew"],
+                    help="linear-solve tolerance: fixed gmres_rtol 1e-4, or Eisenstat-Walker (m1_solver_opts.forcing)")
     ap.add_argument("--realizability", type=int, default=1, choices=[0, 1],
                     help="1: the admissibility fallback of the implicit step (m1_solver_opts.realizability)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -633,7 +635,8 @@ def main():
     ls = int(a.newton == "backtrack")
     rz = a.realizability
     opts = default_opts(advance=0, precision=prec, precond=PRECOND_MG if use_mg else PRECOND_BJ, line_search=ls,
-                        pc_rebuild=a.pc_rebuild, realizability=rz, newton_max=60)
+                        pc_rebuild=a.pc_rebuild, realizability=rz, newton_max=60,
+                        forcing=1 if a.forcing == "ew" else 0)
     dt_cfl = p.dt / a.dt_factor
 
     def timed_steps(o, k, dt=None):

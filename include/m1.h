@@ -119,6 +119,11 @@ typedef struct {
                              wave speeds. */
     int check_every;      /* realizability = 1: Newton steps between checks before convergence (5; 0: only at
                              convergence) */
+    int forcing;          /* 0 (default): every linear solve to gmres_rtol. 1: Eisenstat-Walker forcing (their
+                             choice 2, gamma 0.9, exponent 2): eta_k = 0.9 (||R_k|| / ||R_{k-1}||)^2, safeguarded by
+                             0.9 eta_{k-1}^2 when that exceeds 0.1, clipped to [gmres_rtol, 0.1], and not below
+                             0.5 newton_rtol ||R(U^n)|| / ||R_k|| (no solve tighter than the Newton test needs);
+                             eta_0 = 0.1. Only the path to the root changes, not the root. */
 } m1_solver_opts;
 
 #define M1_HIST 64  /* length of the per-Newton-iteration histories */

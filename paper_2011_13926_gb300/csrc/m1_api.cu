@@ -1052,6 +1052,7 @@ void m1_default_opts(m1_solver_opts* o) {
     o->pc_rebuild = 1;
     o->realizability = 0;
     o->check_every = 5;
+    o->forcing = 0;
 }
 
 m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out) {
@@ -1680,6 +1681,7 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
     rn = r0;
     m1_status result = M1_OK;
     int since = 0;  // Newton steps since the last admissibility check
+    double rprev = 0.0, eta_prev = 0.1;  // Eisenstat-Walker forcing: the previous ||R|| and eta
     while (true) {
         const bool done = rn <= o.newton_rtol * r0;
         if (fbk && (done || (o.check_every > 0 && since >= o.check_every))) {
@@ -1689,6 +1691,7 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
             if (nf > 0) {
                 ctx->fb_cells += nf;
                 inf.fallback_rounds++;
+                rprev = 0.0;  // a new scheme: the forcing restarts
                 g = dev64(ctx, dt);
                 CKS(residual_norm(ctx, g, ctx->Un, ctx->Rt, &r0));  // the reference of the grown scheme
                 CKS(residual_norm(ctx, g, ctx->U, ctx->R, &rn));
@@ -1706,8 +1709,23 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
         int it = 0, ref = 0;
         double bn, rs;
         bool conv;
+        m1_solver_opts ol = o;
+        if (o.forcing == 1) {  // Eisenstat-Walker, choice 2
+            double eta = 0.1;
+            if (rprev > 0.0) {
+                const double q = rn / rprev;
+                eta = 0.9 * q * q;
+                const double sg = 0.9 * eta_prev * eta_prev;
+                if (sg > 0.1) eta = std::max(eta, sg);
+            }
+            eta = std::min(std::max(eta, o.gmres_rtol), 0.1);
+            eta = std::max(eta, std::min(0.1, 0.5 * o.newton_rtol * r0 / rn));
+            ol.gmres_rtol = eta;
+            eta_prev = eta;
+        }
+        rprev = rn;
         m1_status ls =
-            linear_solve(ctx, dt, ctx->U, ctx->Rt, ctx->delta, &o, inf.newton_iters, &it, &ref, &bn, &rs, &conv);
+            linear_solve(ctx, dt, ctx->U, ctx->Rt, ctx->delta, &ol, inf.newton_iters, &it, &ref, &bn, &rs, &conv);
         inf.gmres_iters += it;
         inf.refinements += ref;
         if (ls != M1_OK) {

@@ -50,7 +50,7 @@ class SolverOpts(C.Structure):
                 ("gmres_max", C.c_int), ("gmres_rtol", C.c_double), ("precision", C.c_int),
                 ("precond", C.c_int), ("line_search", C.c_int), ("advance", C.c_int),
                 ("refine_max", C.c_int), ("krylov", C.c_int), ("pc_rebuild", C.c_int),
-                ("realizability", C.c_int), ("check_every", C.c_int)]
+                ("realizability", C.c_int), ("check_every", C.c_int), ("forcing", C.c_int)]
 
 
 M1_HIST = 64
