@@ -418,7 +418,7 @@ __device__ __forceinline__ long long mg_halo_cell(int x0, int y0, int hx, int hy
 // down: z = omega D^-1 r (written), rc = P^T (r - A z) — pre-smoothing,
 // residual and restriction of one assembled level in one pass
 template <int NU>
-__global__ void __launch_bounds__(kMgTX* kMgTY) k_mg_down(int nx, int ny, bool px, bool py,
+__global__ void __launch_bounds__(kMgTX* kMgTY, 4) k_mg_down(int nx, int ny, bool px, bool py,
                                                         const float* __restrict__ A, const float* __restrict__ Dinv,
                                                         const float* __restrict__ r, float* __restrict__ z,
                                                         int nxc, int nyc, float* __restrict__ rc) {
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kMgTX* kMgTY) k_mg_down(int nx, int ny, bool p
 
 // up: zz = z + P zc, zout = zz + omega D^-1 (r - A zz) on one assembled level
 template <int NU>
-__global__ void __launch_bounds__(kMgTX* kMgTY) k_mg_up(int nx, int ny, bool px, bool py,
+__global__ void __launch_bounds__(kMgTX* kMgTY, 3) k_mg_up(int nx, int ny, bool px, bool py,
                                                       const float* __restrict__ A, const float* __restrict__ Dinv,
                                                       const float* __restrict__ r, const float* __restrict__ z,
                                                       const float* __restrict__ zc, int nxc, int nyc,
