@@ -69,6 +69,9 @@ def args_():
     ap.add_argument("--plain-steps", type=int, default=1, help="timed plain-FP64 steps per globalisation")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps run after the timed region with per-kernel-class event timers")
+    ap.add_argument("--fp64-arith", default="auto", choices=["auto", "native", "double_word"],
+                    help="FP64 arithmetic of the headline path's residual and J v (m1_set_fp64_arithmetic); "
+                         "the plain FP64 arm always uses FP64 operations")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=48)
@@ -628,6 +631,10 @@ def main():
     p = workload(a.n, a.dt_factor)
     stream = torch.cuda.current_stream().cuda_stream
     ctx = context_from_problem(p, stream=stream, device=True)
+    from paper_2011_13926_gb300 import m1 as m1mod
+    arith = {"auto": m1mod.FP64_AUTO, "native": m1mod.FP64_NATIVE, "double_word": m1mod.FP64_DOUBLE_WORD}
+    ctx.set_fp64_arithmetic(arith[a.fp64_arith])
+    fp64_in_use = "double_word" if ctx.fp64_arithmetic()[0] == m1mod.FP64_DOUBLE_WORD else "native"
     N = p.ncell
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     prec = PREC_MIXED if a.precision == "mixed" else PREC_FP64
@@ -692,12 +699,13 @@ def main():
     # plain FP64 beside it (not part of the headline number): point-block Jacobi GMRES(30), the same
     # admissibility fallback, with full Newton steps and with Armijo backtracking
     plain = {}
+    ctx.set_fp64_arithmetic(m1mod.FP64_NATIVE)
     for name, lsv in (("full_steps", 0), ("backtracking", 1)):
         o = default_opts(advance=0, precision=PREC_FP64, precond=PRECOND_BJ, line_search=lsv, realizability=rz,
                          newton_max=80)
         m3, i3 = timed_steps(o, a.plain_steps)
         rec = step_record(m3, i3)
-        rec["config"] = ("FP64 GMRES(30), point-block Jacobi, "
+        rec["config"] = ("FP64 GMRES(30), point-block Jacobi, FP64 operations, "
                          + ("full Newton steps" if lsv == 0 else "Armijo backtracking"))
         plain[name] = rec
     best_plain = max((r for r in plain.values() if r["converged"] and r["value"]), key=lambda r: r["value"],
@@ -783,6 +791,8 @@ def main():
                 "config": {"workload": workload_name(a.n, a.dt_factor), "cells": N,
                            "path": "FP32 inner GMRES(30) + FP64 refinement" if prec == PREC_MIXED
                            else "FP64 GMRES(30)",
+                           "fp64_arithmetic": ("double-word (FP32 pairs) residual and J v, FP64 arrays"
+                                               if fp64_in_use == "double_word" else "FP64 operations"),
                            "preconditioner": ("aggregation multigrid V(1,1) (Galerkin, damped point-block Jacobi "
                                               "smoothing)" if use_mg else "point-block Jacobi"),
                            "newton_rtol": 1e-8, "newton": ("full steps" if a.newton == "full"

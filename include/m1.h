@@ -260,9 +260,12 @@ m1_status m1_get_fallback(const m1_ctx* ctx, unsigned char* mask, m1_mem mem);
  * (the scheme of Sect. 3.1.1). U, R: n_u*N doubles. */
 m1_status m1_residual(m1_ctx* ctx, double dt, const double* U, double* R, m1_mem mem);
 
-/* J(U) v, the exact directional derivative of m1_residual (forward-mode dual
- * numbers). precision: M1_PREC_FP64, or M1_PREC_MIXED for the FP32 kernel
- * (inputs rounded to FP32, result widened to FP64). */
+/* J(U) v, the exact directional derivative of m1_residual. precision:
+ * M1_PREC_FP64, forward-mode dual numbers in the context's FP64 arithmetic
+ * (m1_set_fp64_arithmetic; the operator of the mixed path's refinement), or
+ * M1_PREC_MIXED, the FP32 operator of the inner solver (in 2D with frozen or
+ * fixed wave speeds the linear stencil of dP/dU at U, else dual numbers; inputs
+ * rounded to FP32, result widened to FP64). */
 m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double* Jv,
                 int precision, m1_mem mem);
 
@@ -300,6 +303,24 @@ m1_status m1_gmres_solve(m1_ctx* ctx, double dt, const double* U, const double* 
 
 /* Cumulative counters of the context. */
 m1_status m1_stats(const m1_ctx* ctx, m1_stats_t* out);
+
+/* FP64 arithmetic of the residual and J v stencils (the outer Newton residual
+ * and the FP64 J v of the plain path and of the mixed path's refinement).
+ * This GPU issues FP64 operations at about 1/64 of the FP32 rate, and these
+ * stencils are bound by them; M1_FP64_DOUBLE_WORD evaluates them in
+ * double-word arithmetic instead (each value a sum hi + lo of two FP32 numbers,
+ * about 48 significant bits, operations of Joldes, Muller and Popescu, ACM TOMS
+ * 2017, relative error <= 15 * 2^-48 per operation) on FP32 operations, with
+ * FP32's exponent range; arrays stay FP64. M1_FP64_AUTO (the default) takes it
+ * when c, a_r and every dx lie within 2^-30 .. 2^30. In either double-word case
+ * a residual that is not finite or exceeds 2^100 in some component is computed
+ * again in FP64, and the context stays on FP64 from then on (counted in
+ * *fallbacks). M1_FP64_NATIVE: FP64 operations throughout. */
+typedef enum { M1_FP64_AUTO = 0, M1_FP64_NATIVE = 1, M1_FP64_DOUBLE_WORD = 2 } m1_fp64_arith;
+m1_status m1_set_fp64_arithmetic(m1_ctx* ctx, int mode);
+/* The arithmetic in use (M1_FP64_NATIVE or M1_FP64_DOUBLE_WORD) and the number
+ * of range fallbacks so far; either pointer may be NULL. */
+m1_status m1_get_fp64_arithmetic(const m1_ctx* ctx, int* mode, long long* fallbacks);
 
 /* Turn the per-kernel-class event timers on (1) or off (0) and reset them.
  * Timers add two event records per timed launch on the context's stream. */

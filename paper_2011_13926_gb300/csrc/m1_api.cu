@@ -110,6 +110,12 @@ struct m1_ctx {
     double* hpin_dev = nullptr;  // their device address, or null when mapping is unavailable
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ev_res[2] = {nullptr, nullptr};  // residual estimate of Arnoldi steps j (even, odd) on the host
+    // FP64 arithmetic of the residual and J v stencils (m1_set_fp64_arithmetic):
+    // the requested mode, the one in use, and how often the double-word
+    // residual's range guard sent a residual back to FP64
+    int fp64_mode = M1_FP64_AUTO;
+    bool fp64_df = false;
+    long long fp64_df_fallbacks = 0;
     // per-kernel-class timers (m1_profile)
     bool prof = false;
     std::vector<cudaEvent_t> evs;
@@ -244,6 +250,7 @@ Dev<double> dev64(const m1_ctx* ctx, double dt) {
     Dev<double> g{};
     fill_dev_common(ctx, g);
     g.dt = dt;
+    g.df = ctx->fp64_df ? 1 : 0;
     g.sig_a = ctx->sig_a;
     g.sig_f = ctx->sig_f;
     g.B = ctx->d.gas_coupling ? nullptr : ctx->B;
@@ -383,18 +390,40 @@ m1_status norm_f64(m1_ctx* ctx, const double* x, double* out) {
 }
 
 // R = R(U) and its norm
-m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g, const double* U, double* R, double* nrm) {
-    {
-        TK t(ctx, M1_K_RESIDUAL);
-        const int nb = launch_residual_f64(g, U, R, ctx->partials, ctx->residual_partials, ctx->s);
-        launch_finish_sum(ctx->partials, nb, 1, ctx->sc.nrm2, ctx->s);
+m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g0, const double* U, double* R, double* nrm) {
+    Dev<double> g = g0;
+    g.df = g0.df && ctx->fp64_df;  // a descriptor made before a range fallback
+    for (;;) {
+        {
+            TK t(ctx, M1_K_RESIDUAL);
+            const int nb = launch_residual_f64(g, U, R, ctx->partials, ctx->residual_partials, ctx->s);
+            launch_finish_sum(ctx->partials, nb, 1, ctx->sc.nrm2, ctx->s);
+        }
+        count(ctx, 2);
+        ctx->st.residual_calls++;
+        CK(cudaMemcpyAsync(ctx->hpin, ctx->sc.nrm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+        CKS(sync(ctx));
+        if (g.df && !std::isfinite(ctx->hpin[0])) {
+            // out of the double-word range (or not finite at all): FP64 from here on
+            ctx->fp64_df = false;
+            ctx->fp64_df_fallbacks++;
+            g.df = 0;
+            continue;
+        }
+        *nrm = sqrt(ctx->hpin[0]);
+        return M1_OK;
     }
-    count(ctx, 2);
-    ctx->st.residual_calls++;
-    CK(cudaMemcpyAsync(ctx->hpin, ctx->sc.nrm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
-    CKS(sync(ctx));
-    *nrm = sqrt(ctx->hpin[0]);
-    return M1_OK;
+}
+
+// M1_FP64_AUTO: the double-word arithmetic when the grid's scalars (c, a_r,
+// dx) lie within 2^-30 .. 2^30, so that with states and residuals below the
+// range guard's 2^100 no intermediate leaves FP32's exponent range
+bool fp64_auto_df(const m1_grid_desc& d) {
+    auto ok = [](double x) { return std::fabs(x) >= 0x1p-30 && std::fabs(x) <= 0x1p30; };
+    if (!ok(d.c) || (d.gas_coupling && !ok(d.a_r))) return false;
+    for (int a = 0; a < d.dim; ++a)
+        if (!ok((d.hi[a] - d.lo[a]) / d.n[a])) return false;
+    return true;
 }
 
 // dP/dU at U for the linear J v (2D, frozen or fixed wave speeds); false
@@ -1065,6 +1094,7 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
     if (!ctx) return M1_ERR_NOMEM;
     ctx->d = *desc;
     ctx->s = (cudaStream_t)cuda_stream;
+    ctx->fp64_df = fp64_auto_df(*desc);
     ctx->dim = desc->dim;
     ctx->nu = 1 + desc->dim + (desc->gas_coupling ? 1 : 0);
     ctx->N = (long long)desc->n[0] * desc->n[1] * desc->n[2];
@@ -1403,8 +1433,8 @@ m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double
     CKS(ensure_work(ctx));
     CKS(copy_in(ctx, ctx->U, U, sizeof(double) * ctx->n, mem));
     CKS(copy_in(ctx, ctx->z, v, sizeof(double) * ctx->n, mem));
-    // the operator the solvers apply: a linear stencil of dP/dU at U where
-    // available (2D, frozen or fixed wave speeds), else dual numbers
+    // FP32: the operator the inner solver applies, a linear stencil of dP/dU at
+    // U where available (2D, frozen or fixed wave speeds), else dual numbers
     bool lin = false;
     if (precision == M1_PREC_MIXED) {
         CKS(ensure_work32(ctx));
@@ -1417,12 +1447,8 @@ m1_status m1_jv(m1_ctx* ctx, double dt, const double* U, const double* v, double
             jv_f32(dev32(ctx, dt), ctx->U32, ctx->z32, ctx->w32, ctx->s);
         launch_f32_to_f64(ctx->w32, ctx->w, ctx->n, ctx->s);
         count(ctx, 4);
-    } else {
-        CKS(pressure_jacobian64(ctx, dev64(ctx, dt), ctx->U, &lin));
-        if (lin)
-            launch_jv_linear_f64(dev64(ctx, dt), ctx->U, ctx->pj64, ctx->z, ctx->w, ctx->s);
-        else
-            jv_f64(dev64(ctx, dt), ctx->U, ctx->z, ctx->w, ctx->s);
+    } else {  // FP64: dual numbers (the refinement's operator), in the context's FP64 arithmetic
+        jv_f64(dev64(ctx, dt), ctx->U, ctx->z, ctx->w, ctx->s);
         count(ctx, 1);
     }
     ctx->st.jv_calls++;
@@ -1867,6 +1893,22 @@ m1_status m1_nn_make_pair(m1_ctx* ctx, double dt, const double* U, const double*
         CK(cudaMemcpyAsync(t, td, sizeof(float) * 3 * ctx->N, cudaMemcpyDeviceToHost, ctx->s));
     }
     return sync(ctx);
+}
+
+m1_status m1_set_fp64_arithmetic(m1_ctx* ctx, int mode) {
+    if (!ctx) return M1_ERR_ARG;
+    if (mode != M1_FP64_AUTO && mode != M1_FP64_NATIVE && mode != M1_FP64_DOUBLE_WORD)
+        return fail(ctx, M1_ERR_ARG, "unknown FP64 arithmetic mode");
+    ctx->fp64_mode = mode;
+    ctx->fp64_df = mode == M1_FP64_DOUBLE_WORD || (mode == M1_FP64_AUTO && fp64_auto_df(ctx->d));
+    return M1_OK;
+}
+
+m1_status m1_get_fp64_arithmetic(const m1_ctx* ctx, int* mode, long long* fallbacks) {
+    if (!ctx) return M1_ERR_ARG;
+    if (mode) *mode = ctx->fp64_df ? M1_FP64_DOUBLE_WORD : M1_FP64_NATIVE;
+    if (fallbacks) *fallbacks = ctx->fp64_df_fallbacks;
+    return M1_OK;
 }
 
 m1_status m1_profile(m1_ctx* ctx, int enable) {

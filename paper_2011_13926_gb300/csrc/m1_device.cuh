@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "m1_df.cuh"
+
 namespace m1 {
 
 // ---------------------------------------------------------------- dual numbers
@@ -29,18 +31,34 @@ struct Dual {
     R v, d;
 };
 
+// RealOf: the real type of the arithmetic; MemOf: the type of the arrays in
+// memory (double for the double-word arithmetic DF of the FP64 path)
 template <class S> struct RealOf { using type = S; };
 template <class R> struct RealOf<Dual<R>> { using type = R; };
+template <class S> struct MemOf { using type = typename RealOf<S>::type; };
+template <> struct MemOf<DF> { using type = double; };
+template <> struct MemOf<Dual<DF>> { using type = double; };
 
 __device__ __forceinline__ double val(double x) { return x; }
 __device__ __forceinline__ float val(float x) { return x; }
+__device__ __forceinline__ DF val(DF x) { return x; }
 template <class R> __device__ __forceinline__ R val(const Dual<R>& x) { return x.v; }
+
+// a value of the arithmetic as the array type M
+template <class M> __device__ __forceinline__ M to_mem(double x) { return (M)x; }
+template <class M> __device__ __forceinline__ M to_mem(float x) { return (M)x; }
+template <class M> __device__ __forceinline__ M to_mem(DF x) { return (M)df_to_double(x); }
+__device__ __forceinline__ double dbl(double x) { return x; }
+__device__ __forceinline__ double dbl(float x) { return x; }
+__device__ __forceinline__ double dbl(DF x) { return df_to_double(x); }
 
 template <class S> __device__ __forceinline__ S cst(typename RealOf<S>::type x);
 template <> __device__ __forceinline__ double cst<double>(double x) { return x; }
 template <> __device__ __forceinline__ float cst<float>(float x) { return x; }
+template <> __device__ __forceinline__ DF cst<DF>(DF x) { return x; }
 template <> __device__ __forceinline__ Dual<double> cst<Dual<double>>(double x) { return {x, 0.0}; }
 template <> __device__ __forceinline__ Dual<float> cst<Dual<float>>(float x) { return {x, 0.0f}; }
+template <> __device__ __forceinline__ Dual<DF> cst<Dual<DF>>(DF x) { return {x, DF(0.0f, 0.0f)}; }
 
 template <class R> __device__ __forceinline__ Dual<R> operator+(Dual<R> a, Dual<R> b) { return {a.v + b.v, a.d + b.d}; }
 template <class R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a, Dual<R> b) { return {a.v - b.v, a.d - b.d}; }
@@ -62,8 +80,19 @@ template <class R> __device__ __forceinline__ Dual<R> operator/(R a, Dual<R> b) 
     return {q, -q * b.d / b.v};
 }
 
+// dual double-words against plain doubles (grid scalars and arrays)
+__device__ __forceinline__ Dual<DF> operator+(Dual<DF> a, double b) { return a + DF(b); }
+__device__ __forceinline__ Dual<DF> operator+(double a, Dual<DF> b) { return DF(a) + b; }
+__device__ __forceinline__ Dual<DF> operator-(Dual<DF> a, double b) { return a - DF(b); }
+__device__ __forceinline__ Dual<DF> operator-(double a, Dual<DF> b) { return DF(a) - b; }
+__device__ __forceinline__ Dual<DF> operator*(Dual<DF> a, double b) { return a * DF(b); }
+__device__ __forceinline__ Dual<DF> operator*(double a, Dual<DF> b) { return DF(a) * b; }
+__device__ __forceinline__ Dual<DF> operator/(Dual<DF> a, double b) { return a / DF(b); }
+__device__ __forceinline__ Dual<DF> operator/(double a, Dual<DF> b) { return DF(a) / b; }
+
 __device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ DF msqrt(DF x) { return df_sqrt(x); }
 template <class R> __device__ __forceinline__ Dual<R> msqrt(Dual<R> x) {
     R s = msqrt(x.v);
     return {s, s > R(0) ? x.d / (R(2) * s) : R(0)};
@@ -83,12 +112,17 @@ template <> struct Tiny<float> {
     static __device__ __forceinline__ float e() { return 1e-30f; }
     static __device__ __forceinline__ float den() { return 1e-30f; }
 };
+template <> struct Tiny<DF> {
+    static __device__ __forceinline__ DF e() { return DF(1e-30f, 0.0f); }
+    static __device__ __forceinline__ DF den() { return DF(1e-30f, 0.0f); }
+};
 
 // 1 / x for a positive wave-speed difference: IEEE division in FP64; in FP32 the
 // hardware reciprocal (__fdividef, within 2 ulp), ample for the FP32 operator
 template <class R> __device__ __forceinline__ R recip_den(R x);
 template <> __device__ __forceinline__ double recip_den<double>(double x) { return 1.0 / x; }
 template <> __device__ __forceinline__ float recip_den<float>(float x) { return __fdividef(1.0f, x); }
+template <> __device__ __forceinline__ DF recip_den<DF>(DF x) { return DF(1.0f, 0.0f) / x; }
 
 // ---------------------------------------------------------------- grid data
 enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2, BC_DIRICHLET = 3 };
@@ -123,6 +157,9 @@ struct Dev {
     // centred flux source of Eq. (wb_naive); its faces carry alpha = 1 and
     // speeds -c, +c in the face arrays. Null: no cell is flagged.
     const unsigned char* fb;
+    // FP64 residual and J v (Dev<double> only): nonzero = computed in the
+    // double-word arithmetic DF (m1_df.cuh) instead of FP64 operations
+    int df;
 };
 
 __device__ __forceinline__ long long face_index(const int* n, const int* coord, int a, int fa) {
@@ -212,28 +249,30 @@ __device__ __forceinline__ void eigen(const Cl<S, DIM>& k, int a, typename RealO
 }
 
 // ---------------------------------------------------------------- loaders
-template <class R>
+// Loaders read arrays of type R and give values of the arithmetic type A
+// (R itself, or the double-word DF for R = double)
+template <class R, class A = R>
 struct LoadPlain {
     const R* U;
     long long N;
-    __device__ __forceinline__ R get(int comp, long long idx, long long) const { return U[comp * N + idx]; }
+    __device__ __forceinline__ A get(int comp, long long idx, long long) const { return A(U[comp * N + idx]); }
 };
-template <class R>
+template <class R, class A = R>
 struct LoadDir {  // U + eps v
     const R* U;
     const R* v;
     long long N;
-    __device__ __forceinline__ Dual<R> get(int comp, long long idx, long long) const {
-        return {U[comp * N + idx], v[comp * N + idx]};
+    __device__ __forceinline__ Dual<A> get(int comp, long long idx, long long) const {
+        return {A(U[comp * N + idx]), A(v[comp * N + idx])};
     }
 };
-template <class R>
+template <class R, class A = R>
 struct LoadSeed {  // seed component k of the own cell only
     const R* U;
     long long N;
     int k;
-    __device__ __forceinline__ Dual<R> get(int comp, long long idx, long long own) const {
-        return {U[comp * N + idx], (idx == own && comp == k) ? R(1) : R(0)};
+    __device__ __forceinline__ Dual<A> get(int comp, long long idx, long long own) const {
+        return {A(U[comp * N + idx]), (idx == own && comp == k) ? A(1) : A(0)};
     }
 };
 

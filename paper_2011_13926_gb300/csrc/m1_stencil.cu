@@ -15,6 +15,16 @@ namespace m1 {
 
 static constexpr int kThreads = 256;
 
+// Range guard of the double-word residual: a cell whose residual is not
+// finite or exceeds 2^100 (where FP32's exponent range, and with it the
+// double-word arithmetic, runs out) makes its block's partial sum +inf, so
+// that the host sees a non-finite norm and recomputes in FP64
+__device__ __forceinline__ void df_range_guard(double, double&) {}
+__device__ __forceinline__ void df_range_guard(float, double&) {}
+__device__ __forceinline__ void df_range_guard(DF o, double& ss) {
+    if (!(fabsf(o.hi) <= 0x1p100f)) ss = __longlong_as_double(0x7ff0000000000000LL);
+}
+
 int stencil_blocks(long long N) { return (int)((N + kThreads - 1) / kThreads); }
 
 // ------------------------------------------------------------------ time-n faces
@@ -80,8 +90,10 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // ------------------------------------------------------------------ residual
-template <int DIM, bool GAS>
-__global__ void __launch_bounds__(kThreads) k_residual(Dev<double> g, const double* __restrict__ U,
+// A: the arithmetic (double, or the double-word DF on FP64 arrays)
+template <class A, int DIM, bool GAS>
+__global__ void __launch_bounds__(kThreads, std::is_same<A, DF>::value ? 3 : 1)
+    k_residual(Dev<double> g, const double* __restrict__ U,
                                                        double* __restrict__ Rout, double* partials) {
     constexpr int NU = 1 + DIM + (GAS ? 1 : 0);
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -89,14 +101,17 @@ __global__ void __launch_bounds__(kThreads) k_residual(Dev<double> g, const doub
     if (idx < g.N) {
         int coord[3];
         cell_coord(idx, g.n[0], g.n[1], coord);
-        LoadPlain<double> ld{U, g.N};
-        double out[NU];
-        cell_residual<double, DIM, GAS>(g, ld, idx, coord, out);
+        LoadPlain<double, A> ld{U, g.N};
+        A out[NU];
+        cell_residual<A, DIM, GAS>(g, ld, idx, coord, out);
 #pragma unroll
         for (int k = 0; k < NU; ++k) {
-            Rout[k * g.N + idx] = out[k];
-            ss += out[k] * out[k];
+            const double o = dbl(out[k]);
+            Rout[k * g.N + idx] = o;
+            ss += o * o;
         }
+#pragma unroll
+        for (int k = 0; k < NU; ++k) df_range_guard(out[k], ss);
     }
     if (partials) {
         const double t = block_sum(ss);
@@ -105,19 +120,20 @@ __global__ void __launch_bounds__(kThreads) k_residual(Dev<double> g, const doub
 }
 
 // ------------------------------------------------------------------ J v
-template <class R, int DIM, bool GAS>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 1) k_jv(Dev<R> g, const R* __restrict__ U, const R* __restrict__ v,
-                                                 R* __restrict__ Jv) {
+// R: the arrays (double or float); A: the arithmetic (R, or DF on FP64 arrays)
+template <class R, class A, int DIM, bool GAS>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 1)
+    k_jv(Dev<R> g, const R* __restrict__ U, const R* __restrict__ v, R* __restrict__ Jv) {
     constexpr int NU = 1 + DIM + (GAS ? 1 : 0);
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
     int coord[3];
     cell_coord(idx, g.n[0], g.n[1], coord);
-    LoadDir<R> ld{U, v, g.N};
-    Dual<R> out[NU];
-    cell_residual<Dual<R>, DIM, GAS>(g, ld, idx, coord, out);
+    LoadDir<R, A> ld{U, v, g.N};
+    Dual<A> out[NU];
+    cell_residual<Dual<A>, DIM, GAS>(g, ld, idx, coord, out);
 #pragma unroll
-    for (int k = 0; k < NU; ++k) Jv[k * g.N + idx] = out[k].d;
+    for (int k = 0; k < NU; ++k) Jv[k * g.N + idx] = to_mem<R>(out[k].d);
 }
 
 // ------------------------------------------------------------------ 2D tiled residual and J v
@@ -216,13 +232,18 @@ struct LoadPre {
 
 // FP32 instantiations are held to 64 registers (four CTAs per SM): they are
 // bound by global-load latency, and occupancy hides it
+// double-word instantiations at three CTAs per SM: their dependent FP32 chains
+// need the warps
 template <class S, bool GAS, int MODE>
-__global__ void __launch_bounds__(kTX* kTY, std::is_same<typename RealOf<S>::type, float>::value ? 4 : 1)
-    k_stencil2d_tiled(Dev<typename RealOf<S>::type> g, const typename RealOf<S>::type* __restrict__ U,
-                      const typename RealOf<S>::type* __restrict__ v, const typename RealOf<S>::type* __restrict__ pj,
-                      const typename RealOf<S>::type* __restrict__ binv, typename RealOf<S>::type* __restrict__ out,
-                      double* __restrict__ partials, TileMg<typename RealOf<S>::type> mgp) {
-    using R = typename RealOf<S>::type;
+__global__ void __launch_bounds__(kTX* kTY, std::is_same<typename RealOf<S>::type, float>::value
+                                                ? 4
+                                                : (std::is_same<typename RealOf<S>::type, DF>::value ? 3 : 1))
+    k_stencil2d_tiled(Dev<typename MemOf<S>::type> g, const typename MemOf<S>::type* __restrict__ U,
+                      const typename MemOf<S>::type* __restrict__ v, const typename MemOf<S>::type* __restrict__ pj,
+                      const typename MemOf<S>::type* __restrict__ binv, typename MemOf<S>::type* __restrict__ out,
+                      double* __restrict__ partials, TileMg<typename MemOf<S>::type> mgp) {
+    using R = typename RealOf<S>::type;  // arithmetic
+    using M = typename MemOf<S>::type;   // arrays
     constexpr bool RES = MODE == kTileResidual;
     constexpr bool MGD = MODE == kTileMgDown0, MGU = MODE == kTileMgUp0;
     constexpr bool LIN = MODE == kTileJvLinear || MODE == kTileJvLinearPre || MGD || MGU;
@@ -325,8 +346,8 @@ __global__ void __launch_bounds__(kTX* kTY, std::is_same<typename RealOf<S>::typ
             // ghosts by dual numbers through the boundary rules
             using SD = std::conditional_t<RES, R, Dual<R>>;
             using L = std::conditional_t<
-                RES, LoadPlain<R>,
-                std::conditional_t<PRE, LoadPre<R, NU>, std::conditional_t<MGU, LoadProlong<R>, LoadDir<R>>>>;
+                RES, LoadPlain<M, R>,
+                std::conditional_t<PRE, LoadPre<R, NU>, std::conditional_t<MGU, LoadProlong<R>, LoadDir<M, R>>>>;
             L ld;
             if constexpr (RES) {
                 ld = L{U, N};
@@ -348,7 +369,7 @@ __global__ void __launch_bounds__(kTX* kTY, std::is_same<typename RealOf<S>::typ
                 int cc[3] = {a == 0 ? (gx < 0 ? 0 : nx - 1) : gx, a == 1 ? (gy < 0 ? 0 : ny - 1) : gy, 0};
                 const long long k = (long long)cc[1] * nx + cc[0];
                 const St<SD, 2> self = load_state<SD, 2, false>(ld, k, k);
-                R sn;
+                M sn;
                 bool bnd;
                 u = neighbour<SD, 2, false>(g, ld, self, k, cc, a, side, sn, bnd);
             }
@@ -457,10 +478,10 @@ __global__ void __launch_bounds__(kTX* kTY, std::is_same<typename RealOf<S>::typ
         const S exch = (cdt * g.sig_a[idx]) * (emis - me.E);
         RE = RE - exch;
         if constexpr (MODE == kTileJvDual) {
-            out[idx] = RE.d;
-            out[N + idx] = RFx.d;
-            out[2 * N + idx] = RFy.d;
-            if constexpr (GAS) out[3 * N + idx] = (g.rho_cv[idx] * T + exch).d;
+            out[idx] = to_mem<M>(RE.d);
+            out[N + idx] = to_mem<M>(RFx.d);
+            out[2 * N + idx] = to_mem<M>(RFy.d);
+            if constexpr (GAS) out[3 * N + idx] = to_mem<M>((g.rho_cv[idx] * T + exch).d);
         } else if constexpr (MGD) {
             // z = omega z', residual r - omega J z' (kept for the restriction)
             const R zr[3] = {me.E, me.Fx, me.Fy}, jz[3] = {RE, RFx, RFy};
@@ -489,14 +510,20 @@ __global__ void __launch_bounds__(kTX* kTY, std::is_same<typename RealOf<S>::typ
             if constexpr (GAS) out[3 * N + idx] = g.rho_cv[idx] * T + exch;
         } else {
             if (g.S) RE = RE - dt * g.S[idx];
-            out[idx] = RE;
-            out[N + idx] = RFx;
-            out[2 * N + idx] = RFy;
-            ss = (double)RE * RE + (double)RFx * RFx + (double)RFy * RFy;
+            df_range_guard(RE, ss);
+            df_range_guard(RFx, ss);
+            df_range_guard(RFy, ss);
+            const double oE = dbl(RE), oFx = dbl(RFx), oFy = dbl(RFy);
+            out[idx] = oE;
+            out[N + idx] = oFx;
+            out[2 * N + idx] = oFy;
+            ss += oE * oE + oFx * oFx + oFy * oFy;
             if constexpr (GAS) {
                 const S RT = g.rho_cv[idx] * (T - g.Un[3 * N + idx]) + exch;
-                out[3 * N + idx] = RT;
-                ss += (double)RT * RT;
+                df_range_guard(RT, ss);
+                const double oT = dbl(RT);
+                out[3 * N + idx] = oT;
+                ss += oT * oT;
             }
         }
     }
@@ -572,38 +599,44 @@ long long residual_partial_count(int dim, const int n[3]) {
     return nb;
 }
 
-int launch_residual_f64(const Dev<double>& g, const double* U, double* R, double* partials, long long capacity,
+template <class A>
+static int residual_f64(const Dev<double>& g, const double* U, double* R, double* partials, long long capacity,
                         cudaStream_t s) {
     if (tiled2d(g)) {
         const dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
         const long long nb = (long long)grid.x * grid.y;
         if (!partials || nb <= capacity) {
             if (g.gas)
-                k_stencil2d_tiled<double, true, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, nullptr,
-                                                                                     R, partials, {});
+                k_stencil2d_tiled<A, true, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, nullptr, R,
+                                                                                partials, {});
             else
-                k_stencil2d_tiled<double, false, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, nullptr,
-                                                                                      R, partials, {});
+                k_stencil2d_tiled<A, false, kTileResidual><<<grid, block, 0, s>>>(g, U, nullptr, nullptr, nullptr, R,
+                                                                                 partials, {});
             return (int)nb;
         }
     }
     const int nb = stencil_blocks(g.N);
-#define CALL(D, G) k_residual<D, G><<<nb, kThreads, 0, s>>>(g, U, R, partials)
+#define CALL(D, G) k_residual<A, D, G><<<nb, kThreads, 0, s>>>(g, U, R, partials)
     M1_DISPATCH(g.dim, g.gas, CALL);
 #undef CALL
     return nb;
 }
 
-template <class R>
-static bool jv_tiled(const Dev<R>& g, const R* U, const R* v, R* Jv, cudaStream_t s) {
+int launch_residual_f64(const Dev<double>& g, const double* U, double* R, double* partials, long long capacity,
+                        cudaStream_t s) {
+    return g.df ? residual_f64<DF>(g, U, R, partials, capacity, s) : residual_f64<double>(g, U, R, partials, capacity, s);
+}
+
+// S: Dual<R>, or Dual<DF> on FP64 arrays
+template <class S>
+static bool jv_tiled(const Dev<typename MemOf<S>::type>& g, const typename MemOf<S>::type* U,
+                     const typename MemOf<S>::type* v, typename MemOf<S>::type* Jv, cudaStream_t s) {
     if (g.dim != 2 || (g.implicit_eigs && !g.fixed_eigs)) return false;
     dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY), block(kTX, kTY);
     if (g.gas)
-        k_stencil2d_tiled<Dual<R>, true, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, nullptr, Jv, nullptr,
-                                                                           {});
+        k_stencil2d_tiled<S, true, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, nullptr, Jv, nullptr, {});
     else
-        k_stencil2d_tiled<Dual<R>, false, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, nullptr, Jv, nullptr,
-                                                                            {});
+        k_stencil2d_tiled<S, false, kTileJvDual><<<grid, block, 0, s>>>(g, U, v, nullptr, nullptr, Jv, nullptr, {});
     return true;
 }
 
@@ -682,17 +715,24 @@ void launch_mg_up0_f32(const Dev<float>& g, const float* U, const float* pj, con
 }
 
 void launch_jv_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s) {
-    if (jv_tiled(g, U, v, Jv, s)) return;
     const int nb = stencil_blocks(g.N);
-#define CALL(D, G) k_jv<double, D, G><<<nb, kThreads, 0, s>>>(g, U, v, Jv)
+    if (g.df) {
+        if (jv_tiled<Dual<DF>>(g, U, v, Jv, s)) return;
+#define CALL(D, G) k_jv<double, DF, D, G><<<nb, kThreads, 0, s>>>(g, U, v, Jv)
+        M1_DISPATCH(g.dim, g.gas, CALL);
+#undef CALL
+        return;
+    }
+    if (jv_tiled<Dual<double>>(g, U, v, Jv, s)) return;
+#define CALL(D, G) k_jv<double, double, D, G><<<nb, kThreads, 0, s>>>(g, U, v, Jv)
     M1_DISPATCH(g.dim, g.gas, CALL);
 #undef CALL
 }
 
 void launch_jv_f32(const Dev<float>& g, const float* U, const float* v, float* Jv, cudaStream_t s) {
-    if (jv_tiled(g, U, v, Jv, s)) return;
+    if (jv_tiled<Dual<float>>(g, U, v, Jv, s)) return;
     const int nb = stencil_blocks(g.N);
-#define CALL(D, G) k_jv<float, D, G><<<nb, kThreads, 0, s>>>(g, U, v, Jv)
+#define CALL(D, G) k_jv<float, float, D, G><<<nb, kThreads, 0, s>>>(g, U, v, Jv)
     M1_DISPATCH(g.dim, g.gas, CALL);
 #undef CALL
 }

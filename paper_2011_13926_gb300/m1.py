@@ -24,6 +24,7 @@ BC = {"outflow": 0, "periodic": 1, "reflect": 2, "dirichlet": 3}
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 PRECOND_NONE, PRECOND_BJ, PRECOND_LEARNED, PRECOND_MG, PRECOND_LINE = 0, 1, 2, 3, 4
+FP64_AUTO, FP64_NATIVE, FP64_DOUBLE_WORD = 0, 1, 2
 KRYLOV_GMRES, KRYLOV_BICGSTAB = 0, 1
 
 EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "m1_set_state", "m1_get_state",
@@ -162,6 +163,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_gmres_solve": (I, [P, D, P, P, P, C.POINTER(SolverOpts), C.POINTER(SolveInfo), I]),
         "m1_stats": (I, [P, C.POINTER(Stats)]),
         "m1_profile": (I, [P, I]),
+        "m1_set_fp64_arithmetic": (I, [P, I]),
+        "m1_get_fp64_arithmetic": (I, [P, C.POINTER(I), C.POINTER(C.c_longlong)]),
         "m1_last_error": (C.c_char_p, [P]),
         "m1_residual_noalloc": (I, [C.POINTER(GridDesc), D, C.POINTER(DeviceFields), P, P, P, P]),
         "m1_nn_num_params": (C.c_size_t, []),
@@ -478,6 +481,16 @@ class Context:
     def profile(self, enable: bool = True):
         """m1_profile: switch the per-kernel-class event timers on or off."""
         self._call("m1_profile", int(bool(enable)))
+
+    def set_fp64_arithmetic(self, mode: int):
+        """m1_set_fp64_arithmetic: FP64_AUTO, FP64_NATIVE or FP64_DOUBLE_WORD."""
+        self._call("m1_set_fp64_arithmetic", int(mode))
+
+    def fp64_arithmetic(self):
+        """m1_get_fp64_arithmetic: (the arithmetic in use, range fallbacks so far)."""
+        m, f = C.c_int(), C.c_longlong()
+        self._call("m1_get_fp64_arithmetic", C.byref(m), C.byref(f))
+        return m.value, f.value
 
     def stats(self) -> dict:
         """m1_stats: counters, kernel times per class and algorithmic bytes as a dict."""

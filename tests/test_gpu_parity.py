@@ -331,9 +331,12 @@ def test_beam_45_sect53(m1mod, fixed_eigs):
 
 @pytest.mark.parametrize("periodic,gas,n", [(False, False, 12), (False, True, 12), (True, False, 12),
                                             (False, False, 300)])
-def test_line_preconditioner_matches_dense_lu(m1mod, periodic, gas, n):
+@pytest.mark.parametrize("arith", ["native", "double_word"])
+def test_line_preconditioner_matches_dense_lu(m1mod, periodic, gas, n, arith):
     # M1_PRECOND_LINE: on a non-periodic 1D grid the preconditioner is J itself, and
-    # GMRES takes one step (two at most: the convergence test runs one step behind)
+    # GMRES takes one step (two at most: the convergence test runs one step behind).
+    # The line factors are built with FP64 operations; with the J v in double words
+    # the two differ by ~1e-14 relative, and GMRES takes a few more steps to 1e-13.
     from tests.m1_cases import line_case_1d
     p = line_case_1d(periodic, gas, n=n)
     s = Scheme(p)
@@ -341,12 +344,13 @@ def test_line_preconditioner_matches_dense_lu(m1mod, periodic, gas, n):
     b = np.random.default_rng(65).standard_normal(u.size)
     x_lu = dense_solve(s, u, b)
     ctx = ctx_for(m1mod, p)
+    ctx.set_fp64_arithmetic(m1mod.FP64_NATIVE if arith == "native" else m1mod.FP64_DOUBLE_WORD)
     opts = m1mod.default_opts(gmres_rtol=1e-13, gmres_max=300, precond=m1mod.PRECOND_LINE)
     x, info = ctx.gmres_solve(p.dt, b, U=u, opts=opts)
     assert info.converged
     assert np.linalg.norm(x - x_lu) <= 1e-10 * np.linalg.norm(x_lu)
     if not periodic:
-        assert info.iters <= 2, info.iters
+        assert info.iters <= (2 if arith == "native" else 10), info.iters
 
 
 def test_line_preconditioner_rejects_unsupported(m1mod):
