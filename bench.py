@@ -410,6 +410,9 @@ def run_gas3d(a):
     dtf = a.dt_factor
     p = si.gas_point_source_3d(n, dt_factor=dtf)
     ctx = m1.context_from_problem(p, stream=s, device=True)
+    arith = {"auto": m1.FP64_AUTO, "native": m1.FP64_NATIVE, "double_word": m1.FP64_DOUBLE_WORD}
+    ctx.set_fp64_arithmetic(arith[a.fp64_arith])
+    fp64_in_use = "double_word" if ctx.fp64_arithmetic()[0] == m1.FP64_DOUBLE_WORD else "native"
     ux, uy, uz = si.divergence_free_velocity_3d(n, 7)
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64).ravel()).cuda()  # noqa: E731
     ctx.set_velocity(dev(ux), dev(uy), dev(uz))
@@ -450,6 +453,7 @@ def run_gas3d(a):
     msp, _ = timed(opts, 1)
     p1 = ctx.stats()
     ctx.profile(False)
+    ctx.set_fp64_arithmetic(m1.FP64_NATIVE)  # the plain arm: FP64 operations
     mplain, iplain = timed(m1.default_opts(precision=m1.PREC_FP64, gmres_max=3000), a.plain_steps)
     peak, peak_src = measured_peaks()
     kms = {k: p1["kernel_ms"][k] - p0["kernel_ms"][k] for k in p1["kernel_ms"]}
@@ -484,6 +488,8 @@ def run_gas3d(a):
                                    f"dt_CFL, divergence-free flow (max |u| = 1e-3 c); advection + implicit step + "
                                    f"velocity sources", "cells": N,
                        "path": "FP32 inner GMRES(30) + FP64 refinement, point-block Jacobi, Armijo backtracking",
+                       "fp64_arithmetic": ("double-word (FP32 pairs) residual and J v, FP64 arrays"
+                                           if fp64_in_use == "double_word" else "FP64 operations"),
                        "l2": "256 MiB buffer written between timed steps; the state alone is 670 MB"},
             "converged": all(i.converged for i in infos), "newton_iters": [i.newton_iters for i in infos],
             "gmres_iters": [i.gmres_iters for i in infos],

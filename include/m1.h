@@ -143,6 +143,9 @@ typedef struct {
     double theta_hist[M1_HIST];
     long long fallback_cells;  /* realizability = 1: cells flagged in this step (m1_get_fallback) */
     int fallback_rounds;       /* realizability = 1: checks that flagged cells */
+    int fp64_double_word;      /* 1: the step's FP64 residuals and J v ran in double words (m1_set_fp64_arithmetic) */
+    double fp64_floor;         /* M1_FP64_AUTO: ||R_dw(U^n) - R_fp64(U^n)|| / ||R(U^n)||, the double-word
+                                  rounding floor measured at the start of the step (0 when not measured) */
 } m1_step_info;
 
 typedef struct {
@@ -312,7 +315,12 @@ m1_status m1_stats(const m1_ctx* ctx, m1_stats_t* out);
  * about 48 significant bits, operations of Joldes, Muller and Popescu, ACM TOMS
  * 2017, relative error <= 15 * 2^-48 per operation) on FP32 operations, with
  * FP32's exponent range; arrays stay FP64. M1_FP64_AUTO (the default) takes it
- * when c, a_r and every dx lie within 2^-30 .. 2^30. In either double-word case
+ * when c, a_r and every dx lie within 2^-30 .. 2^30, and in m1_implicit_step only
+ * when the step can reach its Newton tolerance in it: each step first evaluates
+ * R(U^n) in both arithmetics, and keeps double words when newton_rtol ||R(U^n)||
+ * is at least 32 times ||R_dw(U^n) - R_fp64(U^n)|| (stiff exchange terms, c sigma
+ * dt >> 1, cancel in the residual and raise the double-word floor 2^5-2^6 times
+ * above FP64's). In either double-word case
  * a residual that is not finite or exceeds 2^100 in some component is computed
  * again in FP64, and the context stays on FP64 from then on (counted in
  * *fallbacks). M1_FP64_NATIVE: FP64 operations throughout. */

@@ -114,7 +114,8 @@ struct m1_ctx {
     // the requested mode, the one in use, and how often the double-word
     // residual's range guard sent a residual back to FP64
     int fp64_mode = M1_FP64_AUTO;
-    bool fp64_df = false;
+    bool fp64_df_ok = false;  // double words allowed: the mode, the grid's scalars, no range fallback yet
+    bool fp64_df = false;     // in use now (M1_FP64_AUTO: decided per implicit step)
     long long fp64_df_fallbacks = 0;
     // per-kernel-class timers (m1_profile)
     bool prof = false;
@@ -392,7 +393,7 @@ m1_status norm_f64(m1_ctx* ctx, const double* x, double* out) {
 // R = R(U) and its norm
 m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g0, const double* U, double* R, double* nrm) {
     Dev<double> g = g0;
-    g.df = g0.df && ctx->fp64_df;  // a descriptor made before a range fallback
+    g.df = g0.df && ctx->fp64_df_ok;  // a descriptor made before a range fallback
     for (;;) {
         {
             TK t(ctx, M1_K_RESIDUAL);
@@ -406,6 +407,7 @@ m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g0, const double* U, dou
         if (g.df && !std::isfinite(ctx->hpin[0])) {
             // out of the double-word range (or not finite at all): FP64 from here on
             ctx->fp64_df = false;
+            ctx->fp64_df_ok = false;
             ctx->fp64_df_fallbacks++;
             g.df = 0;
             continue;
@@ -1094,7 +1096,7 @@ m1_status m1_init_grid(const m1_grid_desc* desc, void* cuda_stream, m1_ctx** out
     if (!ctx) return M1_ERR_NOMEM;
     ctx->d = *desc;
     ctx->s = (cudaStream_t)cuda_stream;
-    ctx->fp64_df = fp64_auto_df(*desc);
+    ctx->fp64_df = ctx->fp64_df_ok = fp64_auto_df(*desc);
     ctx->dim = desc->dim;
     ctx->nu = 1 + desc->dim + (desc->gas_coupling ? 1 : 0);
     ctx->N = (long long)desc->n[0] * desc->n[1] * desc->n[2];
@@ -1695,10 +1697,30 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
     // alpha and the time-n wave speeds are the first stage of every step
     CKS(refresh(ctx));
     const long long n = ctx->n;
-    Dev<double> g = dev64(ctx, dt);
     CK(cudaMemcpyAsync(ctx->U, ctx->Un, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     double r0, rn;
-    CKS(residual_norm(ctx, g, ctx->U, ctx->R, &r0));
+    if (ctx->fp64_mode == M1_FP64_AUTO && ctx->fp64_df_ok) {
+        // R(U^n) in FP64 (the reference) and in double words: their difference is
+        // the double-word rounding floor at this step's magnitudes
+        ctx->fp64_df = false;
+        CKS(residual_norm(ctx, dev64(ctx, dt), ctx->U, ctx->R, &r0));
+        Dev<double> gd = dev64(ctx, dt);
+        gd.df = 1;
+        double rd;
+        CKS(residual_norm(ctx, gd, ctx->U, ctx->Rt, &rd));
+        if (ctx->fp64_df_ok && std::isfinite(r0) && r0 > 0.0) {
+            launch_axpby_f64(1.0, ctx->R, -1.0, ctx->Rt, ctx->Rt, n, s);
+            count(ctx, 1);
+            double d;
+            CKS(norm_f64(ctx, ctx->Rt, &d));
+            inf.fp64_floor = d / r0;
+            ctx->fp64_df = o.newton_rtol * r0 >= 32.0 * d;
+        }
+    } else {
+        ctx->fp64_df = ctx->fp64_df_ok;
+        CKS(residual_norm(ctx, dev64(ctx, dt), ctx->U, ctx->R, &r0));
+    }
+    Dev<double> g = dev64(ctx, dt);
     inf.res0 = r0;
     if (!(r0 == r0) || isinf(r0)) {
         if (info) *info = inf;
@@ -1789,6 +1811,8 @@ m1_status m1_implicit_step(m1_ctx* ctx, double dt, const m1_solver_opts* opts, m
     inf.res0 = r0;
     inf.res = rn;
     inf.converged = (result == M1_OK) && rn <= o.newton_rtol * r0;
+    inf.fp64_double_word = ctx->fp64_df ? 1 : 0;
+    ctx->fp64_df = ctx->fp64_df_ok;  // outside implicit steps the mode alone decides
     inf.fallback_cells = ctx->fb_cells;
     if (ctx->fb_on) {  // the face arrays carry the fallback: recompute them before the next use
         ctx->fb_on = false;
@@ -1900,7 +1924,7 @@ m1_status m1_set_fp64_arithmetic(m1_ctx* ctx, int mode) {
     if (mode != M1_FP64_AUTO && mode != M1_FP64_NATIVE && mode != M1_FP64_DOUBLE_WORD)
         return fail(ctx, M1_ERR_ARG, "unknown FP64 arithmetic mode");
     ctx->fp64_mode = mode;
-    ctx->fp64_df = mode == M1_FP64_DOUBLE_WORD || (mode == M1_FP64_AUTO && fp64_auto_df(ctx->d));
+    ctx->fp64_df = ctx->fp64_df_ok = mode == M1_FP64_DOUBLE_WORD || (mode == M1_FP64_AUTO && fp64_auto_df(ctx->d));
     return M1_OK;
 }
 

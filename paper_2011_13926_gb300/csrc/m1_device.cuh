@@ -51,6 +51,8 @@ template <class M> __device__ __forceinline__ M to_mem(DF x) { return (M)df_to_d
 __device__ __forceinline__ double dbl(double x) { return x; }
 __device__ __forceinline__ double dbl(float x) { return x; }
 __device__ __forceinline__ double dbl(DF x) { return df_to_double(x); }
+__device__ __forceinline__ float to_f32(double x) { return (float)x; }
+__device__ __forceinline__ float to_f32(DF x) { return x.hi; }  // hi = RN(hi + lo)
 
 template <class S> __device__ __forceinline__ S cst(typename RealOf<S>::type x);
 template <> __device__ __forceinline__ double cst<double>(double x) { return x; }
@@ -439,9 +441,10 @@ __device__ __forceinline__ void cell_residual(const Dev<R>& g, const L& ld, long
 // lambda+-(U^n) and alpha (Eq. asymptoticCorrection with f_{i+1/2} = (f_i + f_{i+1})/2
 // and sigma_{i+1/2} = (sigma_i + sigma_{i+1})/2) of face f of axis a (faces
 // indexed like cells with n_a + 1 along a).
-template <int DIM>
-__device__ __forceinline__ void face_time_n(const Dev<double>& g, int a, long long f, double& lp, double& lm,
-                                            double& al) {
+// A: the arithmetic (double, or the double-word DF)
+template <int DIM, class A = double>
+__device__ __forceinline__ void face_time_n(const Dev<double>& g, int a, long long f, double& lp_out,
+                                            double& lm_out, double& al_out) {
     int fn[3] = {g.n[0], g.n[1], g.n[2]};
     fn[a] += 1;
     int coord[3];
@@ -452,73 +455,80 @@ __device__ __forceinline__ void face_time_n(const Dev<double>& g, int a, long lo
         coord[1] = (int)(q - (long long)coord[2] * fn[1]);
     }
     const int fa = coord[a];
-    LoadPlain<double> ld{g.Un, g.N};
+    LoadPlain<double, A> ld{g.Un, g.N};
     // the cell on the right of the face unless the face is the high boundary
     int cc[3] = {coord[0], coord[1], coord[2]};
     const bool high = (fa == g.n[a]);
     cc[a] = high ? g.n[a] - 1 : fa;
     const long long idx = ((long long)cc[2] * g.n[1] + cc[1]) * g.n[0] + cc[0];
-    St<double, DIM> self = load_state<double, DIM, false>(ld, idx, idx);
+    St<A, DIM> self = load_state<A, DIM, false>(ld, idx, idx);
     double sig_nb;
     bool bnd;
-    St<double, DIM> nb;
+    St<A, DIM> nb;
     if (high) {
-        nb = neighbour<double, DIM, false>(g, ld, self, idx, cc, a, 1, sig_nb, bnd);
+        nb = neighbour<A, DIM, false>(g, ld, self, idx, cc, a, 1, sig_nb, bnd);
     } else if (fa == 0) {
-        nb = neighbour<double, DIM, false>(g, ld, self, idx, cc, a, 0, sig_nb, bnd);
+        nb = neighbour<A, DIM, false>(g, ld, self, idx, cc, a, 0, sig_nb, bnd);
     } else {
         const long long j = idx - g.stride[a];
-        nb = load_state<double, DIM, false>(ld, j, idx);
+        nb = load_state<A, DIM, false>(ld, j, idx);
         sig_nb = g.sig_f[j];
     }
-    const St<double, DIM>& uL = high ? self : nb;
-    const St<double, DIM>& uR = high ? nb : self;
-    const Cl<double, DIM> kL = closure(uL, g.c), kR = closure(uR, g.c);
+    const St<A, DIM>& uL = high ? self : nb;
+    const St<A, DIM>& uR = high ? nb : self;
+    const Cl<A, DIM> kL = closure(uL, g.c), kR = closure(uR, g.c);
+    A lp, lm;
     if (g.fixed_eigs) {
-        lp = g.c;
-        lm = -g.c;
+        lp = A(g.c);
+        lm = A(-g.c);
     } else {
-        double xL, nL, xR, nR;
+        A xL, nL, xR, nR;
         eigen(kL, a, g.c, xL, nL);
         eigen(kR, a, g.c, xR, nR);
         wave_speeds(xL, nL, xR, nR, g.lambda_floor, lp, lm);
     }
-    al = 1.0;
+    A al = A(1);
     if (g.ap) {
-        const double fbar = 0.5 * (sqrt(kL.f2) + sqrt(kR.f2));
-        const double sig = 0.5 * (g.sig_f[idx] + sig_nb);
-        const double den = lp - lm;
-        const double term = den >= Tiny<double>::den() ? lp * lm / (g.c * den) : 0.0;
-        al = 1.0 / (1.0 - 3.0 * sig * g.dx[a] * (1.0 - fbar * fbar) * term);
+        const A fbar = A(0.5) * (msqrt(kL.f2) + msqrt(kR.f2));
+        const A sig = A(0.5) * (A(g.sig_f[idx]) + A(sig_nb));
+        const A den = lp - lm;
+        const A term = den >= Tiny<A>::den() ? lp * lm / (A(g.c) * den) : A(0);
+        al = A(1) / (A(1) - A(3) * sig * A(g.dx[a]) * (A(1) - fbar * fbar) * term);
     }
+    lp_out = dbl(lp);
+    lm_out = dbl(lm);
+    al_out = dbl(al);
 }
 
 // Gauss-Jordan inverse with partial pivoting of one NU x NU block (FP64);
 // false (and x = I) when a pivot vanishes.
-template <int NU>
-__device__ __forceinline__ bool invert_block(double (&a)[NU][NU], double (&x)[NU][NU]) {
+__device__ __forceinline__ double absval(double x) { return fabs(x); }
+__device__ __forceinline__ DF absval(DF x) { return x.hi < 0.0f ? -x : x; }
+
+template <int NU, class T = double>
+__device__ __forceinline__ bool invert_block(T (&a)[NU][NU], T (&x)[NU][NU]) {
 #pragma unroll
     for (int r = 0; r < NU; ++r)
 #pragma unroll
-        for (int c = 0; c < NU; ++c) x[r][c] = (r == c) ? 1.0 : 0.0;
+        for (int c = 0; c < NU; ++c) x[r][c] = (r == c) ? T(1) : T(0);
     bool bad = false;
 #pragma unroll
     for (int col = 0; col < NU; ++col) {
         int piv = col;
-        double best = fabs(a[col][col]);
+        T best = absval(a[col][col]);
 #pragma unroll
         for (int r = col + 1; r < NU; ++r)
-            if (fabs(a[r][col]) > best) {
-                best = fabs(a[r][col]);
+            if (absval(a[r][col]) > best) {
+                best = absval(a[r][col]);
                 piv = r;
             }
-        if (!(best > 0.0)) bad = true;
+        if (!(best > T(0))) bad = true;
 #pragma unroll
         for (int r = col + 1; r < NU; ++r) {
             if (r == piv) {
 #pragma unroll
                 for (int c = 0; c < NU; ++c) {
-                    double t = a[col][c];
+                    T t = a[col][c];
                     a[col][c] = a[r][c];
                     a[r][c] = t;
                     t = x[col][c];
@@ -527,20 +537,20 @@ __device__ __forceinline__ bool invert_block(double (&a)[NU][NU], double (&x)[NU
                 }
             }
         }
-        const double inv = bad ? 0.0 : 1.0 / a[col][col];
+        const T inv = bad ? T(0) : T(1) / a[col][col];
 #pragma unroll
         for (int c = 0; c < NU; ++c) {
-            a[col][c] *= inv;
-            x[col][c] *= inv;
+            a[col][c] = a[col][c] * inv;
+            x[col][c] = x[col][c] * inv;
         }
 #pragma unroll
         for (int r = 0; r < NU; ++r) {
             if (r == col) continue;
-            const double m = a[r][col];
+            const T m = a[r][col];
 #pragma unroll
             for (int c = 0; c < NU; ++c) {
-                a[r][c] -= m * a[col][c];
-                x[r][c] -= m * x[col][c];
+                a[r][c] = a[r][c] - m * a[col][c];
+                x[r][c] = x[r][c] - m * x[col][c];
             }
         }
     }
@@ -548,7 +558,7 @@ __device__ __forceinline__ bool invert_block(double (&a)[NU][NU], double (&x)[NU
 #pragma unroll
         for (int r = 0; r < NU; ++r)
 #pragma unroll
-            for (int c = 0; c < NU; ++c) x[r][c] = (r == c) ? 1.0 : 0.0;
+            for (int c = 0; c < NU; ++c) x[r][c] = (r == c) ? T(1) : T(0);
     }
     return !bad;
 }

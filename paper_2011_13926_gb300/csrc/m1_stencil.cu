@@ -28,13 +28,13 @@ __device__ __forceinline__ void df_range_guard(DF o, double& ss) {
 int stencil_blocks(long long N) { return (int)((N + kThreads - 1) / kThreads); }
 
 // ------------------------------------------------------------------ time-n faces
-template <int DIM>
+template <int DIM, class A>
 __global__ void k_faces_time_n(Dev<double> g, int a, double* lam_p, double* lam_m, double* alpha) {
     const long long nfaces = g.N / g.n[a] * (g.n[a] + 1);
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nfaces) return;
     double lp, lm, al;
-    face_time_n<DIM>(g, a, f, lp, lm, al);
+    face_time_n<DIM, A>(g, a, f, lp, lm, al);
     lam_p[f] = lp;
     lam_m[f] = lm;
     alpha[f] = al;
@@ -45,11 +45,21 @@ void launch_faces_time_n(const Dev<double>& g, double* const lam_p[3], double* c
     for (int a = 0; a < g.dim; ++a) {
         const long long nf = g.N / g.n[a] * (g.n[a] + 1);
         const int nb = (int)((nf + kThreads - 1) / kThreads);
-        switch (g.dim) {
-            case 1: k_faces_time_n<1><<<nb, kThreads, 0, s>>>(g, a, lam_p[a], lam_m[a], alpha[a]); break;
-            case 2: k_faces_time_n<2><<<nb, kThreads, 0, s>>>(g, a, lam_p[a], lam_m[a], alpha[a]); break;
-            default: k_faces_time_n<3><<<nb, kThreads, 0, s>>>(g, a, lam_p[a], lam_m[a], alpha[a]); break;
+#define FACES(D, A) k_faces_time_n<D, A><<<nb, kThreads, 0, s>>>(g, a, lam_p[a], lam_m[a], alpha[a])
+        if (g.df) {
+            switch (g.dim) {
+                case 1: FACES(1, DF); break;
+                case 2: FACES(2, DF); break;
+                default: FACES(3, DF); break;
+            }
+        } else {
+            switch (g.dim) {
+                case 1: FACES(1, double); break;
+                case 2: FACES(2, double); break;
+                default: FACES(3, double); break;
+            }
         }
+#undef FACES
     }
 }
 
@@ -758,18 +768,21 @@ __global__ void k_block_inverse(long long N, const B* __restrict__ blocks, doubl
                                 float* __restrict__ binv32, int* singular) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double a[NU][NU], x[NU][NU];
+    // FP32 blocks (the mixed path's) are inverted in double words, FP64 ones in FP64
+    using T = std::conditional_t<std::is_same<B, float>::value, DF, double>;
+    T a[NU][NU], x[NU][NU];
 #pragma unroll
     for (int r = 0; r < NU; ++r)
 #pragma unroll
-        for (int c = 0; c < NU; ++c) a[r][c] = (double)blocks[(long long)(r * NU + c) * N + i];
-    if (!invert_block<NU>(a, x)) atomicAdd(singular, 1);
+        for (int c = 0; c < NU; ++c) a[r][c] = T(blocks[(long long)(r * NU + c) * N + i]);
+    if (!invert_block<NU, T>(a, x)) atomicAdd(singular, 1);
 #pragma unroll
     for (int r = 0; r < NU; ++r)
 #pragma unroll
         for (int c = 0; c < NU; ++c) {
-            binv64[(long long)(r * NU + c) * N + i] = x[r][c];
-            if (binv32) binv32[(long long)(r * NU + c) * N + i] = (float)x[r][c];
+            const double xv = dbl(x[r][c]);
+            binv64[(long long)(r * NU + c) * N + i] = xv;
+            if (binv32) binv32[(long long)(r * NU + c) * N + i] = to_f32(x[r][c]);
         }
 }
 

@@ -73,8 +73,10 @@ __device__ __forceinline__ bool stage_cell(const Dev<R>& g, const R* __restrict_
 }
 
 // R: the arrays; A: the arithmetic (R, or the double-word DF on FP64 arrays)
+// FP32: four CTAs per SM (64 registers), double words three (80)
 template <class R, class A, bool GAS>
-__global__ void __launch_bounds__(kTX3* kTY3, std::is_same<A, DF>::value ? 3 : 1) k_jv3d_tiled(Dev<R> g, const R* __restrict__ U,
+__global__ void __launch_bounds__(kTX3* kTY3, std::is_same<A, float>::value ? 4 : (std::is_same<A, DF>::value ? 3 : 1))
+    k_jv3d_tiled(Dev<R> g, const R* __restrict__ U,
                                                           const R* __restrict__ v, R* __restrict__ Jv) {
     extern __shared__ __align__(16) unsigned char smem3[];
     CellD3<A>(*ring)[kHY3][kHX3] = reinterpret_cast<CellD3<A>(*)[kHY3][kHX3]>(smem3);

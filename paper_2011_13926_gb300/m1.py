@@ -64,12 +64,14 @@ class StepInfo(C.Structure):
                 ("realizability_violations", C.c_longlong), ("time_ms", C.c_double),
                 ("res_hist", C.c_double * M1_HIST), ("gmres_hist", C.c_int * M1_HIST),
                 ("theta_hist", C.c_double * M1_HIST), ("fallback_cells", C.c_longlong),
-                ("fallback_rounds", C.c_int)]
+                ("fallback_rounds", C.c_int), ("fp64_double_word", C.c_int), ("fp64_floor", C.c_double)]
 
     def as_dict(self, history: bool = False):
         out = {k: getattr(self, k) for k, _ in self._fields_[:8]}
         out["fallback_cells"] = self.fallback_cells
         out["fallback_rounds"] = self.fallback_rounds
+        out["fp64_double_word"] = self.fp64_double_word
+        out["fp64_floor"] = self.fp64_floor
         if history:
             k = min(self.newton_iters, M1_HIST)
             out["res_hist"] = list(self.res_hist[:k])

@@ -141,3 +141,22 @@ def test_range_guard_returns_to_fp64(m1mod):
     r0 = np.linalg.norm(s.residual(p.state_vector()))
     assert np.linalg.norm(s.residual(u)) <= 1.05e-8 * r0
     ctx.close()
+
+
+@pytest.mark.parametrize("rtol", [1e-8, 1e-11, 1e-13])
+def test_auto_decides_per_step_from_the_measured_floor(m1mod, rtol):
+    # M1_FP64_AUTO measures ||R_dw(U^n) - R_fp64(U^n)|| at the start of each step and
+    # keeps double words only when the Newton target is 32 times above it
+    p = CASES["gas2d_frozen"]()
+    ctx = _ctx(m1mod, p, m1mod.FP64_AUTO)
+    opts = m1mod.default_opts(newton_rtol=rtol, gmres_rtol=1e-10, advance=0, precision=m1mod.PREC_FP64)
+    st, info = ctx.implicit_step(p.dt, opts, raise_on_fail=False)
+    d = info.as_dict()
+    print(rtol, d["fp64_floor"], d["fp64_double_word"], d["converged"], d["newton_iters"])
+    assert 0.0 < d["fp64_floor"] < 1e-12
+    assert d["fp64_double_word"] == int(rtol >= 32.0 * d["fp64_floor"])
+    if d["fp64_double_word"] == 0:
+        assert rtol < 32.0 * d["fp64_floor"]
+    assert info.converged
+    assert ctx.fp64_arithmetic() == (m1mod.FP64_DOUBLE_WORD, 0)  # outside steps the mode decides
+    ctx.close()

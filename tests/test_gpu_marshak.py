@@ -73,12 +73,17 @@ def test_marshak_wave_sect51(m1mod, reference, ap):
     p = si.marshak_1d(ap_correction=ap)
     ctx = _ctx(m1mod, p)
     o = _opts(m1mod, newton_rtol=1e-6)
+    dw = 0
     for k, dt in enumerate(si.marshak_schedule()):
         st, info = ctx.implicit_step(dt, o, raise_on_fail=False)
         assert st == m1mod.M1_OK and info.converged, (k, dt, info.as_dict())
+        dw += info.fp64_double_word
     T = ctx.get_state()[2]
     err = np.linalg.norm(T - reference.T) / np.linalg.norm(reference.T)
-    print("relative L2 error of T:", "AP" if ap else "HLL", err)
+    # the stiff exchange raises the double-word rounding floor above the 1e-6 target
+    # late in the march: those steps take FP64 operations (M1_FP64_AUTO)
+    print("relative L2 error of T:", "AP" if ap else "HLL", err, "; steps in double words:", dw,
+          "of", len(si.marshak_schedule()))
     if ap:
         assert err <= 0.03
     else:
