@@ -105,62 +105,50 @@ __global__ void k_mg_extract(int nx, int ny, bool px, bool py, int mx, int my, i
 // The linear J v of cell i (2D, radiation only, frozen or fixed wave speeds) is
 // a linear function of the staged derivative quantities (E, Fx, Fy, Pxx, Pxy,
 // Pyy) at five positions: the cell (0) and its faces' neighbours W, E, S, N
-// (1..4). mg_lin_out evaluates it with the formulas of the linear tiled J v.
+// (1..4), with the formulas of the linear tiled J v. mg_lin_self gives the terms
+// of the cell's own tuple outside the faces, mg_lin_face one face's flux and
+// well-balanced source terms; their sum over the faces is J v of the cell.
 struct MgFace {
     float lp, lm, al, sn;  // wave speeds, alpha, the neighbour's flux opacity
+    float inv, pm;         // 1 / (lp - lm) (0 when it vanishes) and lp lm inv, once per face
     bool boundary;         // a non-periodic boundary face (the neighbour is a ghost)
 };
 
-__device__ __forceinline__ void mg_lin_out(const Dev<float>& g, const float (*st)[6], const MgFace* fc,
-                                           float sig_self, float sig_a, bool wbc, float* out) {
-    const float dt = g.dt, c = g.c, c2 = g.c * g.c;
-    float RE = st[0][0], RFx = st[0][1], RFy = st[0][2];
-    float phi[2] = {0.f, 0.f};
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const int p = 1 + 2 * a + side;
-            const float* me = st[0];
-            const float* nb = st[p];
-            const float* L = side ? me : nb;
-            const float* Rr = side ? nb : me;
-            const MgFace& f = fc[p - 1];
-            const float den = f.lp - f.lm;
-            const float inv = den >= Tiny<float>::den() ? 1.f / den : 0.f;
-            const float pm = f.lp * f.lm * inv;
-            const float FaL = a == 0 ? L[1] : L[2], FaR = a == 0 ? Rr[1] : Rr[2];
-            const float Fs = (f.lp * FaL - f.lm * FaR) * inv + pm * (Rr[0] - L[0]);
-            const float PaxL = a == 0 ? L[3] : L[4], PaxR = a == 0 ? Rr[3] : Rr[4];
-            const float PayL = a == 0 ? L[4] : L[5], PayR = a == 0 ? Rr[4] : Rr[5];
-            const float Psx = c2 * (f.lp * PaxL - f.lm * PaxR) * inv + pm * (Rr[1] - L[1]);
-            const float Psy = c2 * (f.lp * PayL - f.lm * PayR) * inv + pm * (Rr[2] - L[2]);
-            const float w = (side ? dt : -dt) * g.inv_dx[a];
-            RE = RE + (w * f.al) * Fs;
-            RFx = RFx + w * Psx;
-            RFy = RFy + w * Psy;
-            if (wbc) {
-                if (f.boundary && g.wb_boundary) {
-                    const float PR = a == 0 ? Rr[3] : Rr[5], PL = a == 0 ? L[3] : L[5];
-                    phi[a] = phi[a] - c * g.inv_dx[a] * (PR - PL);
-                } else {
-                    phi[a] = phi[a] + (0.25f * (sig_self + f.sn)) * (FaL + FaR);
-                }
-            }
-        }
-    }
-    const float cdt = c * dt;
+__device__ __forceinline__ void mg_lin_self(const Dev<float>& g, const float* me, float sig_self, float sig_a,
+                                            bool wbc, float* out) {
+    const float cdt = g.c * g.dt;
+    out[0] = me[0] + (cdt * sig_a) * me[0];  // minus the exchange - c sigma_a dt dE
+    out[1] = wbc ? me[1] : me[1] + cdt * (sig_self * me[1]);
+    out[2] = wbc ? me[2] : me[2] + cdt * (sig_self * me[2]);
+}
+
+// face (a, side) of the cell; me and nb the tuples of the cell and of the
+// neighbour across the face (either may be zero); adds to out
+__device__ __forceinline__ void mg_lin_face(const Dev<float>& g, const float* me, const float* nb, const MgFace& f,
+                                            int a, int side, float sig_self, bool wbc, float* out) {
+    const float c = g.c, c2 = g.c * g.c, cdt = g.c * g.dt;
+    const float* L = side ? me : nb;
+    const float* Rr = side ? nb : me;
+    const float FaL = a == 0 ? L[1] : L[2], FaR = a == 0 ? Rr[1] : Rr[2];
+    const float Fs = (f.lp * FaL - f.lm * FaR) * f.inv + f.pm * (Rr[0] - L[0]);
+    const float PaxL = a == 0 ? L[3] : L[4], PaxR = a == 0 ? Rr[3] : Rr[4];
+    const float PayL = a == 0 ? L[4] : L[5], PayR = a == 0 ? Rr[4] : Rr[5];
+    const float Psx = c2 * (f.lp * PaxL - f.lm * PaxR) * f.inv + f.pm * (Rr[1] - L[1]);
+    const float Psy = c2 * (f.lp * PayL - f.lm * PayR) * f.inv + f.pm * (Rr[2] - L[2]);
+    const float w = (side ? g.dt : -g.dt) * g.inv_dx[a];
+    out[0] += (w * f.al) * Fs;
+    out[1] += w * Psx;
+    out[2] += w * Psy;
     if (wbc) {
-        RFx = RFx + cdt * (0.5f * phi[0]);
-        RFy = RFy + cdt * (0.5f * phi[1]);
-    } else {
-        RFx = RFx + cdt * (sig_self * st[0][1]);
-        RFy = RFy + cdt * (sig_self * st[0][2]);
+        float ph;
+        if (f.boundary && g.wb_boundary) {
+            const float PR = a == 0 ? Rr[3] : Rr[5], PL = a == 0 ? L[3] : L[5];
+            ph = -c * g.inv_dx[a] * (PR - PL);
+        } else {
+            ph = (0.25f * (sig_self + f.sn)) * (FaL + FaR);
+        }
+        out[1 + a] += cdt * (0.5f * ph);
     }
-    const float exch = (cdt * sig_a) * (0.f - st[0][0]);
-    out[0] = RE - exch;
-    out[1] = RFx;
-    out[2] = RFy;
 }
 
 // A0 blocks of every cell: column c of block s is mg_lin_out with a unit
@@ -205,6 +193,9 @@ __global__ void k_mg_assemble2d(Dev<float> g, const float* __restrict__ U, const
                     f.lm = g.lam_m[a][fidx];
                 }
                 f.al = g.alpha[a][fidx];
+                const float den = f.lp - f.lm;
+                f.inv = den >= Tiny<float>::den() ? 1.f / den : 0.f;
+                f.pm = f.lp * f.lm * f.inv;
             }
         }
         // ghost derivatives: gd[face][seed c][quantity]
@@ -234,34 +225,34 @@ __global__ void k_mg_assemble2d(Dev<float> g, const float* __restrict__ U, const
                 }
             }
         }
+        const float zero[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int s = 0; s < 5; ++s) {
-            const long long X = s == 0 ? i : nbi[s - 1];
+        for (int c = 0; c < 3; ++c) {
+            // C: the cell's own unknown c (unit derivative, dP the column c of dP/dU),
+            // and through the boundary rules the ghosts of its boundary faces
+            float t0[6] = {c == 0 ? 1.f : 0.f, c == 1 ? 1.f : 0.f, c == 2 ? 1.f : 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float out[3] = {0.f, 0.f, 0.f};
+            for (int r = 0; r < 3; ++r) t0[3 + r] = pj[(long long)(3 * r + c) * N + i];
+            float out[3];
+            mg_lin_self(g, t0, sig_self, sig_a, wbc, out);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) mg_lin_face(g, t0, fc[p].boundary ? gd[p][c] : zero, fc[p], p / 2, p % 2,
+                                                    sig_self, wbc, out);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) A[((long long)(0 * 3 + r) * 3 + c) * N + i] = out[r];
+            // W, E, S, N: the neighbour's unknown c enters through the one face they share
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                float o[3] = {0.f, 0.f, 0.f};
+                const long long X = nbi[p];
                 if (X >= 0) {
-                    float st[5][6];
+                    float tn[6] = {c == 0 ? 1.f : 0.f, c == 1 ? 1.f : 0.f, c == 2 ? 1.f : 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                    for (int p = 0; p < 5; ++p)
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) st[p][k] = 0.f;
-                    st[s][0] = c == 0 ? 1.f : 0.f;
-                    st[s][1] = c == 1 ? 1.f : 0.f;
-                    st[s][2] = c == 2 ? 1.f : 0.f;
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) st[s][3 + r] = pj[(long long)(3 * r + c) * N + X];
-                    if (s == 0) {
-#pragma unroll
-                        for (int p = 0; p < 4; ++p)
-                            if (fc[p].boundary)
-#pragma unroll
-                                for (int k = 0; k < 6; ++k) st[1 + p][k] = gd[p][c][k];
-                    }
-                    mg_lin_out(g, st, fc, sig_self, sig_a, wbc, out);
+                    for (int r = 0; r < 3; ++r) tn[3 + r] = pj[(long long)(3 * r + c) * N + X];
+                    mg_lin_face(g, zero, tn, fc[p], p / 2, p % 2, sig_self, wbc, o);
                 }
 #pragma unroll
-                for (int r = 0; r < 3; ++r) A[((long long)(s * 3 + r) * 3 + c) * N + i] = out[r];
+                for (int r = 0; r < 3; ++r) A[((long long)((1 + p) * 3 + r) * 3 + c) * N + i] = o[r];
             }
         }
     }
