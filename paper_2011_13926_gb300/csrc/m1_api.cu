@@ -421,11 +421,9 @@ m1_status residual_norm(m1_ctx* ctx, const Dev<double>& g0, const double* U, dou
 // dx) lie within 2^-30 .. 2^30, so that with states and residuals below the
 // range guard's 2^100 no intermediate leaves FP32's exponent range
 bool fp64_auto_df(const m1_grid_desc& d) {
-    auto ok = [](double x) { return std::fabs(x) >= 0x1p-30 && std::fabs(x) <= 0x1p30; };
-    if (!ok(d.c) || (d.gas_coupling && !ok(d.a_r))) return false;
-    for (int a = 0; a < d.dim; ++a)
-        if (!ok((d.hi[a] - d.lo[a]) / d.n[a])) return false;
-    return true;
+    double dx[3];
+    for (int a = 0; a < 3; ++a) dx[a] = (d.hi[a] - d.lo[a]) / d.n[a];
+    return fp64_df_scalars_ok(d.c, d.a_r, d.gas_coupling != 0, d.dim, dx);
 }
 
 // dP/dU at U for the linear J v (2D, frozen or fixed wave speeds); false

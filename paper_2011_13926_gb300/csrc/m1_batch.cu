@@ -92,7 +92,10 @@ __device__ void faces(const Prob& P) {
         const long long nf = P.N / P.g64.n[a] * (P.g64.n[a] + 1);
         for (long long f = threadIdx.x; f < nf; f += blockDim.x) {
             double lp, lm, al;
-            face_time_n<2>(P.g64, a, f, lp, lm, al);
+            if (P.g64.df)
+                face_time_n<2, DF>(P.g64, a, f, lp, lm, al);
+            else
+                face_time_n<2, double>(P.g64, a, f, lp, lm, al);
             const_cast<double*>(P.g64.lam_p[a])[f] = lp;
             const_cast<double*>(P.g64.lam_m[a])[f] = lm;
             const_cast<double*>(P.g64.alpha[a])[f] = al;
@@ -110,34 +113,37 @@ __device__ void faces(const Prob& P) {
     __syncthreads();
 }
 
-// R = R(U) (FP64); returns ||R||^2
+// R = R(U) (FP64 arrays; the arithmetic A is FP64 or double words); returns ||R||^2
+template <class A>
 __device__ double residual(const Prob& P, const double* U, double* R, double* red) {
     double ss = 0.0;
-    LoadPlain<double> ld{U, P.N};
+    LoadPlain<double, A> ld{U, P.N};
     for (long long i = threadIdx.x; i < P.N; i += blockDim.x) {
         int coord[3];
         cell_coord(i, P.g64.n[0], P.g64.n[1], coord);
-        double out[kNU];
-        cell_residual<double, 2, false>(P.g64, ld, i, coord, out);
+        A out[kNU];
+        cell_residual<A, 2, false>(P.g64, ld, i, coord, out);
 #pragma unroll
         for (int k = 0; k < kNU; ++k) {
-            R[k * P.N + i] = out[k];
-            ss += out[k] * out[k];
+            const double o = dbl(out[k]);
+            R[k * P.N + i] = o;
+            ss += o * o;
         }
     }
     return block_sum(ss, red);
 }
 
-template <class R>
+// R: the arrays, A: the arithmetic (R, or double words on FP64 arrays)
+template <class R, class A = R>
 __device__ void jv(const Dev<R>& g, long long N, const R* U, const R* v, R* out) {
-    LoadDir<R> ld{U, v, N};
+    LoadDir<R, A> ld{U, v, N};
     for (long long i = threadIdx.x; i < N; i += blockDim.x) {
         int coord[3];
         cell_coord(i, g.n[0], g.n[1], coord);
-        Dual<R> o[kNU];
-        cell_residual<Dual<R>, 2, false>(g, ld, i, coord, o);
+        Dual<A> o[kNU];
+        cell_residual<Dual<A>, 2, false>(g, ld, i, coord, o);
 #pragma unroll
-        for (int k = 0; k < kNU; ++k) out[k * N + i] = o[k].d;
+        for (int k = 0; k < kNU; ++k) out[k * N + i] = to_mem<R>(o[k].d);
     }
     __syncthreads();
 }
@@ -146,19 +152,19 @@ __device__ void bj_build(const Prob& P, float* binv) {
     for (long long i = threadIdx.x; i < P.N; i += blockDim.x) {
         int coord[3];
         cell_coord(i, P.g32.n[0], P.g32.n[1], coord);
-        double a[kNU][kNU], x[kNU][kNU];
+        DF a[kNU][kNU], x[kNU][kNU];  // FP32 blocks, inverted in double words
         for (int k = 0; k < kNU; ++k) {
             LoadSeed<float> ld{P.U32, P.N, k};
             Dual<float> o[kNU];
             cell_residual<Dual<float>, 2, false>(P.g32, ld, i, coord, o);
 #pragma unroll
-            for (int r = 0; r < kNU; ++r) a[r][k] = (double)o[r].d;
+            for (int r = 0; r < kNU; ++r) a[r][k] = DF(o[r].d);
         }
-        invert_block<kNU>(a, x);
+        invert_block<kNU, DF>(a, x);
 #pragma unroll
         for (int r = 0; r < kNU; ++r)
 #pragma unroll
-            for (int c = 0; c < kNU; ++c) binv[(long long)(r * kNU + c) * P.N + i] = (float)x[r][c];
+            for (int c = 0; c < kNU; ++c) binv[(long long)(r * kNU + c) * P.N + i] = to_f32(x[r][c]);
     }
     __syncthreads();
 }
@@ -338,7 +344,21 @@ __global__ void __launch_bounds__(512) k_batch_solve(const Prob* __restrict__ pr
         // Newton from U^n
         for (long long e = threadIdx.x; e < n; e += blockDim.x) P.U[e] = P.g64.Un[e];
         __syncthreads();
-        const double r0 = sqrt(residual(P, P.U, P.R, red));
+        const double r0 = sqrt(residual<double>(P, P.U, P.R, red));
+        // double words for this problem's residuals and refinement J v when its grid
+        // allows them and the Newton target is 32 times above their rounding floor,
+        // measured as ||R_dw(U^n) - R(U^n)||
+        bool df = false;
+        if (P.g64.df) {
+            const double rd = sqrt(residual<DF>(P, P.U, P.Rt, red));
+            double ss = 0.0;
+            for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+                const double d = P.R[e] - P.Rt[e];
+                ss += d * d;
+            }
+            const double floor = sqrt(block_sum(ss, red));
+            df = rd == rd && rd <= 1e300 && o.newton_rtol * r0 >= 32.0 * floor;
+        }
         double rn = r0;
         int nit = 0, git = 0;
         bool bad = !(r0 == r0);
@@ -366,7 +386,10 @@ __global__ void __launch_bounds__(512) k_batch_solve(const Prob* __restrict__ pr
                 git += inner_gmres(P, W, inner_tol, o.gmres_max - git, o.restart, red, sm);
                 for (long long e = threadIdx.x; e < n; e += blockDim.x) P.x[e] += rr * W.xin[e];
                 __syncthreads();
-                jv<double>(P.g64, P.N, P.U, P.x, P.w64);
+                if (df)
+                    jv<double, DF>(P.g64, P.N, P.U, P.x, P.w64);
+                else
+                    jv<double, double>(P.g64, P.N, P.U, P.x, P.w64);
                 double ss = 0.0;
                 for (long long e = threadIdx.x; e < n; e += blockDim.x) {
                     const double v = P.b[e] - P.w64[e];
@@ -380,7 +403,7 @@ __global__ void __launch_bounds__(512) k_batch_solve(const Prob* __restrict__ pr
             for (int ls = 0; ls < 7; ++ls) {
                 for (long long e = threadIdx.x; e < n; e += blockDim.x) P.Ut[e] = P.U[e] + theta * P.x[e];
                 __syncthreads();
-                rt = sqrt(residual(P, P.Ut, P.Rt, red));
+                rt = sqrt(df ? residual<DF>(P, P.Ut, P.Rt, red) : residual<double>(P, P.Ut, P.Rt, red));
                 if (!o.line_search || rt <= (1.0 - 1e-4 * theta) * rn) break;
                 theta *= 0.5;
             }
@@ -572,6 +595,7 @@ m1_status m1_batch_create(int nprob, const m1_grid_desc* descs, void* stream, m1
         g.fixed_eigs = d.fixed_eigs;
         g.wb_boundary = d.wb_boundary;
         g.implicit_eigs = 0;
+        g.df = fp64_df_scalars_ok(d.c, d.a_r, false, 2, g.dx) ? 1 : 0;
         double *siga, *sigf, *Bf, *Un;
         if (balloc(B, &siga, N) || balloc(B, &sigf, N) || balloc(B, &Bf, N) || balloc(B, &Un, P.n) ||
             balloc(B, &P.U, P.n) || balloc(B, &P.R, P.n) || balloc(B, &P.Ut, P.n) || balloc(B, &P.Rt, P.n) ||

@@ -32,6 +32,17 @@ void launch_jv_linear_f64(const Dev<double>& g, const double* U, const double* p
                           cudaStream_t s);
 void launch_jv_linear_f32(const Dev<float>& g, const float* U, const float* pj, const float* v, float* Jv,
                           cudaStream_t s);
+// Double-word FP64 arithmetic (m1_df.cuh) is allowed for a grid whose scalars c,
+// a_r (with gas) and dx lie within 2^-30 .. 2^30: with states and residuals
+// below the residual's range guard (2^100) no intermediate then leaves FP32's
+// exponent range
+inline bool fp64_df_scalars_ok(double c, double a_r, bool gas, int dim, const double* dx) {
+    auto ok = [](double x) { return fabs(x) >= 0x1p-30 && fabs(x) <= 0x1p30; };
+    if (!ok(c) || (gas && !ok(a_r))) return false;
+    for (int a = 0; a < dim; ++a)
+        if (!ok(dx[a])) return false;
+    return true;
+}
 // 3D J v tiled in x-y and marching in z (m1_stencil3d.cu): for wave speeds frozen at time n or
 // fixed; false (nothing launched) otherwise
 bool launch_jv3d_tiled_f64(const Dev<double>& g, const double* U, const double* v, double* Jv, cudaStream_t s);
