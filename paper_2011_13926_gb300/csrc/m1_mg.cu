@@ -155,7 +155,9 @@ __device__ __forceinline__ void mg_lin_face(const Dev<float>& g, const float* me
 // derivative of unknown c at that position's cell (its pressure derivative the
 // column of dP/dU there); a boundary ghost depends on the cell itself (dual
 // numbers through the boundary rule), so it enters the C block.
-__global__ void k_mg_assemble2d(Dev<float> g, const float* __restrict__ U, const float* __restrict__ pj,
+// three CTAs per SM (at most 85 registers): the kernel is latency-bound
+__global__ void __launch_bounds__(kMgThreads, 3) k_mg_assemble2d(Dev<float> g, const float* __restrict__ U,
+                                                                const float* __restrict__ pj,
                                 float* __restrict__ A) {
     const int nx = g.n[0];
     const long long N = g.N;
@@ -166,7 +168,6 @@ __global__ void k_mg_assemble2d(Dev<float> g, const float* __restrict__ U, const
         const bool wbc = g.wb && !(g.fb && g.fb[i]);
         MgFace fc[4];
         long long nbi[4];
-        bool any_boundary = false;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
 #pragma unroll
@@ -176,7 +177,6 @@ __global__ void k_mg_assemble2d(Dev<float> g, const float* __restrict__ U, const
                 const bool inside = ca >= 0 && ca < g.n[a];
                 const bool periodic = g.bc[a][side] == BC_PERIODIC;
                 f.boundary = !inside && !periodic;
-                any_boundary |= f.boundary;
                 long long j = -1;
                 if (inside)
                     j = i + (side ? g.stride[a] : -g.stride[a]);
@@ -198,35 +198,9 @@ __global__ void k_mg_assemble2d(Dev<float> g, const float* __restrict__ U, const
                 f.pm = f.lp * f.lm * f.inv;
             }
         }
-        // ghost derivatives: gd[face][seed c][quantity]
-        float gd[4][3][6];
-        if (any_boundary) {
-            const LoadSeed<float> ld{U, N, -1};  // in-domain loads (not taken on a boundary face): no seed
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                if (!fc[p].boundary) continue;
-                const int a = p / 2, side = p % 2;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    St<Dual<float>, 2> self;
-                    self.E = Dual<float>{U[i], c == 0 ? 1.f : 0.f};
-                    self.F[0] = Dual<float>{U[N + i], c == 1 ? 1.f : 0.f};
-                    self.F[1] = Dual<float>{U[2 * N + i], c == 2 ? 1.f : 0.f};
-                    float sn;
-                    bool bnd;
-                    const St<Dual<float>, 2> gh = neighbour<Dual<float>, 2, false>(g, ld, self, i, coord, a, side, sn, bnd);
-                    const Cl<Dual<float>, 2> k = closure(gh, g.c);
-                    gd[p][c][0] = gh.E.d;
-                    gd[p][c][1] = gh.F[0].d;
-                    gd[p][c][2] = gh.F[1].d;
-                    gd[p][c][3] = pressure(k, 0, 0).d;
-                    gd[p][c][4] = pressure(k, 0, 1).d;
-                    gd[p][c][5] = pressure(k, 1, 1).d;
-                }
-            }
-        }
         const float zero[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
+        const LoadSeed<float> ld{U, N, -1};  // in-domain loads (not taken on a boundary face): no seed
+#pragma unroll 1
         for (int c = 0; c < 3; ++c) {
             // C: the cell's own unknown c (unit derivative, dP the column c of dP/dU),
             // and through the boundary rules the ghosts of its boundary faces
@@ -236,8 +210,30 @@ __global__ void k_mg_assemble2d(Dev<float> g, const float* __restrict__ U, const
             float out[3];
             mg_lin_self(g, t0, sig_self, sig_a, wbc, out);
 #pragma unroll
-            for (int p = 0; p < 4; ++p) mg_lin_face(g, t0, fc[p].boundary ? gd[p][c] : zero, fc[p], p / 2, p % 2,
-                                                    sig_self, wbc, out);
+            for (int p = 0; p < 4; ++p) {
+                float gh[6];
+                if (fc[p].boundary) {  // the ghost's derivatives in the cell's unknown c (dual numbers)
+                    St<Dual<float>, 2> self;
+                    self.E = Dual<float>{U[i], c == 0 ? 1.f : 0.f};
+                    self.F[0] = Dual<float>{U[N + i], c == 1 ? 1.f : 0.f};
+                    self.F[1] = Dual<float>{U[2 * N + i], c == 2 ? 1.f : 0.f};
+                    float sn;
+                    bool bnd;
+                    const St<Dual<float>, 2> u = neighbour<Dual<float>, 2, false>(g, ld, self, i, coord, p / 2, p % 2,
+                                                                                 sn, bnd);
+                    const Cl<Dual<float>, 2> k = closure(u, g.c);
+                    gh[0] = u.E.d;
+                    gh[1] = u.F[0].d;
+                    gh[2] = u.F[1].d;
+                    gh[3] = pressure(k, 0, 0).d;
+                    gh[4] = pressure(k, 0, 1).d;
+                    gh[5] = pressure(k, 1, 1).d;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) gh[q] = 0.f;
+                }
+                mg_lin_face(g, t0, gh, fc[p], p / 2, p % 2, sig_self, wbc, out);
+            }
 #pragma unroll
             for (int r = 0; r < 3; ++r) A[((long long)(0 * 3 + r) * 3 + c) * N + i] = out[r];
             // W, E, S, N: the neighbour's unknown c enters through the one face they share
