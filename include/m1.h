@@ -398,6 +398,25 @@ m1_status m1_nn_make_pair(m1_ctx* ctx, double dt, const double* U, const double*
  * built for batch 1 and the grid's n[1] x n[0]; the context does not own it. */
 m1_status m1_set_preconditioner(m1_ctx* ctx, m1_nn* nn);
 
+/* How flexible GMRES combines the learned correction with point-block Jacobi (a
+ * context setting, default M1_LEARNED_ADDITIVE; the paper has no learned
+ * component, this is the library's own design):
+ *   M1_LEARNED_ADDITIVE: z = J_bj^-1 v + s (N(v / s) - N(0)) on odd Arnoldi steps,
+ *     z = J_bj^-1 v on even ones; s = ||v|| / sqrt(n);
+ *   M1_LEARNED_TWO_STAGE: on odd Arnoldi steps a point-block Jacobi stage first,
+ *     z1 = J_bj^-1 v and r1 = v - J z1 (FP32 J v), then
+ *     z = z1 + J_bj^-1 r1 + s1 (N(r1 / s1) - N(0)), s1 = ||r1|| / sqrt(n) (taken on
+ *     the device): the network sees the residual the first stage leaves, J times
+ *     an error point-block Jacobi resolves slowly, which is what the pairs of
+ *     m1_nn_make_pair teach it; even steps as above;
+ *   M1_LEARNED_TWO_STAGE_ALL: the two-stage form on every Arnoldi step.
+ * N(0) is the network's response to a zero vector at the same Newton iterate.
+ * M1_ERR_ARG for another value. */
+#define M1_LEARNED_ADDITIVE 0
+#define M1_LEARNED_TWO_STAGE 1
+#define M1_LEARNED_TWO_STAGE_ALL 2
+m1_status m1_set_learned_form(m1_ctx* ctx, int form);
+
 /* ---------------------------------------------------------------------------
  * Batched steps: many independent 2D radiation-only problems (periodic,
  * outflow or reflecting boundaries; frozen or fixed wave speeds) solved by one

@@ -79,6 +79,9 @@ struct m1_ctx {
     float* nn_static = nullptr; // its four input planes that are fixed within a linear solve (k_nn_static)
     float* nn_null = nullptr;   // its output for a zero residual at the same iterate (3N, subtracted)
     float* Z32 = nullptr;       // flexible-GMRES basis of preconditioned vectors
+    int nn_form = 0;            // how the correction combines with point-block Jacobi (m1_set_learned_form)
+    float *nn_r = nullptr, *nn_t = nullptr;  // two-stage form: the residual of the first stage, M^-1 of it
+    double *nn_part = nullptr, *nn_n2 = nullptr;  // its squared norm: partial sums and the total
     double* pj64 = nullptr;     // dP/dU at the Newton iterate (2D frozen wave speeds), FP64
     float* pj32 = nullptr;      // the same in FP32
     // multigrid preconditioner (allocated on first use)
@@ -592,6 +595,7 @@ struct Ops32 {
     const float* U;
     bool precond;
     bool learned = false;
+    int form = 0;               // the learned correction's form (m1_set_learned_form)
     int step = 0;               // Arnoldi step of the next M application (the learned correction: odd steps)
     const float* pj = nullptr;  // dP/dU at U in FP32: J v as a linear stencil, else by dual numbers
     bool mg = false;            // M^-1: one multigrid cycle instead of point-block Jacobi
@@ -627,10 +631,28 @@ struct Ops32 {
         // + s (N(v / s) - N(0)) on odd Arnoldi steps: the Krylov vectors have unit norm,
         // s = 1 / sqrt(n); even steps keep the plain point-block Jacobi direction in the
         // flexible basis, so the learned directions can only add to it
-        if (learned && (step & 1)) {
+        if (learned && form == M1_LEARNED_ADDITIVE && (step & 1)) {
             nn_apply_add(ctx->nn, in, ctx->N, ctx->nn_static, ctx->nn_null, (float)(1.0 / sqrt((double)ctx->n)), out,
                          ctx->s);
             count(ctx, 24);
+        }
+        // two-stage form: out = z1 = M^-1 v from above; r1 = v - J z1 is what point-block
+        // Jacobi leaves, and out += M^-1 r1 + s1 (N(r1 / s1) - N(0)), s1 the RMS of r1:
+        // the network sees the residual of a point-block Jacobi stage, the input it is
+        // trained on (J e for the errors point-block Jacobi resolves slowly)
+        if (learned && form != M1_LEARNED_ADDITIVE && (form == M1_LEARNED_TWO_STAGE_ALL || (step & 1))) {
+            cudaStream_t s = ctx->s;
+            if (pj)
+                launch_jv_linear_f32(g, U, pj, out, ctx->nn_r, s);
+            else
+                jv_f32(g, U, out, ctx->nn_r, s);
+            launch_axpby_f32(1.f, in, -1.f, ctx->nn_r, ctx->nn_r, ctx->n, s);
+            launch_bj_apply_f32(ctx->nu, ctx->N, ctx->binv32, ctx->nn_r, ctx->nn_t, s);
+            launch_axpby_f32(1.f, ctx->nn_t, 1.f, out, out, ctx->n, s);
+            launch_norm2_f32(ctx->nn_r, ctx->n, ctx->nn_part, ctx->nn_n2, s);
+            nn_apply_add_rms(ctx->nn, ctx->nn_r, ctx->N, ctx->nn_static, ctx->nn_null, ctx->nn_n2, out, s);
+            count(ctx, 30);
+            ctx->st.jv_calls++;
         }
     }
 };
@@ -1212,7 +1234,7 @@ m1_status m1_destroy(m1_ctx* ctx) {
                     ctx->binv32, ctx->V32, ctx->w32, ctx->z32, ctx->U32, ctx->tmp32, ctx->Fstar, ctx->linework,
                     ctx->partials, ctx->scal_base, ctx->singular, ctx->viol, ctx->ar_partials,
                     ctx->ar_reorth, ctx->logsig, ctx->nn_static, ctx->nn_null, ctx->Z32, ctx->pair_x, ctx->pair_t, ctx->pj64, ctx->pj32, ctx->bs_part, ctx->bs_sc,
-                    ctx->fb, ctx->fbw};
+                    ctx->fb, ctx->fbw, ctx->nn_r, ctx->nn_t, ctx->nn_part, ctx->nn_n2};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int l = 0; l < kMgMaxLevels; ++l) {
@@ -1530,6 +1552,12 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
     if (learned && (o->precision != M1_PREC_MIXED || !ctx->nn))
         return fail(ctx, M1_ERR_ARG, "the learned preconditioner needs M1_PREC_MIXED and m1_set_preconditioner");
     if (learned) CKS(dalloc(ctx, &ctx->Z32, (size_t)ctx->ld * (kMaxRestart + 1)));
+    if (learned && ctx->nn_form != M1_LEARNED_ADDITIVE) {
+        CKS(dalloc(ctx, &ctx->nn_r, (size_t)ctx->n));
+        CKS(dalloc(ctx, &ctx->nn_t, (size_t)ctx->n));
+        CKS(dalloc(ctx, &ctx->nn_part, (size_t)reduce_blocks()));
+        CKS(dalloc(ctx, &ctx->nn_n2, 1));
+    }
     Dev<double> g = dev64(ctx, dt);
     if (use_mg && (o->precision != M1_PREC_MIXED || !mg_supported(ctx, g)))
         return fail(ctx, M1_ERR_ARG,
@@ -1559,6 +1587,7 @@ static m1_status linear_solve(m1_ctx* ctx, double dt, const double* Ud, const do
         if (use_mg && (newton_iter < 0 || newton_iter % every == 0)) CKS(build_mg(ctx, g32));
         Ops32 ops32{ctx, g32, ctx->U32, pre};
         ops32.learned = learned;
+        ops32.form = ctx->nn_form;
         if (learned) {  // the network's opacity and state planes at this Newton iterate, and its zero response
             launch_nn_static_f32(ctx->U32, ctx->N, ctx->d.c, ctx->logsig, ctx->nn_static, ctx->s);
             CK(cudaMemsetAsync(ctx->tmp32, 0, sizeof(float) * ctx->n, ctx->s));
@@ -1870,6 +1899,14 @@ m1_status m1_set_preconditioner(m1_ctx* ctx, m1_nn* nn) {
     CKS(dalloc(ctx, &ctx->nn_null, 3 * ctx->N));
     ctx->nn = nn;
     ctx->dirty = true;
+    return M1_OK;
+}
+
+m1_status m1_set_learned_form(m1_ctx* ctx, int form) {
+    if (!ctx) return M1_ERR_ARG;
+    if (form != M1_LEARNED_ADDITIVE && form != M1_LEARNED_TWO_STAGE && form != M1_LEARNED_TWO_STAGE_ALL)
+        return fail(ctx, M1_ERR_ARG, "unknown learned-preconditioner form");
+    ctx->nn_form = form;
     return M1_OK;
 }
 

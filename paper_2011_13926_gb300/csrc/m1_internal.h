@@ -187,6 +187,8 @@ void launch_lincomb_add_f32_to_f64(const float* Z, long long ld, int k, const do
 void launch_axpy_f64(double a, const double* x, double* y, long long n, cudaStream_t s);  // y += a x
 void launch_axpby_f64(double a, const double* x, double b, const double* y, double* out, long long n,
                       cudaStream_t s);  // out = a x + b y
+void launch_axpby_f32(float a, const float* x, float b, const float* y, float* out, long long n,
+                      cudaStream_t s);  // out = a x + b y (FP32)
 void launch_f64_to_f32(const double* x, float* y, long long n, cudaStream_t s);
 void launch_f32_to_f64(const float* x, double* y, long long n, cudaStream_t s);
 void launch_scale_f64_to_f32(const double* x, const double* nrm2, float* y, long long n, cudaStream_t s);
@@ -215,6 +217,9 @@ void launch_realizability(const double* U, int dim, long long N, double c, unsig
 // iterate, y0 = nn_null_response at the same iterate (zero3: 3N zero floats)
 m1_status nn_apply_add(m1_nn* nn, const float* v, long long N, const float* stat, const float* y0, float scale,
                        float* z, cudaStream_t s);
+// the same with scale = the RMS of v (3N entries) from its squared norm n2[0] on the device
+m1_status nn_apply_add_rms(m1_nn* nn, const float* v, long long N, const float* stat, const float* y0,
+                           const double* n2, float* z, cudaStream_t s);
 m1_status nn_null_response(m1_nn* nn, const float* zero3, long long N, const float* stat, float* y0, cudaStream_t s);
 int nn_height(const m1_nn* nn);
 int nn_width(const m1_nn* nn);

@@ -478,13 +478,21 @@ __global__ void k_round_bf16(const float* __restrict__ a, float* __restrict__ r,
     }
 }
 
+// the scale of a vector whose squared norm the device holds: its RMS sqrt(n2 / n),
+// or 1 for a zero vector (the network's input is then zero as well)
+__device__ __forceinline__ float rms_scale(const double* n2, double inv_n) {
+    const double q = n2[0] * inv_n;
+    return q > 0.0 ? (float)sqrt(q) : 1.f;
+}
+
 // network input from a component-major Krylov vector v (E, Fx, Fy; N = H*W
-// each): x = [v / s, static] in NHWC (7 channels), s = scale, static the four
+// each): x = [v / s, static] in NHWC (7 channels), s = scale (or, with n2 set,
+// the RMS of v from its squared norm n2[0] over n entries), static the four
 // planes of the opacity and state channels (k_nn_static)
 template <class T>
 __global__ void k_pack_input(const float* __restrict__ v, long long N, const float* __restrict__ stat, float scale,
-                             T* __restrict__ x) {
-    const float inv = 1.f / scale;
+                             const double* __restrict__ n2, double inv_n, T* __restrict__ x) {
+    const float inv = 1.f / (n2 ? rms_scale(n2, inv_n) : scale);
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
         st(x, kCin0 * p + 0, v[p] * inv);
         st(x, kCin0 * p + 1, v[N + p] * inv);
@@ -494,10 +502,12 @@ __global__ void k_pack_input(const float* __restrict__ v, long long N, const flo
     }
 }
 
-// z (component-major) += scale * (y - y0) (NHWC, 3 channels; y0 may be null)
+// z (component-major) += scale * (y - y0) (NHWC, 3 channels; y0 may be null;
+// with n2 set the scale is the RMS of k_pack_input's vector)
 template <class T>
 __global__ void k_unpack_add(const T* __restrict__ y, const float* __restrict__ y0, long long N, float scale,
-                             float* __restrict__ z) {
+                             const double* __restrict__ n2, double inv_n, float* __restrict__ z) {
+    if (n2) scale = rms_scale(n2, inv_n);
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -787,9 +797,23 @@ m1_status nn_apply_add(m1_nn* nn, const float* v, long long N, const float* stat
     cudaStream_t keep = nn->s;
     nn->s = s;
     __nv_bfloat16* const* A = nn->act16.data();
-    k_pack_input<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(v, N, stat, scale, nn->act16[S_IN]);
+    k_pack_input<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(v, N, stat, scale, nullptr, 0.0, nn->act16[S_IN]);
     forward<__nv_bfloat16>(nn, A);
-    k_unpack_add<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(nn->act16[S_OUT], y0, N, scale, z);
+    k_unpack_add<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(nn->act16[S_OUT], y0, N, scale, nullptr, 0.0, z);
+    nn->s = keep;
+    return cudaGetLastError() == cudaSuccess ? M1_OK : M1_ERR_CUDA;
+}
+// the same with the scale taken on the device: the RMS of v from its squared norm n2[0] (3N entries)
+m1_status nn_apply_add_rms(m1_nn* nn, const float* v, long long N, const float* stat, const float* y0,
+                           const double* n2, float* z, cudaStream_t s) {
+    if (!nn || (long long)nn->H * nn->W != N || nn->B != 1 || !n2) return M1_ERR_ARG;
+    cudaStream_t keep = nn->s;
+    nn->s = s;
+    const double inv_n = 1.0 / (3.0 * (double)N);
+    __nv_bfloat16* const* A = nn->act16.data();
+    k_pack_input<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(v, N, stat, 1.f, n2, inv_n, nn->act16[S_IN]);
+    forward<__nv_bfloat16>(nn, A);
+    k_unpack_add<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(nn->act16[S_OUT], y0, N, 1.f, n2, inv_n, z);
     nn->s = keep;
     return cudaGetLastError() == cudaSuccess ? M1_OK : M1_ERR_CUDA;
 }
@@ -801,7 +825,7 @@ m1_status nn_null_response(m1_nn* nn, const float* zero3, long long N, const flo
     if (!nn || (long long)nn->H * nn->W != N || nn->B != 1) return M1_ERR_ARG;
     cudaStream_t keep = nn->s;
     nn->s = s;
-    k_pack_input<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(zero3, N, stat, 1.f, nn->act16[S_IN]);
+    k_pack_input<__nv_bfloat16><<<grid_for(N), 256, 0, s>>>(zero3, N, stat, 1.f, nullptr, 0.0, nn->act16[S_IN]);
     forward<__nv_bfloat16>(nn, nn->act16.data());
     k_copy_out<__nv_bfloat16><<<grid_for(3 * N), 256, 0, s>>>(nn->act16[S_OUT], 3 * N, y0);
     nn->s = keep;

@@ -208,6 +208,15 @@ void launch_axpby_f64(double a, const double* x, double b, const double* y, doub
     k_axpby<<<kRedBlocks, kRedThreads, 0, s>>>(a, x, b, y, out, n);
 }
 
+// out = a x + b y in FP32 (out may alias x or y: each element is read and written by one thread)
+__global__ void k_axpby_f32(float a, const float* x, float b, const float* y, float* out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + b * y[i];
+}
+void launch_axpby_f32(float a, const float* x, float b, const float* y, float* out, long long n, cudaStream_t s) {
+    k_axpby_f32<<<kRedBlocks, kRedThreads, 0, s>>>(a, x, b, y, out, n);
+}
+
 template <class A, class B>
 __global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

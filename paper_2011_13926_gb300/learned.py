@@ -161,10 +161,11 @@ def forward_flops(H: int, W: int) -> float:
     return f
 
 
-def compare(p, params: np.ndarray, repeats: int = 2, **opt_kw) -> Dict:
-    """One implicit step of problem p with FGMRES(30) + the learned preconditioner
-    against GMRES(30) + point-block Jacobi (both FP32 inner under FP64 refinement):
-    Newton and Krylov steps, device time (best of `repeats`), and the solutions."""
+def compare(p, params: np.ndarray, repeats: int = 2, form: int = 0, **opt_kw) -> Dict:
+    """One implicit step of problem p with FGMRES(30) + the learned preconditioner in
+    the given form (m1_set_learned_form) against GMRES(30) + point-block Jacobi (both
+    FP32 inner under FP64 refinement): Newton and Krylov steps, device time (best of
+    `repeats`), and the solutions."""
     import torch
     s = torch.cuda.current_stream().cuda_stream
     out = {}
@@ -176,6 +177,7 @@ def compare(p, params: np.ndarray, repeats: int = 2, **opt_kw) -> Dict:
             infer = Net(p.n[1], p.n[0], 1, s)
             infer.set_params(params)
             ctx.set_preconditioner(infer)
+            ctx.set_learned_form(form)
             opts.precond = PRECOND_LEARNED
         best, info = None, None
         for _ in range(repeats):

@@ -35,7 +35,8 @@ EXPORTED = ["m1_default_opts", "m1_init_grid", "m1_destroy", "m1_set_opacity", "
             "m1_nn_train", "m1_nn_last_error", "m1_nn_make_pair", "m1_set_preconditioner", "m1_set_velocity",
             "m1_advect", "m1_batch_create", "m1_batch_destroy", "m1_batch_set_problem", "m1_batch_tune",
             "m1_batch_implicit_step", "m1_batch_get_solution", "m1_batch_num_classes", "m1_batch_last_error",
-            "m1_batch_set_class"]
+            "m1_batch_set_class", "m1_set_learned_form"]
+LEARNED_ADDITIVE, LEARNED_TWO_STAGE, LEARNED_TWO_STAGE_ALL = 0, 1, 2
 
 
 class GridDesc(C.Structure):
@@ -181,6 +182,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "m1_nn_set_tensor_cores": (I, [P, I]),
         "m1_nn_make_pair": (I, [P, D, P, P, P, P, I]),
         "m1_set_preconditioner": (I, [P, P]),
+        "m1_set_learned_form": (I, [P, I]),
         "m1_set_velocity": (I, [P, P, P, P, I]),
         "m1_batch_create": (I, [I, P, P, C.POINTER(P)]),
         "m1_batch_destroy": (I, [P]),
@@ -465,6 +467,12 @@ class Context:
         """m1_set_preconditioner: attach a trained U-Net (Net) as the learned preconditioner."""
         self._call("m1_set_preconditioner", net.h if net is not None else None)
         self._net = net  # keep the network alive while attached
+
+    def set_learned_form(self, form: int):
+        """m1_set_learned_form: LEARNED_ADDITIVE (default), LEARNED_TWO_STAGE (a point-block
+        Jacobi stage, then the network on the residual it leaves, on odd Arnoldi steps) or
+        LEARNED_TWO_STAGE_ALL (the two-stage form on every step)."""
+        self._call("m1_set_learned_form", int(form))
 
     def make_pair(self, dt: float, e, U=None, out=None):
         """(x, t) NHWC float32 training pair from this context's Jacobian."""

@@ -133,8 +133,9 @@ def test_make_pair_matches_oracle(m1mod):
 
 def test_training_and_learned_fgmres(m1mod):
     """Train on pairs from the plain solver's Jacobians of seeded problems,
-    then solve a held-out step with FGMRES + the network; the result must meet
-    the same parity bar as the other implicit paths."""
+    then solve a held-out step with FGMRES + the network in each of its forms;
+    every result must meet the same parity bar as the other implicit paths, and
+    the two-stage forms must take fewer Krylov steps than point-block Jacobi."""
     n = 32
     pairs_x, pairs_t = [], []
     for k in range(6):
@@ -166,11 +167,14 @@ def test_training_and_learned_fgmres(m1mod):
     infer = m1mod.Net(n, n, 1)
     infer.set_params(net.get_params())
     out = {}
-    for kind in ("bj", "learned"):
+    forms = {"learned": m1mod.LEARNED_ADDITIVE, "two_stage": m1mod.LEARNED_TWO_STAGE,
+             "two_stage_all": m1mod.LEARNED_TWO_STAGE_ALL}
+    for kind in ("bj",) + tuple(forms):
         ctx = m1mod.context_from_problem(p)
         opts = m1mod.default_opts(newton_rtol=1e-10, gmres_rtol=1e-8, advance=0, precision=m1mod.PREC_MIXED)
-        if kind == "learned":
+        if kind in forms:
             ctx.set_preconditioner(infer)
+            ctx.set_learned_form(forms[kind])
             opts.precond = m1mod.PRECOND_LEARNED
         st, inf = ctx.implicit_step(p.dt, opts)
         assert inf.converged
@@ -181,4 +185,8 @@ def test_training_and_learned_fgmres(m1mod):
             a, b = u[c * N:(c + 1) * N], ref.u[c * N:(c + 1) * N]
             assert np.abs(a - b).max() <= 1e-7 * max(np.abs(b).max(), 1e-300)
         out[kind] = inf.gmres_iters
-    print("gmres iterations (bj, learned):", out["bj"], out["learned"])
+    print("gmres iterations:", out)
+    # what the trained network gains: in the two-stage forms (point-block Jacobi, then the
+    # network on the residual it leaves) FGMRES needs fewer Krylov steps than point-block
+    # Jacobi alone to the same tolerance (measured: 673 -> 429 and 339)
+    assert out["two_stage"] < out["bj"] and out["two_stage_all"] < 0.8 * out["bj"], out
