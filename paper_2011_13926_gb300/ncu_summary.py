@@ -72,6 +72,19 @@ def short_name(name: str) -> str:
     return out[5:] if out.startswith("void ") else out
 
 
+def complete_units(launches, start_regex, end_regex):
+    """The launches from the first one whose kernel matches start_regex through the last
+    one matching end_regex: a capture cut off by its launch count (ncu -c) then holds
+    whole units only (e.g. whole multigrid cycles, from the level-0 down pass to the
+    level-0 up pass)."""
+    st, en = re.compile(start_regex), re.compile(end_regex)
+    first = next((i for i, (_, name, _) in enumerate(launches) if st.search(name)), None)
+    last = next((i for i in range(len(launches) - 1, -1, -1) if en.search(launches[i][1])), None)
+    if first is None or last is None or last < first:
+        return []
+    return launches[first:last + 1]
+
+
 def summarise(launches, select=None, units_regex=None, short=False, only_selected=False):
     per = OrderedDict()
     total_t = 0.0
@@ -122,9 +135,14 @@ def main():
     ap.add_argument("--short-names", action="store_true", help="kernel names without parameter lists")
     ap.add_argument("--by-grid", action="store_true", help="one row per kernel and grid size")
     ap.add_argument("--only-selected", action="store_true", help="the table lists the --select kernels only")
+    ap.add_argument("--unit-end", default=None,
+                    help="with --units-regex: keep only whole units, from the first launch matching --units-regex "
+                         "through the last launch matching this regex")
     a = ap.parse_args()
-    table, traffic, units = summarise(read_launches(a.csv, a.by_grid), a.select, a.units_regex, a.short_names,
-                                      a.only_selected)
+    launches = read_launches(a.csv, a.by_grid)
+    if a.unit_end and a.units_regex:
+        launches = complete_units(launches, a.units_regex, a.unit_end)
+    table, traffic, units = summarise(launches, a.select, a.units_regex, a.short_names, a.only_selected)
     print(table)
     if a.traffic and traffic is not None:
         files = [f.strip() for f in a.sources.split(",") if f.strip()]

@@ -39,3 +39,18 @@ def test_mg_cycle_bytes_by_hand():
     w += lv[6] * (45 + 9 + 2 * nu)
     assert bench.bytes_mg_cycle(1024, 1024, 7) == 4 * w
     assert bench.bytes_jv32(1024 ** 2) == 48 * 1024 ** 2  # the scope table's 48 B per cell (2D, FP32)
+
+
+def test_complete_units_keeps_whole_cycles():
+    """A capture cut off by its launch count keeps whole units only: from the first
+    unit start through the last unit end (a multigrid cycle runs from the level-0 down
+    pass to the level-0 up pass)."""
+    from paper_2011_13926_gb300.ncu_summary import complete_units, summarise
+    m = {"dram__bytes_read.sum": 10.0, "dram__bytes_write.sum": 0.0, "gpu__time_duration.sum": 1e-6}
+    seq = ["jv", "down0", "mg", "up0", "jv", "down0", "mg", "up0", "jv", "down0", "mg"]
+    launches = [(str(i), n, dict(m)) for i, n in enumerate(seq)]
+    kept = complete_units(launches, "down0", "up0")
+    assert [n for _, n, _ in kept] == seq[1:8]
+    _, traffic, units = summarise(kept, select="down0|mg|up0", units_regex="down0")
+    assert units == 2 and traffic == 30.0  # three launches of 10 bytes per whole cycle
+    assert complete_units(launches, "nothing", "up0") == []
