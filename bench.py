@@ -54,6 +54,9 @@ def args_():
     ap.add_argument("--train-krylov-steps", type=int, default=0,
                     help="learned workload: random training directions are smooth fields (0) or the error they "
                          "leave after this many point-block Jacobi GMRES steps")
+    ap.add_argument("--train-first-stage", type=int, default=0, choices=[0, 1],
+                    help="learned workload: 1 turns each random training direction e into the error one "
+                         "point-block Jacobi stage leaves of it (the input of the two-stage forms)")
     ap.add_argument("--learned-forms", default="0,1",
                     help="forms of the learned preconditioner timed (m1_set_learned_form: 0 additive, 1 two-stage "
                          "on odd Arnoldi steps, 2 two-stage on every step); the first is the line's value")
@@ -64,9 +67,10 @@ def args_():
     ap.add_argument("--other-steps", type=int, default=2, help="timed steps per other dt")
     ap.add_argument("--forcing", default="fixed", choices=["fixed", "ew"],
                     help="linear-solve tolerance: fixed (--gmres-rtol), or Eisenstat-Walker (m1_solver_opts.forcing)")
-    ap.add_argument("--gmres-rtol", type=float, default=5e-3,
-                    help="fixed relative tolerance of every linear solve of the headline path "
-                         "(m1_solver_opts.gmres_rtol); the Newton test stays ||R|| <= 1e-8 ||R(U^n)|| in FP64")
+    ap.add_argument("--gmres-rtol", type=float, default=None,
+                    help="fixed relative tolerance of every linear solve of the mixed path "
+                         "(m1_solver_opts.gmres_rtol; default 5e-3 for the beam, 1e-4 for gas3d); the Newton "
+                         "test stays ||R|| <= 1e-8 ||R(U^n)|| in FP64")
     ap.add_argument("--plain-gmres-rtol", type=float, default=1e-4,
                     help="the same for the plain FP64 arm (1e-4: its fastest measured forcing; at 1e-3 its full "
                          "steps take longer and its backtracking does not converge within 80 Newton steps)")
@@ -333,7 +337,7 @@ def run_learned(a):
 
     res = learned.train(prob, range(1000, 1100), n=n, rounds=a.train_rounds, pairs_per_round=a.train_pairs,
                         epochs=4, lr=1e-3, lr_final=1e-4, krylov_steps=a.train_krylov_steps,
-                        init=unet.init_params(0))
+                        init=unet.init_params(0), first_stage=bool(a.train_first_stage))
     form_names = {0: "additive", 1: "two_stage", 2: "two_stage_all"}
     forms = [int(f) for f in a.learned_forms.split(",") if f.strip()]
     paths = {"mixed_learned": dict(precision=m1.PREC_MIXED, precond=learned.PRECOND_LEARNED, form=forms[0])}
@@ -409,7 +413,9 @@ def run_learned(a):
             "training": {"pairs": res["pairs"], "seconds": res["seconds"], "first_loss": res["first_loss"],
                          "final_loss": res["final_loss"], "rounds": a.train_rounds,
                          "directions": ("smooth random fields" if a.train_krylov_steps == 0 else
-                                        f"errors left by {a.train_krylov_steps} point-block Jacobi GMRES steps")},
+                                        f"errors left by {a.train_krylov_steps} point-block Jacobi GMRES steps")
+                                       + (", then the error one point-block Jacobi stage leaves"
+                                          if a.train_first_stage else "")},
             "paths": out, "speedup_vs_plain_fp64": v / plain if v and plain else None,
             "roofline": {"bound": "tensor", "kernel_class": "network forward (tensor-core convolutions)",
                          "achieved": flops / (fwd_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -473,7 +479,8 @@ def run_gas3d(a):
             infos.append(info)
         return ms, infos
 
-    opts = m1.default_opts(precision=m1.PREC_MIXED, gmres_max=3000)
+    rtol = 1e-4 if a.gmres_rtol is None else a.gmres_rtol
+    opts = m1.default_opts(precision=m1.PREC_MIXED, gmres_max=3000, gmres_rtol=rtol)
     timed(opts, a.warmup)
     s0 = ctx.stats()
     clocks = ClockSampler(0)
@@ -487,7 +494,8 @@ def run_gas3d(a):
     p1 = ctx.stats()
     ctx.profile(False)
     ctx.set_fp64_arithmetic(m1.FP64_NATIVE)  # the plain arm: FP64 operations
-    mplain, iplain = timed(m1.default_opts(precision=m1.PREC_FP64, gmres_max=3000), a.plain_steps)
+    mplain, iplain = timed(m1.default_opts(precision=m1.PREC_FP64, gmres_max=3000, gmres_rtol=a.plain_gmres_rtol),
+                           a.plain_steps)
     peak, peak_src = measured_peaks()
     kms = {k: p1["kernel_ms"][k] - p0["kernel_ms"][k] for k in p1["kernel_ms"]}
     kcount = {k: p1["kernel_count"][k] - p0["kernel_count"][k] for k in p1["kernel_count"]}
@@ -637,6 +645,8 @@ def run_batch(a):
 # ----------------------------------------------------------------------------- GPU path
 def main():
     a = args_()
+    if a.gmres_rtol is None and a.workload != "gas3d":
+        a.gmres_rtol = 5e-3
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "learned":

@@ -76,12 +76,25 @@ def slow_modes(ctx, dt: float, U, e_true, krylov_steps: int):
     return e_true - x
 
 
+def first_stage_pair(ctx, dt: float, U, e, x_out, t_out):
+    """The pair of the error a point-block Jacobi stage leaves of e, e1 = e - J_bj^-1 J e
+    (up to scale): the network's input is then r1 = J e1, the residual the two-stage
+    forms hand it (m1_set_learned_form). The first m1_nn_make_pair gives e1 / s as its
+    target; the second makes the pair of e1."""
+    N = ctx.N
+    ctx.make_pair(dt, e, U=U, out=(x_out, t_out))
+    e1 = t_out.reshape(N, 3).t().contiguous().reshape(-1).double()
+    ctx.make_pair(dt, e1, U=U, out=(x_out, t_out))
+
+
 def collect_pairs(ctx, dt: float, X, T, start: int, gen, n_random: int = 6,
-                  ells=(1.0, 2.0, 4.0, 8.0), newton_max: int = 8, krylov_steps: int = 0) -> int:
+                  ells=(1.0, 2.0, 4.0, 8.0), newton_max: int = 8, krylov_steps: int = 0,
+                  first_stage: bool = False) -> int:
     """Fill rows start, start + 1, ... of the device buffers X (pairs x N x 7) and
     T (pairs x N x 3) from this context; returns the next free row (stops at the
     buffer's end). krylov_steps > 0: the random directions are replaced by the
-    error they leave after that many point-block Jacobi GMRES steps (slow_modes)."""
+    error they leave after that many point-block Jacobi GMRES steps (slow_modes);
+    first_stage: by the error one point-block Jacobi stage leaves (first_stage_pair)."""
     import torch
     cap = X.shape[0]
     i = start
@@ -91,13 +104,17 @@ def collect_pairs(ctx, dt: float, X, T, start: int, gen, n_random: int = 6,
         dirs = [torch.zeros_like(U)]  # a zero residual: the correction must vanish
         if k + 1 < len(its):
             dirs.append(its[k + 1] - U)
+        first = len(dirs)
         for q in range(n_random):
             e = smooth_fields(ny, nx, ells[q % len(ells)], gen)
             dirs.append(slow_modes(ctx, dt, U, e, krylov_steps) if krylov_steps > 0 else e)
-        for e in dirs:
+        for j, e in enumerate(dirs):
             if i >= cap:
                 return i
-            ctx.make_pair(dt, e, U=U, out=(X[i].reshape(-1), T[i].reshape(-1)))
+            if first_stage and j >= first:
+                first_stage_pair(ctx, dt, U, e, X[i].reshape(-1), T[i].reshape(-1))
+            else:
+                ctx.make_pair(dt, e, U=U, out=(X[i].reshape(-1), T[i].reshape(-1)))
             i += 1
     return i
 
@@ -105,7 +122,7 @@ def collect_pairs(ctx, dt: float, X, T, start: int, gen, n_random: int = 6,
 def train(problem: Callable[[int], object], seeds: Iterable[int], *, n: int, rounds: int, pairs_per_round: int,
           epochs: int = 2, lr: float = 1e-3, lr_final: float = 1e-4, batch: int = 4, n_random: int = 6,
           krylov_steps: int = 10, init: Optional[np.ndarray] = None, seed: int = 1,
-          log: Optional[Callable[[str], None]] = None) -> Dict:
+          log: Optional[Callable[[str], None]] = None, first_stage: bool = False) -> Dict:
     """Online training on problems problem(seed) of n x n cells (2D, radiation only);
     the random directions are the slow modes of krylov_steps point-block Jacobi GMRES
     steps (0: the smooth fields themselves).
@@ -133,7 +150,8 @@ def train(problem: Callable[[int], object], seeds: Iterable[int], *, n: int, rou
             p = problem(seeds[si % len(seeds)])
             si += 1
             ctx = context_from_problem(p, stream=torch.cuda.current_stream().cuda_stream, device=True)
-            filled = collect_pairs(ctx, p.dt, X, T, filled, gen, n_random=n_random, krylov_steps=krylov_steps)
+            filled = collect_pairs(ctx, p.dt, X, T, filled, gen, n_random=n_random, krylov_steps=krylov_steps,
+                                   first_stage=first_stage)
             ctx.close()
         seen += filled
         frac = r / max(rounds - 1, 1)
