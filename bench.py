@@ -89,6 +89,9 @@ def args_():
     ap.add_argument("--fp64-arith", default="auto", choices=["auto", "native", "double_word"],
                     help="FP64 arithmetic of the headline path's residual and J v (m1_set_fp64_arithmetic); "
                          "the plain FP64 arm always uses FP64 operations")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket each timed headline step by cudaProfilerStart/Stop, for an ncu capture of the "
+                         "whole step as one range (--replay-mode app-range)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=80,
@@ -695,15 +698,20 @@ def main():
                         forcing=1 if a.forcing == "ew" else 0)
     dt_cfl = p.dt / a.dt_factor
 
-    def timed_steps(o, k, dt=None):
+    def timed_steps(o, k, dt=None, profile_range=False):
         infos, ms = [], []
         for _ in range(k):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if profile_range:  # the step alone between cudaProfilerStart and cudaProfilerStop
+                torch.cuda.synchronize()
+                torch.cuda.profiler.start()
             e0.record()
             st, info = ctx.implicit_step(p.dt if dt is None else dt, o, raise_on_fail=False)
             e1.record()
             torch.cuda.synchronize()
+            if profile_range:
+                torch.cuda.profiler.stop()
             ms.append(e0.elapsed_time(e1))
             infos.append(info)
         return ms, infos
@@ -723,7 +731,7 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
-    ms, infos = timed_steps(opts, a.steps)
+    ms, infos = timed_steps(opts, a.steps, profile_range=a.profile_range)
     barrier()
     clk = clocks.stop()
     s1 = ctx.stats()
