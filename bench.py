@@ -469,15 +469,20 @@ def run_gas3d(a):
         ctx.velocity_sources(p.dt)
         return info
 
-    def timed(opts, k):
+    def timed(opts, k, profile_range=False):
         ms, infos = [], []
         for _ in range(k):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if profile_range:  # the step alone between cudaProfilerStart and cudaProfilerStop
+                torch.cuda.synchronize()
+                torch.cuda.profiler.start()
             e0.record()
             info = step(opts)
             e1.record()
             torch.cuda.synchronize()
+            if profile_range:
+                torch.cuda.profiler.stop()
             ms.append(e0.elapsed_time(e1))
             infos.append(info)
         return ms, infos
@@ -488,7 +493,7 @@ def run_gas3d(a):
     s0 = ctx.stats()
     clocks = ClockSampler(0)
     clocks.start()
-    ms, infos = timed(opts, a.steps)
+    ms, infos = timed(opts, a.steps, profile_range=a.profile_range)
     clk = clocks.stop()
     s1 = ctx.stats()
     ctx.profile(True)
@@ -514,6 +519,10 @@ def run_gas3d(a):
         roof["algorithmic_bytes"] = bytes_jv32_3d_gas(N)
     if roof["achieved"]:
         roof["frac"] = roof["achieved"] / peak
+    # whole-step bytes per cell-update from the committed range capture of this workload's step
+    bps, rec = profile_traffic(f"step_traffic_gas_point_source_{n}.md")
+    roof["step_dram_bytes_per_cell_update"] = bps / N if bps else None
+    roof["step_traffic_record"] = rec
     cpu = None
     if not a.no_cpu_baseline:
         from oracle import Scheme, newton_solve

@@ -9,7 +9,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.mark.parametrize("name", ["multigrid_cycle_beam_lognormal_1024_dt50.md",
-                                  "step_traffic_beam_lognormal_1024_dt50.md"])
+                                  "step_traffic_beam_lognormal_1024_dt50.md",
+                                  "step_traffic_gas_point_source_256.md"])
 def test_traffic_record_parses(name):
     import bench
     from paper_2011_13926_gb300.ncu_summary import source_hash
