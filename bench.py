@@ -69,7 +69,7 @@ def args_():
                     help="linear-solve tolerance: fixed (--gmres-rtol), or Eisenstat-Walker (m1_solver_opts.forcing)")
     ap.add_argument("--gmres-rtol", type=float, default=None,
                     help="fixed relative tolerance of every linear solve of the mixed path "
-                         "(m1_solver_opts.gmres_rtol; default 5e-3 for the beam, 1e-4 for gas3d); the Newton "
+                         "(m1_solver_opts.gmres_rtol; default 5e-3 for the beam and the batch, 1e-4 otherwise); the Newton "
                          "test stays ||R|| <= 1e-8 ||R(U^n)|| in FP64")
     ap.add_argument("--plain-gmres-rtol", type=float, default=1e-4,
                     help="the same for the plain FP64 arm (1e-4: its fastest measured forcing; at 1e-3 its full "
@@ -582,7 +582,7 @@ def run_batch(a):
     cells = sum(p.ncell for p in probs)
     dts = [p.dt for p in probs]
     B = m1.Batch(probs, s)
-    opts = m1.default_opts()
+    opts = m1.default_opts(gmres_rtol=1e-4 if a.gmres_rtol is None else a.gmres_rtol)
     chosen = B.tune(dts, opts)
     for _ in range(max(1, a.warmup - 1)):
         B.implicit_step(dts, opts)
@@ -607,7 +607,7 @@ def run_batch(a):
     B.close()
     # plain FP64, problem by problem through single-grid contexts
     plain_ms, plain_conv = 0.0, True
-    po = m1.default_opts(advance=0, precision=m1.PREC_FP64)
+    po = m1.default_opts(advance=0, precision=m1.PREC_FP64, gmres_rtol=a.plain_gmres_rtol)
     for p in probs:
         ctx = m1.context_from_problem(p, stream=s, device=True)
         st, inf = ctx.implicit_step(p.dt, po, raise_on_fail=False)
@@ -633,7 +633,8 @@ def run_batch(a):
                        "cells": cells, "problems": len(probs),
                        "path": "persistent CTA-per-problem classes (one CUDA graph) + single-grid contexts for the "
                                "classes m1_batch_tune sends there; FP32 inner GMRES(30) + FP64 refinement, "
-                               "point-block Jacobi"},
+                               "point-block Jacobi",
+                       "gmres_forcing": opts.gmres_rtol},
             "per_class": {f"{n}^2": {"problems": sum(1 for p in probs if p.n[0] == n),
                                      "path": ("single-grid" if int(chosen[i]) == 0
                                               else f"persistent, {int(chosen[i])} threads"),
@@ -657,7 +658,7 @@ def run_batch(a):
 # ----------------------------------------------------------------------------- GPU path
 def main():
     a = args_()
-    if a.gmres_rtol is None and a.workload != "gas3d":
+    if a.gmres_rtol is None and a.workload in ("beam", "batch"):
         a.gmres_rtol = 5e-3
     if a.impl == "reference":
         return run_reference(a)
@@ -866,6 +867,9 @@ def main():
                            "admissibility": ("a posteriori fallback: centred source, alpha = 1, speeds +-c in "
                                              "flagged cells" if rz else "none (violations counted)"),
                            "gmres_forcing": ("Eisenstat-Walker" if a.forcing == "ew" else a.gmres_rtol),
+                           "learned_arm": ("bench.py --workload learned: the learned preconditioner on 512^2 "
+                                           "systems, where it does not beat point-block Jacobi; this line's "
+                                           "preconditioner is the multigrid cycle"),
                            "wave_speeds": "frozen at time n",
                            "l2": "256 MiB buffer written between timed steps; basis traffic exceeds L2",
                            "parallelism": f"replicas x{world}"},
